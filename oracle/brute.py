@@ -1,0 +1,111 @@
+"""Brute-force 2^N state vector for small lattices -- TEST INFRASTRUCTURE ONLY.
+
+The amplitudes A(sigma) of Eq. Psi are built as a full state vector by
+absorbing the single-layer site tensors one at a time while keeping every
+physical leg open (never forming a double layer), then every quantity of
+Sec. 3 is evaluated directly on the vector:
+
+  norm        = sum_sigma A(sigma)^2                        (Eq. norm)
+  <X_k>       = sum_sigma A(sigma) A(sigma with k flipped) / norm   (Eq. mx)
+  <Z_i Z_j>   = sum_sigma A(sigma)^2 sigma_i sigma_j / norm (Eq. cij, 1st term)
+  E           = <Psi|H|Psi> / norm with H built as a sparse matrix from
+                Kronecker products (Eqs. Hamiltonian, Etot), and the exact
+                ground energy E_0 of that H by Lanczos (scipy eigsh).
+
+Basis convention: site k (row-major) is bit k of the basis index, bit = p, and
+p = 1 means sigma = +1 (x = (sigma + 1) / 2, Sec. 3).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def state_vector(L: int, W: int, D: int, flat: np.ndarray) -> np.ndarray:
+    """psi[index] with bit k of index = p of site k (row-major)."""
+    from paper_1908_08553_gb300.inputs import split_sites  # input layout only
+    sites = split_sites(np.asarray(flat, np.float64), L, W, D)
+    # T axes: [phys bits 0..k-1 (2 each, site 0 first)] + boundary legs
+    # boundary before site (r, c): dn_0..dn_{c-1} of row r, h, u_c..u_{W-1}
+    T = np.ones([1] * (W + 1))  # h + W u-legs of row 0, all of dimension 1
+    nphys = 0
+    for r in range(L):
+        for c in range(W):
+            A = sites[r * W + c]  # [p][u][l][dn][rt]
+            # boundary axes start after nphys; position of h is nphys + c,
+            # position of u_c is nphys + c + 1
+            ah, au = nphys + c, nphys + c + 1
+            # contract h with l and u_c with u -> result axes: rest of T + (p, dn, rt)
+            R = np.tensordot(T, A, axes=([ah, au], [2, 1]))
+            # R axes: T axes without (ah, au) in order, then p, dn, rt
+            nT = T.ndim - 2
+            p_ax, dn_ax, rt_ax = nT, nT + 1, nT + 2
+            # move p to position nphys (after the previous physical bits),
+            # dn to position nphys + 1 + c, rt right after it
+            order = list(range(nT))
+            phys = order[:nphys]
+            rest = order[nphys:]
+            new = phys + [p_ax] + rest[:c] + [dn_ax, rt_ax] + rest[c:]
+            T = np.transpose(R, new)
+            nphys += 1
+        # end of the row: the trailing h' (rt of the last column) has dim 1;
+        # re-insert a fresh dim-1 h before the dn legs for the next row
+        T = T.reshape(T.shape[:nphys] + T.shape[nphys:nphys + W] + (1,))
+        T = np.moveaxis(T, -1, nphys)
+    psi = T.reshape(T.shape[:nphys])
+    # psi axes: site 0 .. N-1; index bit k must be p of site k -> site k is the
+    # k-th least significant bit, so reverse the axis order before flattening
+    psi = np.transpose(psi, list(range(nphys))[::-1]).reshape(-1)
+    return psi
+
+
+def observables(L: int, W: int, D: int, flat: np.ndarray):
+    """(norm, <X_k>[N], <Z_i Z_j>[nb]) straight from the state vector."""
+    from paper_1908_08553_gb300.inputs import bonds
+    psi = state_vector(L, W, D, flat)
+    N = L * W
+    idx = np.arange(psi.size)
+    norm = float(psi @ psi)
+    sx = np.empty(N)
+    for k in range(N):
+        sx[k] = float(psi @ psi[idx ^ (1 << k)]) / norm
+    sig = [np.where((idx >> k) & 1, 1.0, -1.0) for k in range(N)]
+    zz = []
+    for (ri, ci), (rj, cj) in bonds(L, W):
+        i, j = ri * W + ci, rj * W + cj
+        zz.append(float(np.sum(psi * psi * sig[i] * sig[j])) / norm)
+    return norm, sx, np.array(zz)
+
+
+def hamiltonian(L: int, W: int, J: float, h: float):
+    """Sparse TFIM Hamiltonian -J sum Z_i Z_j - h sum X_k on the 2^N basis."""
+    import scipy.sparse as sp
+    from paper_1908_08553_gb300.inputs import bonds
+    N = L * W
+    dim = 1 << N
+    idx = np.arange(dim)
+    diag = np.zeros(dim)
+    for (ri, ci), (rj, cj) in bonds(L, W):
+        i, j = ri * W + ci, rj * W + cj
+        si = np.where((idx >> i) & 1, 1.0, -1.0)
+        sj = np.where((idx >> j) & 1, 1.0, -1.0)
+        diag -= J * si * sj
+    rows, cols, vals = [idx], [idx], [diag]
+    for k in range(N):
+        rows.append(idx)
+        cols.append(idx ^ (1 << k))
+        vals.append(np.full(dim, -h))
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(dim, dim))
+
+
+def energy(L: int, W: int, D: int, flat: np.ndarray, J: float, h: float) -> float:
+    psi = state_vector(L, W, D, flat)
+    H = hamiltonian(L, W, J, h)
+    return float(psi @ (H @ psi)) / float(psi @ psi)
+
+
+def ground_energy(L: int, W: int, J: float, h: float) -> float:
+    from scipy.sparse.linalg import eigsh
+    H = hamiltonian(L, W, J, h)
+    w = eigsh(H, k=1, which="SA", return_eigenvectors=False, tol=1e-10)
+    return float(w[0])
