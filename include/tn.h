@@ -1,0 +1,241 @@
+/*
+ * tn.h -- C-ABI of libtn: exact contraction of open-boundary PEPS on one GB300.
+ *
+ * What is computed (Sec. 3 of the paper, Eqs. norm, Etot, mx, cij):
+ *   <Psi|Psi>, every <X_k> (Eq. mx with S^x = X), every nearest-neighbour
+ *   <Z_i Z_j> (first term of Eq. cij) and the transverse-field Ising energy
+ *   E = -J sum_<ij> <Z_i Z_j> - h sum_k <X_k> (Eqs. Hamiltonian, Etot), with
+ *   Pauli operators (spins +-1) and Z = diag(-1, +1) on the physical index p,
+ *   because p = 1 is sigma = +1 (Eq. Psi, x = (sigma + 1)/2).
+ *
+ * How (Sec. 4): the double-layer network <Psi|O|Psi> (bond dimension D^2) is
+ * contracted exactly as chains of pairwise contractions that absorb one site
+ * into a large boundary tensor; the lattice is partitioned by the paper's
+ * minimum-bottleneck heuristic into up to four corners (row scheme, quadrant
+ * scheme or a cut in between) whose ring is closed by dense products.
+ *
+ * Site tensors (Sec. 5): site (r, c) of an L x W lattice holds
+ * A[p][u][l][dn][rt] in C order, p in {0, 1}, bond legs of dimension D and
+ * dimension 1 where a leg would leave the lattice (the paper's rank-3 edge and
+ * rank-2 corner tensors).  Sites are concatenated in row-major site order, so a
+ * lattice has n_elems = sum over sites of 2*u*l*dn*rt FP64 entries (288 for
+ * 4x4 D=2, 3872 for 12x12 D=2, 7200 for 8x8 D=3).
+ *
+ * Outputs: bonds are ordered horizontal (r,c)-(r,c+1) row-major first, then
+ * vertical (r,c)-(r+1,c) row-major; nb = L(W-1) + W(L-1).
+ *
+ * Conventions for every entry point:
+ *   - no C++ exception crosses this boundary; every call returns tn_status;
+ *   - the caller owns every host buffer passed in; the library copies tensors
+ *     on set/submit and owns its device memory, all of which it takes from the
+ *     context's HBM budget;
+ *   - a handle is used by one host thread at a time, except tn_submit /
+ *     tn_poll / tn_wait on one context, which are internally locked;
+ *   - a call that needs a GPU returns TN_ERR_NO_DEVICE on a context created
+ *     with device = -1 (planning-only context).
+ */
+#ifndef TN_H
+#define TN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TN_OK = 0,
+    TN_NOT_READY = 1,          /* tn_poll: the job is still running */
+    TN_ERR_INVALID = -1,       /* bad argument (sizes, pointers, enum values) */
+    TN_ERR_OVER_BUDGET = -2,   /* exact footprint exceeds the context's HBM budget */
+    TN_ERR_OOM = -3,           /* device allocation failed inside the budget */
+    TN_ERR_CUDA = -4,          /* a CUDA runtime call failed */
+    TN_ERR_TIMEOUT = -5,       /* tn_wait deadline passed, or a bounded device wait gave up */
+    TN_ERR_NUMERIC = -6,       /* non-finite result or zero norm */
+    TN_ERR_NO_DEVICE = -7      /* context has no GPU (device = -1) */
+} tn_status;
+
+typedef enum {
+    TN_FP64 = 0,      /* FP64 storage and arithmetic */
+    TN_FP32 = 1,      /* FP32 storage and arithmetic, FP64 reductions and ratios */
+    TN_BF16X3 = 2     /* FP32 storage; dense products on tcgen05 tensor cores with
+                         split-BF16 operands and FP32 accumulation */
+} tn_precision;
+
+typedef enum {
+    TN_SCHED_AUTO = 0,     /* minimum-bottleneck choice over all cuts (Sec. 4) */
+    TN_SCHED_ROW = 1,      /* row scheme, Fig. 2a */
+    TN_SCHED_COL = 2,      /* row scheme on the transposed lattice */
+    TN_SCHED_QUADRANT = 3  /* quadrant scheme, Fig. 2b, cut at (ceil(L/2), ceil(W/2)) */
+} tn_schedule;
+
+typedef enum {
+    TN_WORK_NORM = 0,      /* <Psi|Psi> only */
+    TN_WORK_ENERGY = 1     /* norm, every <X_k>, every <Z_i Z_j> */
+} tn_work;
+
+typedef enum {
+    TN_OP_NORM = 0,        /* <Psi|Psi> (returned as a ratio 1) */
+    TN_OP_X = 1,           /* <X_i>, Eq. mx */
+    TN_OP_ZZ = 2           /* <Z_i Z_j> for nearest neighbours i, j, Eq. cij first term */
+} tn_op;
+
+/* value = mant * 2^exp2 (the norm of a large lattice leaves the FP64 range). */
+typedef struct {
+    double mant;
+    int64_t exp2;
+} tn_scalar;
+
+typedef struct {
+    double energy;            /* E for the (J, h) of the call */
+    double energy_per_site;   /* E / (L W) */
+    tn_scalar norm;           /* <Psi|Psi> */
+    double *sx;               /* caller-owned, L*W entries, or NULL */
+    double *szsz;             /* caller-owned, nb entries, or NULL */
+    double err_bound_est;     /* a-priori relative rounding bound of the precision used */
+    int precision;            /* tn_precision used */
+    int schedule_o, schedule_i, schedule_j;   /* partition actually used (see tn_plan) */
+} tn_result;
+
+typedef struct tn_ctx tn_ctx;
+typedef struct tn_lattice tn_lattice;
+typedef struct tn_batch tn_batch;
+
+/* ----------------------------------------------------------- context ---- */
+
+/* Create a context on CUDA device `device` (or -1: planning only, no GPU).
+ * hbm_budget_bytes caps every device allocation the library makes (0 = 90% of
+ * the device's free memory).  cuda_stream (a cudaStream_t, or NULL for a
+ * stream the context creates) is where every kernel of this context runs. */
+tn_status tn_ctx_create(int device, size_t hbm_budget_bytes, void *cuda_stream, tn_ctx **out);
+tn_status tn_ctx_destroy(tn_ctx *ctx);
+/* Bytes of the budget currently held by lattices, batches and jobs. */
+tn_status tn_ctx_memory(const tn_ctx *ctx, size_t *used, size_t *budget);
+
+/* ----------------------------------------------------------- lattices --- */
+
+/* A lattice of L x W sites, bond D (1 <= L, W <= 16, 1 <= D <= 4).  Tensors
+ * start at zero.  Works on a planning-only context (no device memory). */
+tn_status tn_create_lattice(tn_ctx *ctx, int L, int W, int D, tn_lattice **out);
+tn_status tn_destroy_lattice(tn_lattice *lat);
+/* Number of FP64 entries the site tensors of (L, W, D) take (layout above). */
+size_t tn_lattice_elems(int L, int W, int D);
+/* Copy n_elems host doubles (must equal tn_lattice_elems) into the lattice. */
+tn_status tn_set_site_tensors(tn_lattice *lat, const double *host, size_t n_elems);
+/* Fill with i.i.d. uniform[-1,1) from `seed`: SplitMix64 (Steele, Lea & Flood
+ * 2014) as a counter-based generator, entry k (fill order above) is
+ * 2 * (mix64(seed + (k+1) * 0x9E3779B97F4A7C15) >> 11) * 2^-53 - 1. */
+tn_status tn_fill_random(tn_lattice *lat, uint64_t seed);
+/* Copy the lattice's FP64 tensors back to the host (n_elems entries). */
+tn_status tn_get_site_tensors(const tn_lattice *lat, double *host, size_t n_elems);
+
+/* ------------------------------------------------------------ planning -- */
+
+/* Exact device bytes the library allocates to run `work` on this lattice with
+ * this schedule and precision (the arena admission control checks). */
+tn_status tn_footprint(const tn_lattice *lat, tn_schedule sched, tn_precision prec,
+                       tn_work work, size_t *peak_bytes);
+/* The contraction schedule chosen by the heuristic of Sec. 4 as int64 words:
+ *   [0] = 1 (format), [1] = o, [2] = i, [3] = j, [4] = number of steps,
+ *   [5] = bottleneck entries, [6] = multiply-adds of one norm,
+ *   then 9 words per site-absorption step:
+ *   corner (0 TL, 1 TR, 2 BL, 3 BR), frame row k, frame column c,
+ *   lattice row r, lattice column c, P, K, N, S
+ * where the step maps the boundary [P, K, S] to [P, N, S].  o = 1 means the
+ * cut (i, j) is taken on the transposed lattice.  Writes at most cap words
+ * and the full length to *n. */
+tn_status tn_plan(const tn_lattice *lat, tn_schedule sched, int64_t *out, size_t cap, size_t *n);
+
+/* ---------------------------------------------------------- contraction -- */
+
+/* <Psi|Psi> (blocking). */
+tn_status tn_contract_norm(tn_lattice *lat, tn_precision prec, tn_schedule sched, tn_scalar *out);
+/* One expectation value (blocking): op = TN_OP_X with site i = r*W + c, or
+ * TN_OP_ZZ with nearest-neighbour sites i < j.  Returns the ratio to the norm. */
+tn_status tn_expectation(tn_lattice *lat, tn_precision prec, int op, int i, int j, double *out);
+/* Norm, every <X_k>, every <Z_i Z_j> and E for (J, h) (blocking, AUTO schedule). */
+tn_status tn_energy(tn_lattice *lat, double J, double h, tn_precision prec, tn_result *out);
+/* As tn_energy with an explicit schedule. */
+tn_status tn_energy_sched(tn_lattice *lat, double J, double h, tn_precision prec,
+                          tn_schedule sched, tn_result *out);
+
+/* ------------------------------------------------------------- batches --- */
+
+/* n independent lattices of possibly different (L, W, D), evaluated together:
+ * every wave of site absorptions and dense products of all members runs as one
+ * grouped launch; the launch sequence is captured once into a CUDA graph and
+ * replayed.  Device memory for all members is taken from the budget here. */
+tn_status tn_batch_create(tn_ctx *ctx, int n, const int *L, const int *W, const int *D,
+                          tn_precision prec, tn_schedule sched, tn_work work, tn_batch **out);
+tn_status tn_batch_destroy(tn_batch *b);
+/* Total FP64 entries of all members' tensors (members in order). */
+size_t tn_batch_elems(const tn_batch *b);
+/* Member tensors, concatenated in member order: from host memory, from device
+ * memory (a device pointer), or from the generator (member k uses seed
+ * mix64(batch_seed + (k+1) * 0x9E3779B97F4A7C15)).  Asynchronous on the ctx
+ * stream; the host buffer must stay valid until the next synchronising call. */
+tn_status tn_batch_set_tensors(tn_batch *b, const double *host, size_t n_elems);
+tn_status tn_batch_set_tensors_device(tn_batch *b, const double *dev, size_t n_elems);
+tn_status tn_batch_fill_random(tn_batch *b, uint64_t batch_seed);
+/* Run the whole batch (asynchronous on the ctx stream).  h holds one field per
+ * member; J is shared. */
+tn_status tn_batch_run(tn_batch *b, double J, const double *h);
+/* Per member: 4 + L*W + nb doubles [energy, log2 norm, norm mantissa, norm
+ * exponent, <X_k>..., <Z_i Z_j>...] (work = ENERGY) or 4 doubles (NORM),
+ * members concatenated.  _size gives the total; _host synchronises and copies;
+ * _device returns the device pointer of the same array (valid until the next
+ * run). */
+size_t tn_batch_result_size(const tn_batch *b);
+tn_status tn_batch_results_host(tn_batch *b, double *host, size_t cap);
+tn_status tn_batch_results_device(tn_batch *b, const double **dev);
+/* Number of kernel launches one tn_batch_run issues. */
+tn_status tn_batch_launch_count(const tn_batch *b, int64_t *n);
+
+/* ------------------------------------------------------------- serving --- */
+
+typedef struct {
+    int L, W, D;
+    tn_precision precision;
+    double J, h;
+    const double *tensors;   /* host, tn_lattice_elems(L,W,D) entries, copied at submit; or NULL */
+    uint64_t seed;           /* used when tensors == NULL (tn_fill_random's generator) */
+} tn_job;
+
+/* Queue a job.  It is admitted to the GPU when its exact footprint fits the
+ * budget left by running jobs; jobs that can never fit return
+ * TN_ERR_OVER_BUDGET here.  Admitted jobs run concurrently with earlier ones. */
+tn_status tn_submit(tn_ctx *ctx, const tn_job *job, uint64_t *ticket);
+/* TN_NOT_READY until the job is done; then fills *out (sx/szsz if non-NULL)
+ * and releases the ticket. */
+tn_status tn_poll(tn_ctx *ctx, uint64_t ticket, tn_result *out);
+/* As tn_poll but blocks up to timeout_s seconds (TN_ERR_TIMEOUT after). */
+tn_status tn_wait(tn_ctx *ctx, uint64_t ticket, double timeout_s, tn_result *out);
+
+/* -------------------------------------------------- kernel entry points -- */
+
+/* One site absorption on device buffers (the pairwise contraction of Sec. 4
+ * that dominates the paper's profile, Sec. 7):
+ *   out[p][n][s] = sum_k in[p][k][s] * E[k][n],  p < P, k < K, n < N, s < S,
+ * all arrays C order, dtype 0 = FP64, 1 = FP32.  Runs on `stream`; no
+ * rescaling.  Returns TN_ERR_INVALID for non-positive sizes or NULL pointers. */
+tn_status tn_absorb(int dtype, const void *in, const void *E, void *out,
+                    int64_t P, int32_t K, int32_t N, int64_t S, void *stream);
+
+/* ------------------------------------------------------------ misc -------- */
+
+const char *tn_status_string(tn_status s);
+/* Message of the last failing call on this host thread ("" if none). */
+const char *tn_last_error(void);
+/* Per kernel family since the last reset: launches, summed device time (ms,
+ * from CUDA events around each launch, only while profiling is on),
+ * algorithmic bytes and multiply-adds.  family: 0 absorb, 1 absorb-dot,
+ * 2 SIMT dense product, 3 tensor-core dense product, 4 other. */
+tn_status tn_ctx_set_profiling(tn_ctx *ctx, int on);
+tn_status tn_ctx_kernel_stats(tn_ctx *ctx, int family, int64_t *launches, double *ms,
+                              double *bytes, double *macs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TN_H */

@@ -1,0 +1,418 @@
+// extern "C" entry points of libtn (declared in include/tn.h).  Every function
+// catches exceptions and returns a tn_status; no exception crosses the ABI.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "runtime.h"
+
+using namespace tn;
+
+namespace tn {
+const char* last_error();
+}
+
+namespace {
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+// SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014).
+uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void fill_uniform(uint64_t seed, double* out, size_t n) {
+    for (size_t k = 0; k < n; ++k) {
+        const uint64_t z = mix64(seed + (uint64_t)(k + 1) * kGamma);
+        out[k] = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+    }
+}
+
+size_t lattice_elems(int L, int W, int D) {
+    size_t n = 0;
+    for (int r = 0; r < L; ++r)
+        for (int c = 0; c < W; ++c) {
+            const size_t u = r == 0 ? 1 : D, l = c == 0 ? 1 : D;
+            const size_t dn = r == L - 1 ? 1 : D, rt = c == W - 1 ? 1 : D;
+            n += 2 * u * l * dn * rt;
+        }
+    return n;
+}
+
+bool valid_dims(int L, int W, int D) { return L >= 1 && L <= 16 && W >= 1 && W <= 16 && D >= 1 && D <= 4; }
+
+double unit_roundoff(tn_precision p) {
+    switch (p) {
+        case TN_FP64: return 0x1.0p-53;
+        case TN_FP32: return 0x1.0p-24;
+        default: return 0x1.0p-16;
+    }
+}
+
+#define TN_GUARD_BEGIN try {
+#define TN_GUARD_END                                                    \
+    }                                                                   \
+    catch (const std::bad_alloc&) { set_error("host allocation failed"); return TN_ERR_OOM; } \
+    catch (const std::exception& e) { set_error(e.what()); return TN_ERR_INVALID; }            \
+    catch (...) { set_error("unknown error"); return TN_ERR_INVALID; }
+
+// Run one lattice through its cached one-member batch and read the results.
+tn_status run_single(tn_lattice* lat, tn_precision prec, tn_schedule sched, tn_work work, double J,
+                     double h, std::vector<double>* res, tn_batch** used) {
+    if (!lat->ctx || lat->ctx->device < 0) { set_error("context has no device"); return TN_ERR_NO_DEVICE; }
+    auto key = std::make_tuple((int)prec, (int)sched, (int)work);
+    tn_batch* b = nullptr;
+    auto it = lat->cache.find(key);
+    if (it != lat->cache.end()) {
+        b = it->second;
+    } else {
+        const int L = lat->L, W = lat->W, D = lat->D;
+        tn_status s = batch_create(lat->ctx, 1, &L, &W, &D, prec, sched, work, true, &b, nullptr);
+        if (s != TN_OK) return s;
+        lat->cache[key] = b;
+    }
+    cudaStream_t st = b->stream;
+    cudaError_t e = cudaMemcpyAsync(b->buf + b->lay.in_off, lat->host.data(), lat->host.size() * 8,
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e, "tensor upload");
+    b->h_final[0].J = J;
+    b->h_final[0].h = h;
+    tn_status s = batch_run(b, st);
+    if (s != TN_OK) return s;
+    res->resize((size_t)b->lay.nres);
+    e = cudaMemcpyAsync(res->data(), b->buf + b->lay.res_off, res->size() * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e, "result read");
+    if (used) *used = b;
+    return TN_OK;
+}
+
+tn_status fill_result(const std::vector<double>& r, const tn_batch* b, tn_precision prec, int L, int W,
+                      tn_result* out) {
+    const int N = L * W, nb = L * (W - 1) + W * (L - 1);
+    out->energy = r[0];
+    out->energy_per_site = r[0] / N;
+    out->norm.mant = r[2];
+    out->norm.exp2 = (int64_t)r[3];
+    if (out->sx) std::memcpy(out->sx, r.data() + 4, sizeof(double) * N);
+    if (out->szsz) std::memcpy(out->szsz, r.data() + 4 + N, sizeof(double) * nb);
+    const Plan& p = b->m[0].pg->plan;
+    out->err_bound_est = unit_roundoff(prec) * (double)(2 * N + 4);
+    out->precision = (int)prec;
+    out->schedule_o = p.o;
+    out->schedule_i = p.i;
+    out->schedule_j = p.j;
+    if (!std::isfinite(r[0]) || !(r[2] != 0.0)) { set_error("non-finite result or zero norm"); return TN_ERR_NUMERIC; }
+    return TN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tn_status_string(tn_status s) {
+    switch (s) {
+        case TN_OK: return "ok";
+        case TN_NOT_READY: return "not ready";
+        case TN_ERR_INVALID: return "invalid argument";
+        case TN_ERR_OVER_BUDGET: return "footprint exceeds the HBM budget";
+        case TN_ERR_OOM: return "out of memory";
+        case TN_ERR_CUDA: return "CUDA error";
+        case TN_ERR_TIMEOUT: return "timeout";
+        case TN_ERR_NUMERIC: return "non-finite result or zero norm";
+        case TN_ERR_NO_DEVICE: return "no device";
+    }
+    return "unknown status";
+}
+
+const char* tn_last_error(void) { return tn::last_error(); }
+
+tn_status tn_ctx_create(int device, size_t budget, void* stream, tn_ctx** out) {
+    TN_GUARD_BEGIN
+    if (!out) return TN_ERR_INVALID;
+    *out = nullptr;
+    auto ctx = std::make_unique<tn_ctx>();
+    ctx->device = device;
+    if (device >= 0) {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || device >= ndev) {
+            set_error("no such CUDA device");
+            return TN_ERR_NO_DEVICE;
+        }
+        cudaError_t e = cudaSetDevice(device);
+        if (e != cudaSuccess) return cuda_status(e, "cudaSetDevice");
+        size_t fr = 0, tot = 0;
+        e = cudaMemGetInfo(&fr, &tot);
+        if (e != cudaSuccess) return cuda_status(e, "cudaMemGetInfo");
+        ctx->budget = budget ? budget : (size_t)(0.9 * (double)fr);
+        if (stream) {
+            ctx->stream = static_cast<cudaStream_t>(stream);
+        } else {
+            e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_status(e, "stream create");
+            ctx->own_stream = true;
+        }
+    } else {
+        ctx->budget = budget;
+    }
+    *out = ctx.release();
+    return TN_OK;
+    TN_GUARD_END
+}
+
+tn_status tn_ctx_destroy(tn_ctx* ctx) {
+    if (!ctx) return TN_ERR_INVALID;
+    server_stop(ctx);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return TN_OK;
+}
+
+tn_status tn_ctx_memory(const tn_ctx* ctx, size_t* used, size_t* budget) {
+    if (!ctx) return TN_ERR_INVALID;
+    if (used) *used = ctx->used.load();
+    if (budget) *budget = ctx->budget;
+    return TN_OK;
+}
+
+size_t tn_lattice_elems(int L, int W, int D) { return valid_dims(L, W, D) ? lattice_elems(L, W, D) : 0; }
+
+tn_status tn_create_lattice(tn_ctx* ctx, int L, int W, int D, tn_lattice** out) {
+    TN_GUARD_BEGIN
+    if (!ctx || !out || !valid_dims(L, W, D)) { set_error("bad lattice arguments"); return TN_ERR_INVALID; }
+    auto lat = std::make_unique<tn_lattice>();
+    lat->ctx = ctx;
+    lat->L = L; lat->W = W; lat->D = D;
+    lat->host.assign(lattice_elems(L, W, D), 0.0);
+    *out = lat.release();
+    return TN_OK;
+    TN_GUARD_END
+}
+
+tn_status tn_destroy_lattice(tn_lattice* lat) {
+    if (!lat) return TN_ERR_INVALID;
+    for (auto& kv : lat->cache) batch_destroy(kv.second);
+    delete lat;
+    return TN_OK;
+}
+
+tn_status tn_set_site_tensors(tn_lattice* lat, const double* host, size_t n) {
+    if (!lat || !host || n != lat->host.size()) { set_error("tensor count mismatch"); return TN_ERR_INVALID; }
+    std::memcpy(lat->host.data(), host, n * sizeof(double));
+    return TN_OK;
+}
+
+tn_status tn_get_site_tensors(const tn_lattice* lat, double* host, size_t n) {
+    if (!lat || !host || n != lat->host.size()) return TN_ERR_INVALID;
+    std::memcpy(host, lat->host.data(), n * sizeof(double));
+    return TN_OK;
+}
+
+tn_status tn_fill_random(tn_lattice* lat, uint64_t seed) {
+    if (!lat) return TN_ERR_INVALID;
+    fill_uniform(seed, lat->host.data(), lat->host.size());
+    return TN_OK;
+}
+
+tn_status tn_footprint(const tn_lattice* lat, tn_schedule sched, tn_precision prec, tn_work work,
+                       size_t* bytes) {
+    TN_GUARD_BEGIN
+    if (!lat || !bytes) return TN_ERR_INVALID;
+    tn_batch* b = nullptr;
+    const int L = lat->L, W = lat->W, D = lat->D;
+    tn_status s = batch_create(lat->ctx, 1, &L, &W, &D, prec, sched, work, false, &b, bytes);
+    if (b) delete b;
+    return s;
+    TN_GUARD_END
+}
+
+tn_status tn_plan(const tn_lattice* lat, tn_schedule sched, int64_t* out, size_t cap, size_t* n) {
+    TN_GUARD_BEGIN
+    if (!lat || !n || sched < TN_SCHED_AUTO || sched > TN_SCHED_QUADRANT) return TN_ERR_INVALID;
+    const Plan p = plan_choose(lat->L, lat->W, lat->D, sched);
+    std::vector<int64_t> w = {1, p.o, p.i, p.j, 0, p.peak, p.mac};
+    int64_t nsteps = 0;
+    for (int q = 0; q < 4; ++q)
+        for (const Step& s : p.corner[q].steps) {
+            w.insert(w.end(), {(int64_t)s.corner, s.k, s.c, s.r, s.col, s.P, s.K, s.N, s.S});
+            ++nsteps;
+        }
+    w[4] = nsteps;
+    *n = w.size();
+    if (out) std::memcpy(out, w.data(), sizeof(int64_t) * std::min(cap, w.size()));
+    return TN_OK;
+    TN_GUARD_END
+}
+
+tn_status tn_contract_norm(tn_lattice* lat, tn_precision prec, tn_schedule sched, tn_scalar* out) {
+    TN_GUARD_BEGIN
+    if (!lat || !out) return TN_ERR_INVALID;
+    std::vector<double> r;
+    tn_status s = run_single(lat, prec, sched, TN_WORK_NORM, 1.0, 0.0, &r, nullptr);
+    if (s != TN_OK) return s;
+    out->mant = r[2];
+    out->exp2 = (int64_t)r[3];
+    if (!(r[2] != 0.0) || !std::isfinite(r[2])) { set_error("zero or non-finite norm"); return TN_ERR_NUMERIC; }
+    return TN_OK;
+    TN_GUARD_END
+}
+
+tn_status tn_energy_sched(tn_lattice* lat, double J, double h, tn_precision prec, tn_schedule sched,
+                          tn_result* out) {
+    TN_GUARD_BEGIN
+    if (!lat || !out) return TN_ERR_INVALID;
+    std::vector<double> r;
+    tn_batch* b = nullptr;
+    tn_status s = run_single(lat, prec, sched, TN_WORK_ENERGY, J, h, &r, &b);
+    if (s != TN_OK) return s;
+    return fill_result(r, b, prec, lat->L, lat->W, out);
+    TN_GUARD_END
+}
+
+tn_status tn_energy(tn_lattice* lat, double J, double h, tn_precision prec, tn_result* out) {
+    return tn_energy_sched(lat, J, h, prec, TN_SCHED_AUTO, out);
+}
+
+tn_status tn_expectation(tn_lattice* lat, tn_precision prec, int op, int i, int j, double* out) {
+    TN_GUARD_BEGIN
+    if (!lat || !out) return TN_ERR_INVALID;
+    const int L = lat->L, W = lat->W, N = L * W;
+    if (op == TN_OP_NORM) { *out = 1.0; return TN_OK; }
+    if (op == TN_OP_X) {
+        if (i < 0 || i >= N) return TN_ERR_INVALID;
+    } else if (op == TN_OP_ZZ) {
+        if (i < 0 || j < 0 || i >= N || j >= N) return TN_ERR_INVALID;
+        if (i > j) std::swap(i, j);
+        const bool h = (j == i + 1) && (i / W == j / W), v = (j == i + W);
+        if (!h && !v) { set_error("sites are not nearest neighbours"); return TN_ERR_INVALID; }
+    } else {
+        return TN_ERR_INVALID;
+    }
+    std::vector<double> r;
+    tn_status s = run_single(lat, prec, TN_SCHED_AUTO, TN_WORK_ENERGY, 1.0, 0.0, &r, nullptr);
+    if (s != TN_OK) return s;
+    if (op == TN_OP_X) { *out = r[4 + i]; return TN_OK; }
+    const int ri = i / W, ci = i % W;
+    int bi;
+    if (j == i + 1 && ri == j / W) bi = ri * (W - 1) + ci;
+    else bi = L * (W - 1) + ri * W + ci;
+    *out = r[4 + N + bi];
+    return TN_OK;
+    TN_GUARD_END
+}
+
+// ------------------------------------------------------------- batches --
+
+tn_status tn_batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int* D, tn_precision prec,
+                          tn_schedule sched, tn_work work, tn_batch** out) {
+    TN_GUARD_BEGIN
+    if (!ctx || !out) return TN_ERR_INVALID;
+    *out = nullptr;
+    return batch_create(ctx, n, L, W, D, prec, sched, work, true, out, nullptr);
+    TN_GUARD_END
+}
+
+tn_status tn_batch_destroy(tn_batch* b) {
+    if (!b) return TN_ERR_INVALID;
+    batch_destroy(b);
+    return TN_OK;
+}
+
+size_t tn_batch_elems(const tn_batch* b) { return b ? (size_t)b->lay.nin : 0; }
+size_t tn_batch_result_size(const tn_batch* b) { return b ? (size_t)b->lay.nres : 0; }
+
+tn_status tn_batch_set_tensors(tn_batch* b, const double* host, size_t n) {
+    if (!b || !host || n != (size_t)b->lay.nin) { set_error("tensor count mismatch"); return TN_ERR_INVALID; }
+    return cuda_status(cudaMemcpyAsync(b->buf + b->lay.in_off, host, n * 8, cudaMemcpyHostToDevice, b->stream),
+                       "tensor upload");
+}
+
+tn_status tn_batch_set_tensors_device(tn_batch* b, const double* dev, size_t n) {
+    if (!b || !dev || n != (size_t)b->lay.nin) { set_error("tensor count mismatch"); return TN_ERR_INVALID; }
+    return cuda_status(cudaMemcpyAsync(b->buf + b->lay.in_off, dev, n * 8, cudaMemcpyDeviceToDevice, b->stream),
+                       "tensor copy");
+}
+
+tn_status tn_batch_fill_random(tn_batch* b, uint64_t batch_seed) {
+    TN_GUARD_BEGIN
+    if (!b) return TN_ERR_INVALID;
+    std::vector<double> h((size_t)b->lay.nin);
+    for (size_t k = 0; k < b->m.size(); ++k) {
+        const uint64_t seed = mix64(batch_seed + (uint64_t)(k + 1) * kGamma);
+        fill_uniform(seed, h.data() + b->m[k].in_off, (size_t)b->m[k].in_elems);
+    }
+    cudaError_t e = cudaMemcpyAsync(b->buf + b->lay.in_off, h.data(), h.size() * 8, cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return cuda_status(e, "tensor upload");
+    TN_GUARD_END
+}
+
+tn_status tn_batch_run(tn_batch* b, double J, const double* h) {
+    TN_GUARD_BEGIN
+    if (!b || !h) return TN_ERR_INVALID;
+    for (size_t k = 0; k < b->m.size(); ++k) {
+        b->h_final[k].J = J;
+        b->h_final[k].h = h[k];
+    }
+    return batch_run(b, b->stream);
+    TN_GUARD_END
+}
+
+tn_status tn_batch_results_host(tn_batch* b, double* host, size_t cap) {
+    if (!b || !host || cap < (size_t)b->lay.nres) return TN_ERR_INVALID;
+    cudaError_t e = cudaMemcpyAsync(host, b->buf + b->lay.res_off, (size_t)b->lay.nres * 8, cudaMemcpyDeviceToHost,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return cuda_status(e, "result read");
+}
+
+tn_status tn_batch_results_device(tn_batch* b, const double** dev) {
+    if (!b || !dev) return TN_ERR_INVALID;
+    *dev = reinterpret_cast<const double*>(b->buf + b->lay.res_off);
+    return TN_OK;
+}
+
+tn_status tn_batch_launch_count(const tn_batch* b, int64_t* n) {
+    if (!b || !n) return TN_ERR_INVALID;
+    *n = (int64_t)b->launches.size() + 2;   // + init + final
+    return TN_OK;
+}
+
+// ---------------------------------------------------------- kernel entry --
+
+tn_status tn_absorb(int dtype, const void* in, const void* E, void* out, int64_t P, int32_t K, int32_t N,
+                    int64_t S, void* stream) {
+    if ((dtype != 0 && dtype != 1) || !in || !E || !out || P <= 0 || K <= 0 || N <= 0 || S <= 0) {
+        set_error("bad absorb arguments");
+        return TN_ERR_INVALID;
+    }
+    if (!absorb_has_fast_path(K, N)) { set_error("K, N must be in {1, 4, 16} or {1, 9, 81}"); return TN_ERR_INVALID; }
+    return cuda_status(launch_absorb_plain(dtype, in, E, out, P, K, N, S, static_cast<cudaStream_t>(stream)),
+                       "absorb launch");
+}
+
+// ---------------------------------------------------------------- misc --
+
+tn_status tn_ctx_set_profiling(tn_ctx* ctx, int on) {
+    if (!ctx) return TN_ERR_INVALID;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->profiling = on != 0;
+    if (on) for (auto& s : ctx->stats) s = KStat();
+    return TN_OK;
+}
+
+tn_status tn_ctx_kernel_stats(tn_ctx* ctx, int family, int64_t* launches, double* ms, double* bytes, double* macs) {
+    if (!ctx || family < 0 || family > 4) return TN_ERR_INVALID;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    const KStat& s = ctx->stats[family];
+    if (launches) *launches = s.launches;
+    if (ms) *ms = s.ms;
+    if (bytes) *bytes = s.bytes;
+    if (macs) *macs = s.macs;
+    return TN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,609 @@
+// CUDA kernels of libtn (sm_103a): site absorption (Sec. 4's pairwise
+// contraction of one site into the boundary, the paper's `contract tVtl par`,
+// Sec. 7), dense ring products, dot products, site-matrix construction and the
+// final FP64 ratios.
+//
+// Every kernel takes a list of independent tasks; block b serves the task whose
+// [tile0, tile0 + ntiles) holds b.  Rescaling: a consumer multiplies each loaded
+// entry by 2^-e (e from the producer's recorded max), which is exact, and the
+// producer records max|out| with an atomicMax in its epilogue, so no extra pass
+// over any tensor is needed.  Dot products accumulate per tile in FP64 and the
+// last tile of a task sums the tile partials in index order, so a result does
+// not depend on which other tasks share the launch.
+#include <cfloat>
+#include <cstdint>
+
+#include "tn_kernels.h"
+
+namespace tn {
+
+namespace {
+
+__device__ __forceinline__ int slot_shift(const Slot* s) {
+    const double m = __longlong_as_double((long long)s->maxbits);
+    if (!(m > 0.0)) return 0;
+    int e;
+    frexp(m, &e);
+    return e;
+}
+
+template <typename T> __device__ __forceinline__ T pow2(int e);
+template <> __device__ __forceinline__ double pow2<double>(int e) { return ldexp(1.0, e); }
+template <> __device__ __forceinline__ float pow2<float>(int e) {
+    e = e < -125 ? -125 : (e > 125 ? 125 : e);
+    return __int_as_float((127 + e) << 23);
+}
+
+template <typename Task>
+__device__ __forceinline__ int find_task(const Task* __restrict__ tasks, int ntasks, long long tile) {
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide reductions for blockDim.x == 256; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += red[k];
+    return r;
+}
+__device__ __forceinline__ double block_max(double v, double* red) {
+    v = warp_max(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r = fmax(r, red[k]);
+    return r;
+}
+
+__device__ __forceinline__ void record_max(Slot* s, double m) {
+    atomicMax(&s->maxbits, (unsigned long long)__double_as_longlong(m));
+}
+
+// Deterministic completion of a per-tile FP64 sum: every tile writes its
+// partial; the last tile to arrive sums all partials in index order.
+__device__ void finish_sum(double part, double* partial, int ntiles, long long local,
+                           Slot* out, long long X, double* red) {
+    __shared__ int is_last;
+    if (threadIdx.x == 0) {
+        partial[local] = part;
+        __threadfence();
+        const unsigned prev = atomicAdd(&out->count, 1u);
+        is_last = (prev == (unsigned)(ntiles - 1));
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < ntiles; k += blockDim.x) acc += __ldcg(partial + k);
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        out->mant = acc;
+        out->X = X;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ absorption --
+
+// One tile (kAbsorbThreads outer positions (p, s)) of a site absorption.
+// MODE 0: plain (no slots, tn_absorb); 1: absorb with rescale; 2: absorb-dot.
+template <typename T, int K, int N, int MODE>
+__device__ __forceinline__ void absorb_tile(const AbsorbTask& t, long long local,
+                                            Slot* __restrict__ slots, T* Es, double* red) {
+    const T* E = static_cast<const T*>(t.E);
+    for (int idx = threadIdx.x; idx < K * N; idx += blockDim.x) {
+        const int k = idx / N, n = idx - k * N;
+        Es[idx] = t.transE ? E[n * K + k] : E[idx];
+    }
+    int e_in = 0, e_adj = 0;
+    T sc_in = T(1), sc_adj = T(1);
+    if (MODE >= 1) {
+        e_in = slot_shift(&slots[t.slot_in]);
+        sc_in = pow2<T>(-e_in);
+    }
+    if (MODE == 2) {
+        e_adj = slot_shift(&slots[t.slot_adj]);
+        sc_adj = pow2<T>(-e_adj);
+    }
+    __syncthreads();
+    const long long S = t.S;
+    const long long o = local * kAbsorbThreads + threadIdx.x;
+    double lmax = 0.0, ldot = 0.0;
+    if (o < t.P * S) {
+        const long long p = o / S, s = o - p * S;
+        const T* in = static_cast<const T*>(t.in) + p * K * S + s;
+        T y[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) y[n] = T(0);
+#pragma unroll 3
+        for (int k = 0; k < K; ++k) {
+            const T x = in[k * S] * sc_in;
+#pragma unroll
+            for (int n = 0; n < N; ++n) y[n] = fma(x, Es[k * N + n], y[n]);
+        }
+        if (MODE < 2) {
+            T* out = static_cast<T*>(t.out) + p * N * S + s;
+            T m = T(0);
+#pragma unroll
+            for (int n = 0; n < N; ++n) {
+                out[n * S] = y[n];
+                m = fmax(m, fabs(y[n]));
+            }
+            lmax = (double)m;
+        } else {
+            const T* adj = static_cast<const T*>(t.adj) + p * N * S + s;
+            T acc = T(0);
+#pragma unroll
+            for (int n = 0; n < N; ++n) acc = fma(y[n], adj[n * S] * sc_adj, acc);
+            ldot = (double)acc;
+        }
+    }
+    if (MODE == 1) {
+        const double m = block_max(lmax, red);
+        if (threadIdx.x == 0) {
+            record_max(&slots[t.slot_out], m);
+            if (local == 0) slots[t.slot_out].X = slots[t.slot_in].X + e_in + slots[t.slot_E].X;
+        }
+    } else if (MODE == 2) {
+        const double part = block_sum(ldot, red);
+        const long long X = slots[t.slot_in].X + e_in + slots[t.slot_E].X + slots[t.slot_adj].X + e_adj;
+        finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_out], X, red);
+    }
+}
+
+template <typename T, int K, int N, int MODE>
+__global__ void __launch_bounds__(kAbsorbThreads)
+k_absorb(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    const long long tile = blockIdx.x;
+    const AbsorbTask& t = tasks[find_task(tasks, ntasks, tile)];
+    absorb_tile<T, K, N, MODE>(t, tile - t.tile0, slots, reinterpret_cast<T*>(smem_raw), red);
+}
+
+// Single task passed by value (the plain kernel entry point allocates nothing).
+template <typename T, int K, int N>
+__global__ void __launch_bounds__(kAbsorbThreads)
+k_absorb_one(const __grid_constant__ AbsorbTask t) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    absorb_tile<T, K, N, 0>(t, (long long)blockIdx.x, nullptr, reinterpret_cast<T*>(smem_raw), red);
+}
+
+// Generic sizes (D = 4 and anything outside the unrolled set): E read from
+// global memory, one output leg at a time.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kAbsorbThreads)
+k_absorb_generic(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+    __shared__ double red[32];
+    const long long tile = blockIdx.x;
+    const AbsorbTask& t = tasks[find_task(tasks, ntasks, tile)];
+    const int K = t.K, N = t.N;
+    const T* E = static_cast<const T*>(t.E);
+    int e_in = 0, e_adj = 0;
+    T sc_in = T(1), sc_adj = T(1);
+    if (MODE >= 1) { e_in = slot_shift(&slots[t.slot_in]); sc_in = pow2<T>(-e_in); }
+    if (MODE == 2) { e_adj = slot_shift(&slots[t.slot_adj]); sc_adj = pow2<T>(-e_adj); }
+    const long long local = tile - t.tile0;
+    const long long S = t.S;
+    const long long o = local * kAbsorbThreads + threadIdx.x;
+    double lmax = 0.0, ldot = 0.0;
+    if (o < t.P * S) {
+        const long long p = o / S, s = o - p * S;
+        const T* in = static_cast<const T*>(t.in) + p * K * S + s;
+        for (int n = 0; n < N; ++n) {
+            T y = T(0);
+            for (int k = 0; k < K; ++k) {
+                const T e = t.transE ? E[(long long)n * K + k] : E[(long long)k * N + n];
+                y = fma(in[k * S] * sc_in, e, y);
+            }
+            if (MODE < 2) {
+                static_cast<T*>(t.out)[(p * N + n) * S + s] = y;
+                lmax = fmax(lmax, (double)fabs(y));
+            } else {
+                ldot += (double)(y * static_cast<const T*>(t.adj)[(p * N + n) * S + s] * sc_adj);
+            }
+        }
+    }
+    if (MODE == 1) {
+        const double m = block_max(lmax, red);
+        if (threadIdx.x == 0) {
+            record_max(&slots[t.slot_out], m);
+            if (local == 0) slots[t.slot_out].X = slots[t.slot_in].X + e_in + slots[t.slot_E].X;
+        }
+    } else if (MODE == 2) {
+        const double part = block_sum(ldot, red);
+        const long long X = slots[t.slot_in].X + e_in + slots[t.slot_E].X + slots[t.slot_adj].X + e_adj;
+        finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_out], X, red);
+    }
+}
+
+long long absorb_tiles(long long P, long long S, int K, int N) {
+    (void)K; (void)N;
+    return (P * S + kAbsorbThreads - 1) / kAbsorbThreads;
+}
+
+namespace {
+
+bool kn_fast(int K, int N) {
+    auto ok = [](int x) { return x == 1 || x == 4 || x == 16 || x == 9 || x == 81; };
+    if (!ok(K) || !ok(N)) return false;
+    // both from the same bond family (D = 2: 1,4,16; D = 3: 1,9,81)
+    const bool two = (K == 4 || K == 16 || N == 4 || N == 16);
+    const bool three = (K == 9 || K == 81 || N == 9 || N == 81);
+    return !(two && three);
+}
+
+template <typename T, int MODE>
+cudaError_t absorb_dispatch(int K, int N, const AbsorbTask* tasks, int ntasks, long long nblocks,
+                            Slot* slots, cudaStream_t st) {
+    const size_t smem = (size_t)K * N * sizeof(T);
+#define TN_ABSORB_CASE(KK, NN)                                                              \
+    if (K == KK && N == NN) {                                                               \
+        auto fn = k_absorb<T, KK, NN, MODE>;                                                \
+        if (smem > 48 * 1024)                                                               \
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        fn<<<(unsigned)nblocks, kAbsorbThreads, smem, st>>>(tasks, ntasks, slots);          \
+        return cudaGetLastError();                                                          \
+    }
+    TN_ABSORB_CASE(1, 1)
+    TN_ABSORB_CASE(1, 4) TN_ABSORB_CASE(4, 1) TN_ABSORB_CASE(4, 4)
+    TN_ABSORB_CASE(1, 16) TN_ABSORB_CASE(16, 1) TN_ABSORB_CASE(4, 16) TN_ABSORB_CASE(16, 4)
+    TN_ABSORB_CASE(16, 16)
+    TN_ABSORB_CASE(1, 9) TN_ABSORB_CASE(9, 1) TN_ABSORB_CASE(9, 9)
+    TN_ABSORB_CASE(1, 81) TN_ABSORB_CASE(81, 1) TN_ABSORB_CASE(9, 81) TN_ABSORB_CASE(81, 9)
+    TN_ABSORB_CASE(81, 81)
+#undef TN_ABSORB_CASE
+    k_absorb_generic<T, MODE><<<(unsigned)nblocks, kAbsorbThreads, 0, st>>>(tasks, ntasks, slots);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool absorb_has_fast_path(int K, int N) { return kn_fast(K, N); }
+
+cudaError_t launch_absorb(int dt, bool dot, int K, int N, const AbsorbTask* tasks, int ntasks,
+                          long long nblocks, Slot* slots, cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (dt == 0)
+        return dot ? absorb_dispatch<double, 2>(K, N, tasks, ntasks, nblocks, slots, st)
+                   : absorb_dispatch<double, 1>(K, N, tasks, ntasks, nblocks, slots, st);
+    return dot ? absorb_dispatch<float, 2>(K, N, tasks, ntasks, nblocks, slots, st)
+               : absorb_dispatch<float, 1>(K, N, tasks, ntasks, nblocks, slots, st);
+}
+
+// ------------------------------------------------------ dense products ---
+
+// C = A B with 64 x 64 output tiles, 16-deep k slices staged in shared memory,
+// a 4 x 4 register tile per thread.  Operands are read through arbitrary
+// strides (row- or column-major views of the ring tensors) and rescaled on load.
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(256)
+k_gemm(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+    constexpr int BM = kGemmTile, BN = kGemmTile, BK = 16;
+    __shared__ T As[BK][BM + 4];
+    __shared__ T Bs[BK][BN + 4];
+    __shared__ double red[32];
+    const long long tile = blockIdx.x;
+    const GemmTask& t = tasks[find_task(tasks, ntasks, tile)];
+    const long long local = tile - t.tile0;
+    const long long m0 = (local / t.tiles_n) * BM, n0 = (local % t.tiles_n) * BN;
+    const int eA = slot_shift(&slots[t.slot_A]), eB = slot_shift(&slots[t.slot_B]);
+    const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
+    const T* A = static_cast<const T*>(t.A);
+    const T* B = static_cast<const T*>(t.B);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    const bool a_kfast = (t.sak == 1);
+    const bool b_nfast = (t.sbn == 1);
+    for (long long k0 = 0; k0 < t.K; k0 += BK) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = threadIdx.x + r * 256;
+            int mm, kk;
+            if (a_kfast) { kk = idx & (BK - 1); mm = idx >> 4; }
+            else { mm = idx & (BM - 1); kk = idx >> 6; }
+            const long long gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < t.M && gk < t.K) ? A[gm * t.sam + gk * t.sak] * sA : T(0);
+            int nn2, kk2;
+            if (b_nfast) { nn2 = idx & (BN - 1); kk2 = idx >> 6; }
+            else { kk2 = idx & (BK - 1); nn2 = idx >> 4; }
+            const long long gn = n0 + nn2, gk2 = k0 + kk2;
+            Bs[kk2][nn2] = (gn < t.N && gk2 < t.K) ? B[gk2 * t.sbk + gn * t.sbn] * sB : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    if (!DOT) {
+        T* C = static_cast<T*>(t.C);
+        double m = 0.0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const long long gm = m0 + ty * 4 + i;
+            if (gm >= t.M) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const long long gn = n0 + tx * 4 + j;
+                if (gn < t.N) {
+                    C[gm * t.N + gn] = acc[i][j];
+                    m = fmax(m, (double)fabs(acc[i][j]));
+                }
+            }
+        }
+        m = block_max(m, red);
+        if (threadIdx.x == 0) {
+            record_max(&slots[t.slot_C], m);
+            if (local == 0) slots[t.slot_C].X = slots[t.slot_A].X + eA + slots[t.slot_B].X + eB;
+        }
+    } else {
+        const int eD = slot_shift(&slots[t.slot_D]);
+        const T sD = pow2<T>(-eD);
+        const T* Dm = static_cast<const T*>(t.Dm);
+        T s = T(0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const long long gm = m0 + ty * 4 + i;
+            if (gm >= t.M) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const long long gn = n0 + tx * 4 + j;
+                if (gn < t.N) s = fma(acc[i][j], Dm[gm * t.N + gn] * sD, s);
+            }
+        }
+        const double part = block_sum((double)s, red);
+        const long long X = slots[t.slot_A].X + eA + slots[t.slot_B].X + eB + slots[t.slot_D].X + eD;
+        finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_C], X, red);
+    }
+}
+
+cudaError_t launch_gemm(int dt, bool dot, const GemmTask* tasks, int ntasks, long long nblocks,
+                        Slot* slots, cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (dt == 0) {
+        if (dot) k_gemm<double, true><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+        else k_gemm<double, false><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+    } else {
+        if (dot) k_gemm<float, true><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+        else k_gemm<float, false><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ dot -------
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_dot(const DotTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+    __shared__ double red[32];
+    const long long tile = blockIdx.x;
+    const DotTask& t = tasks[find_task(tasks, ntasks, tile)];
+    const long long local = tile - t.tile0;
+    const int eA = slot_shift(&slots[t.slot_A]), eB = slot_shift(&slots[t.slot_B]);
+    const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
+    const T* A = static_cast<const T*>(t.A);
+    const T* B = static_cast<const T*>(t.B);
+    const long long base = local * kDotPerBlock;
+    T s = T(0);
+    for (int k = threadIdx.x; k < kDotPerBlock; k += 256) {
+        const long long g = base + k;
+        if (g < t.n) s = fma(A[g] * sA, B[g] * sB, s);
+    }
+    const double part = block_sum((double)s, red);
+    const long long X = slots[t.slot_A].X + eA + slots[t.slot_B].X + eB;
+    finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_out], X, red);
+}
+
+cudaError_t launch_dot(int dt, const DotTask* tasks, int ntasks, long long nblocks, Slot* slots,
+                       cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (dt == 0) k_dot<double><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+    else k_dot<float><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ site matrices ----
+
+// E_O[(h_a h_b)(u_a u_b)][(dn_a dn_b)(rt_a rt_b)] =
+//   sum_{p,q} A[p](legs a) O[p][q] A[q](legs b) * 2^(-2 e_A)
+// in the corner's frame (h = frame l leg, h' = frame rt leg), where e_A is the
+// frexp exponent of max|A| (so the matrix is O(1) and its slot carries 2 e_A).
+// The two copies are the bra and ket layers of Sec. 5 (real amplitudes, no
+// conjugation); O is I, X or Z = diag(-1, +1).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_sitemat(const SiteMatTask* __restrict__ tasks, Slot* __restrict__ slots) {
+    __shared__ double red[32];
+    const SiteMatTask& t = tasks[blockIdx.x];
+    const int* dm = t.dims;
+    const int nA = 2 * dm[0] * dm[1] * dm[2] * dm[3];
+    double mx = 0.0;
+    for (int k = threadIdx.x; k < nA; k += blockDim.x) mx = fmax(mx, fabs(t.A[k]));
+    mx = block_max(mx, red);
+    __shared__ int eA;
+    if (threadIdx.x == 0) {
+        int e = 0;
+        if (mx > 0.0) frexp(mx, &e);
+        eA = e;
+        slots[t.slot_E].X = 2 * e;
+    }
+    __syncthreads();
+    const double sc = ldexp(1.0, -2 * eA);
+    const int fu = dm[t.map[0]], fl = dm[t.map[1]], fd = dm[t.map[2]], fr = dm[t.map[3]];
+    double o00, o01, o10, o11;
+    if (t.phys == 1) { o00 = 0; o01 = 1; o10 = 1; o11 = 0; }
+    else if (t.phys == 2) { o00 = -1; o01 = 0; o10 = 0; o11 = 1; }
+    else { o00 = 1; o01 = 0; o10 = 0; o11 = 1; }
+    T* E = static_cast<T*>(t.E);
+    const int K = t.K, N = t.N;
+    // shapes are checked on the host; never read outside A if they disagree
+    const bool shape_ok = (K == fl * fl * fu * fu) && (N == fd * fd * fr * fr);
+    const long long stride_p = (long long)dm[0] * dm[1] * dm[2] * dm[3];
+    for (int idx = threadIdx.x; idx < K * N; idx += blockDim.x) {
+        const int k = idx / N, n = idx - k * N;
+        const int uu = k % (fu * fu), hh = k / (fu * fu);
+        const int rr = n % (fr * fr), dd = n / (fr * fr);
+        const int ua = uu / fu, ub = uu % fu, la = hh / fl, lb = hh % fl;
+        const int da = dd / fd, db = dd % fd, ra = rr / fr, rb = rr % fr;
+        int va[4], vb[4];
+        va[t.map[0]] = ua; va[t.map[1]] = la; va[t.map[2]] = da; va[t.map[3]] = ra;
+        vb[t.map[0]] = ub; vb[t.map[1]] = lb; vb[t.map[2]] = db; vb[t.map[3]] = rb;
+        if (!shape_ok) { E[idx] = T(0); continue; }
+        const long long ia = ((long long)(va[0] * dm[1] + va[1]) * dm[2] + va[2]) * dm[3] + va[3];
+        const long long ib = ((long long)(vb[0] * dm[1] + vb[1]) * dm[2] + vb[2]) * dm[3] + vb[3];
+        const double a0 = t.A[ia], a1 = t.A[stride_p + ia];
+        const double b0 = t.A[ib], b1 = t.A[stride_p + ib];
+        const double v = a0 * (o00 * b0 + o01 * b1) + a1 * (o10 * b0 + o11 * b1);
+        E[idx] = shape_ok ? (T)(v * sc) : T(0);
+    }
+}
+
+cudaError_t launch_sitemat(int dt, const SiteMatTask* tasks, int ntasks, Slot* slots,
+                           cudaStream_t st) {
+    if (ntasks <= 0) return cudaSuccess;
+    if (dt == 0) k_sitemat<double><<<ntasks, 256, 0, st>>>(tasks, slots);
+    else k_sitemat<float><<<ntasks, 256, 0, st>>>(tasks, slots);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- init ------
+
+__global__ void k_init(Slot* slots, long long nslots, const ConstOne* ones, int nones, int dt) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = i; k < nslots; k += stride) {
+        Slot z;
+        z.X = 0; z.maxbits = 0; z.mant = 0.0; z.count = 0; z.pad = 0;
+        slots[k] = z;
+    }
+    for (long long k = i; k < nones; k += stride) {
+        if (dt == 0) *static_cast<double*>(ones[k].ptr) = 1.0;
+        else *static_cast<float*>(ones[k].ptr) = 1.0f;
+    }
+}
+
+cudaError_t launch_init(Slot* slots, long long nslots, const ConstOne* ones, int nones, int dt,
+                        cudaStream_t st) {
+    long long need = nslots > nones ? nslots : nones;
+    long long blocks = (need + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 4096) blocks = 4096;
+    k_init<<<(unsigned)blocks, 256, 0, st>>>(slots, nslots, ones, nones, dt);
+    return cudaGetLastError();
+}
+
+// const-one tensors also carry max = 1 so consumers see a normalised value
+// ------------------------------------------------------------ final ------
+
+// <O> = (m_O / m_norm) 2^(X_O - X_norm) in FP64; E = -J sum <zz> - h sum <x>.
+__global__ void k_final(const FinalTask* __restrict__ tasks, const Slot* __restrict__ slots) {
+    const FinalTask& t = tasks[blockIdx.x];
+    const Slot& nz = slots[t.norm_slot];
+    const double mn = nz.mant;
+    const long long Xn = nz.X;
+    double sxx = 0.0, szz = 0.0;
+    for (int k = threadIdx.x; k < t.n_sites; k += blockDim.x) {
+        const Slot& s = slots[t.sx_slots[k]];
+        t.out[4 + k] = ldexp(s.mant / mn, (int)(s.X - Xn));
+    }
+    for (int k = threadIdx.x; k < t.n_bonds; k += blockDim.x) {
+        const Slot& s = slots[t.zz_slots[k]];
+        t.out[4 + t.n_sites + k] = ldexp(s.mant / mn, (int)(s.X - Xn));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < t.n_sites; ++k) sxx += t.out[4 + k];
+        for (int k = 0; k < t.n_bonds; ++k) szz += t.out[4 + t.n_sites + k];
+        t.out[0] = -t.J * szz - t.h * sxx;
+        t.out[1] = log2(fabs(mn)) + (double)Xn;
+        t.out[2] = mn;
+        t.out[3] = (double)Xn;
+    }
+}
+
+cudaError_t launch_final(const FinalTask* tasks, int ntasks, const Slot* slots, cudaStream_t st) {
+    if (ntasks <= 0) return cudaSuccess;
+    k_final<<<ntasks, 128, 0, st>>>(tasks, slots);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------- plain absorption ---
+
+namespace {
+template <typename T>
+cudaError_t absorb_plain(const AbsorbTask& t, long long nblocks, cudaStream_t st) {
+    const int K = t.K, N = t.N;
+    const size_t smem = (size_t)K * N * sizeof(T);
+#define TN_PLAIN_CASE(KK, NN)                                                               \
+    if (K == KK && N == NN) {                                                               \
+        auto fn = k_absorb_one<T, KK, NN>;                                                  \
+        if (smem > 48 * 1024)                                                               \
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        fn<<<(unsigned)nblocks, kAbsorbThreads, smem, st>>>(t);                             \
+        return cudaGetLastError();                                                          \
+    }
+    TN_PLAIN_CASE(1, 1)
+    TN_PLAIN_CASE(1, 4) TN_PLAIN_CASE(4, 1) TN_PLAIN_CASE(4, 4)
+    TN_PLAIN_CASE(1, 16) TN_PLAIN_CASE(16, 1) TN_PLAIN_CASE(4, 16) TN_PLAIN_CASE(16, 4)
+    TN_PLAIN_CASE(16, 16)
+    TN_PLAIN_CASE(1, 9) TN_PLAIN_CASE(9, 1) TN_PLAIN_CASE(9, 9)
+    TN_PLAIN_CASE(1, 81) TN_PLAIN_CASE(81, 1) TN_PLAIN_CASE(9, 81) TN_PLAIN_CASE(81, 9)
+    TN_PLAIN_CASE(81, 81)
+#undef TN_PLAIN_CASE
+    return cudaErrorNotSupported;
+}
+}  // namespace
+
+cudaError_t launch_absorb_plain(int dt, const void* in, const void* E, void* out, long long P,
+                                int K, int N, long long S, cudaStream_t st) {
+    AbsorbTask t{};
+    t.in = in; t.E = E; t.out = out;
+    t.P = P; t.S = S; t.K = K; t.N = N;
+    t.tile0 = 0;
+    const long long nb = absorb_tiles(P, S, K, N);
+    t.ntiles = (int)nb;
+    if (nb <= 0) return cudaSuccess;
+    return dt == 0 ? absorb_plain<double>(t, nb, st) : absorb_plain<float>(t, nb, st);
+}
+
+}  // namespace tn

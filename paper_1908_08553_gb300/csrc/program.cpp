@@ -1,0 +1,368 @@
+// Program builder: turns a plan (planner.cpp) into the list of pairwise
+// contractions that yield the norm and, for TN_WORK_ENERGY, every <X_k> and
+// every nearest-neighbour <Z_i Z_j> (Sec. 5: "the network must be similarly
+// fully contracted for every site and pair").
+//
+// Structure (oriented lattice, corners TL, TR, BL, BR):
+//   F[q][t]   forward chain of corner q: F[q][t] = absorb(F[q][t-1], E_I(site t))
+//   M_top = TL TR^T, M_bot = BL BR^T, norm = <M_top, M_bot>     (ring closure)
+//   Env[TL] = M_bot TR, Env[TR] = M_bot^T TL, Env[BL] = M_top BR, Env[BR] = M_top^T BL
+//   G[q][t]   environment sweep: G[q][T] = Env[q],
+//             G[q][t-1] = absorb(G[q][t], E_I(site t)^T), so <F[q][t], G[q][t]> = norm
+//   site k at step t:      <absorb(F[q][t-1], E_X), G[q][t]>
+//   bond inside corner q:  Z inserted at the first site, the chain carried to
+//                          the second site (1 step, or one frame row), Z there,
+//                          dotted with G at that step
+//   bond across a cut:     both corners regrown with Z to their last step, then
+//                          one dense product with the rest of the ring.
+// Every value is exact (no truncation); reusing the unchanged corners and
+// environments instead of one full contraction per observable changes only the
+// amount of work.  Every tensor is a separate SSA value; an interval allocator
+// packs their lifetimes (wave of production .. last wave that reads them) into
+// one arena.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+
+#include "tn_internal.h"
+#include "tn_kernels.h"
+
+namespace tn {
+
+namespace {
+
+struct SiteRef {
+    int q = -1, t = -1, k = -1, c = -1;   // corner, 1-based chain step, frame row / column
+};
+
+class Builder {
+public:
+    Builder(Program& pg) : pg_(pg) {}
+
+    int tensor(int64_t n, int level) {
+        Tensor t;
+        t.n = n;
+        t.level = level;
+        t.slot = pg_.n_slots++;
+        pg_.tensors.push_back(t);
+        return (int)pg_.tensors.size() - 1;
+    }
+    int scalar(int level) { return tensor(0, level); }
+    int const_one() {
+        if (one_ < 0) {
+            one_ = tensor(1, 0);
+            pg_.tensors[one_].is_const_one = true;
+        }
+        return one_;
+    }
+    void use(int tid, int level) {
+        Tensor& t = pg_.tensors[tid];
+        t.last_use = std::max(t.last_use, level);
+    }
+    int level_of(int tid) const { return pg_.tensors[tid].level; }
+
+    int add(Op op) {
+        pg_.ops.push_back(op);
+        return (int)pg_.ops.size() - 1;
+    }
+
+    // Site matrix of `site` with physical operator `phys` in its corner's frame.
+    int sitemat(int site, int phys, const CornerPlan& cp, const Step& s) {
+        auto key = std::make_pair(site, phys);
+        auto it = E_.find(key);
+        if (it != E_.end()) return it->second;
+        const int e = tensor((int64_t)s.K * s.N, 0);
+        Op op;
+        op.kind = OP_SITEMAT;
+        op.level = 0;
+        op.out = e;
+        op.site = site;
+        op.phys = phys;
+        op.K = s.K;
+        op.N = s.N;
+        std::memcpy(op.map, cp.map, sizeof(op.map));
+        for (int k = 0; k < 4; ++k) op.fdim[k] = pg_.site_dims[4 * site + cp.map[k]];
+        // the chain step's leg groups must be the site's frame legs (double layer)
+        const int fu = op.fdim[0], fl = op.fdim[1], fd = op.fdim[2], fr = op.fdim[3];
+        if (s.K != fl * fl * fu * fu || s.N != fd * fd * fr * fr)
+            throw std::logic_error("site matrix shape does not match its chain step");
+        op.bytes = (double)s.K * s.N * pg_.esize;
+        add(op);
+        E_[key] = e;
+        return e;
+    }
+
+    // out = absorb(in, E) with the shape of step s (transposed: backward sweep).
+    int absorb(int in, int E, const Step& s, bool trans) {
+        const int level = std::max(level_of(in), level_of(E)) + 1;
+        const int64_t nout = trans ? s.n_in : s.n_out;
+        const int out = tensor(nout, level);
+        Op op;
+        op.kind = OP_ABSORB;
+        op.level = level;
+        op.in = in; op.E = E; op.out = out;
+        op.P = s.P; op.S = s.S;
+        op.K = trans ? s.N : s.K;
+        op.N = trans ? s.K : s.N;
+        op.transE = trans;
+        op.bytes = (double)(s.n_in + s.n_out) * pg_.esize;
+        op.macs = (double)s.mac;
+        use(in, level); use(E, level);
+        add(op);
+        return out;
+    }
+
+    // scalar = <absorb(in, E), adj> with the shape of step s.
+    int absorb_dot(int in, int E, int adj, const Step& s) {
+        const int level = std::max({level_of(in), level_of(E), level_of(adj)}) + 1;
+        const int out = scalar(level);
+        Op op;
+        op.kind = OP_ABSORB_DOT;
+        op.level = level;
+        op.in = in; op.E = E; op.adj = adj; op.out = out;
+        op.P = s.P; op.S = s.S; op.K = s.K; op.N = s.N;
+        op.bytes = (double)(s.n_in + 2 * s.n_out) * pg_.esize;
+        op.macs = (double)s.mac + (double)s.n_out;
+        use(in, level); use(E, level); use(adj, level);
+        add(op);
+        return out;
+    }
+
+    // C[m][n] = sum_k A(m,k) B(k,n); dot partner Cd -> scalar.
+    int gemm(int A, int B, int64_t M, int64_t N, int64_t K, int64_t sam, int64_t sak,
+             int64_t sbk, int64_t sbn, int Cd = -1) {
+        int level = std::max(level_of(A), level_of(B)) + 1;
+        if (Cd >= 0) level = std::max(level, level_of(Cd) + 1);
+        const int out = Cd >= 0 ? scalar(level) : tensor(M * N, level);
+        Op op;
+        op.kind = Cd >= 0 ? OP_GEMM_DOT : OP_GEMM;
+        op.level = level;
+        op.A = A; op.B = B; op.C = Cd; op.out = out;
+        op.gm = M; op.gn = N; op.gk = K;
+        op.sam = sam; op.sak = sak; op.sbk = sbk; op.sbn = sbn;
+        op.bytes = (double)(M * K + K * N + M * N) * pg_.esize;
+        op.macs = (double)M * N * K;
+        use(A, level); use(B, level);
+        if (Cd >= 0) use(Cd, level);
+        add(op);
+        return out;
+    }
+
+    int dot(int A, int B, int64_t n) {
+        const int level = std::max(level_of(A), level_of(B)) + 1;
+        const int out = scalar(level);
+        Op op;
+        op.kind = OP_DOT;
+        op.level = level;
+        op.A = A; op.B = B; op.out = out;
+        op.gm = n;
+        op.bytes = 2.0 * n * pg_.esize;
+        op.macs = (double)n;
+        use(A, level); use(B, level);
+        add(op);
+        return out;
+    }
+
+private:
+    Program& pg_;
+    int one_ = -1;
+    std::map<std::pair<int, int>, int> E_;
+};
+
+// Greedy first-fit interval packing of tensor lifetimes, wave by wave.
+int64_t pack_arena(Program& pg) {
+    const int64_t align = 256;
+    struct Block { int64_t off, len; };
+    std::vector<Block> freel;   // sorted by offset
+    int64_t top = 0;
+    int max_level = 0;
+    for (const auto& t : pg.tensors) max_level = std::max({max_level, t.level, t.last_use});
+    std::vector<std::vector<int>> born(max_level + 1), dies(max_level + 2);
+    for (int k = 0; k < (int)pg.tensors.size(); ++k) {
+        Tensor& t = pg.tensors[k];
+        if (t.n == 0) continue;
+        if (t.last_use < t.level) t.last_use = t.level;
+        born[t.level].push_back(k);
+        dies[t.last_use + 1].push_back(k);
+    }
+    auto release = [&](int64_t off, int64_t len) {
+        freel.push_back({off, len});
+        std::sort(freel.begin(), freel.end(), [](const Block& a, const Block& b) { return a.off < b.off; });
+        std::vector<Block> merged;
+        for (const auto& b : freel) {
+            if (!merged.empty() && merged.back().off + merged.back().len == b.off) merged.back().len += b.len;
+            else merged.push_back(b);
+        }
+        freel.swap(merged);
+        if (!freel.empty() && freel.back().off + freel.back().len == top) {
+            top = freel.back().off;
+            freel.pop_back();
+        }
+    };
+    int64_t high = 0;
+    for (int lv = 0; lv <= max_level; ++lv) {
+        for (int k : dies[lv]) {
+            const Tensor& t = pg.tensors[k];
+            release(t.offset, (t.n * pg.esize + align - 1) / align * align);
+        }
+        for (int k : born[lv]) {
+            Tensor& t = pg.tensors[k];
+            const int64_t len = (t.n * pg.esize + align - 1) / align * align;
+            bool placed = false;
+            for (size_t b = 0; b < freel.size(); ++b) {
+                if (freel[b].len >= len) {
+                    t.offset = freel[b].off;
+                    freel[b].off += len;
+                    freel[b].len -= len;
+                    if (freel[b].len == 0) freel.erase(freel.begin() + b);
+                    placed = true;
+                    break;
+                }
+            }
+            if (!placed) {
+                t.offset = top;
+                top += len;
+            }
+            high = std::max(high, top);
+        }
+    }
+    return high;
+}
+
+}  // namespace
+
+std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sched,
+                                             tn_precision prec, tn_work work) {
+    auto pgp = std::make_shared<Program>();
+    Program& pg = *pgp;
+    pg.plan = plan_choose(L, W, D, sched);
+    pg.work = work;
+    pg.dt = prec == TN_FP64 ? DT_F64 : DT_F32;
+    pg.esize = pg.dt == DT_F64 ? 8 : 4;
+    const Plan& pl = pg.plan;
+    const int nsite = L * W;
+
+    // raw FP64 input layout, [p][u][l][dn][rt] per site, row-major sites
+    pg.site_offset.resize(nsite + 1);
+    pg.site_dims.resize(4 * nsite);
+    pg.site_offset[0] = 0;
+    for (int r = 0; r < L; ++r)
+        for (int c = 0; c < W; ++c) {
+            const int s = r * W + c;
+            int* dm = &pg.site_dims[4 * s];
+            dm[0] = r == 0 ? 1 : D;
+            dm[1] = c == 0 ? 1 : D;
+            dm[2] = r == L - 1 ? 1 : D;
+            dm[3] = c == W - 1 ? 1 : D;
+            pg.site_offset[s + 1] = pg.site_offset[s] + 2LL * dm[0] * dm[1] * dm[2] * dm[3];
+        }
+    pg.input_bytes = pg.site_offset[nsite] * 8;
+
+    Builder bd(pg);
+    std::vector<SiteRef> where(nsite);
+    for (int q = 0; q < 4; ++q) {
+        const auto& st = pl.corner[q].steps;
+        for (int t = 0; t < (int)st.size(); ++t) {
+            SiteRef& w = where[st[t].r * W + st[t].col];
+            w.q = q; w.t = t + 1; w.k = st[t].k; w.c = st[t].c;
+        }
+    }
+    auto step_of = [&](int q, int t) -> const Step& { return pl.corner[q].steps[t - 1]; };
+    auto site_of = [&](int q, int t) { const Step& s = step_of(q, t); return s.r * W + s.col; };
+    auto E_at = [&](int q, int t, int phys) {
+        return bd.sitemat(site_of(q, t), phys, pl.corner[q], step_of(q, t));
+    };
+
+    // forward chains
+    std::vector<int> F[4];
+    int Qt[4];
+    for (int q = 0; q < 4; ++q) {
+        const int T = (int)pl.corner[q].steps.size();
+        F[q].assign(T + 1, -1);
+        F[q][0] = bd.const_one();
+        for (int t = 1; t <= T; ++t) F[q][t] = bd.absorb(F[q][t - 1], E_at(q, t, PH_I), step_of(q, t), false);
+        Qt[q] = F[q][T];
+    }
+    const int64_t hbL = pl.hb_L, hbR = pl.hb_R, vrT = pl.vr_T, vrB = pl.vr_B;
+    // ring closure
+    const int Mtop = bd.gemm(Qt[TL], Qt[TR], hbL, hbR, vrT, vrT, 1, 1, vrT);
+    const int Mbot = bd.gemm(Qt[BL], Qt[BR], hbL, hbR, vrB, vrB, 1, 1, vrB);
+    pg.norm_slot = pg.tensors[bd.dot(Mtop, Mbot, hbL * hbR)].slot;
+
+    if (work == TN_WORK_ENERGY) {
+        int Env[4] = {-1, -1, -1, -1};
+        auto nonempty = [&](int q) { return !pl.corner[q].steps.empty(); };
+        if (nonempty(TL)) Env[TL] = bd.gemm(Mbot, Qt[TR], hbL, vrT, hbR, hbR, 1, vrT, 1);
+        if (nonempty(TR)) Env[TR] = bd.gemm(Mbot, Qt[TL], hbR, vrT, hbL, 1, hbR, vrT, 1);
+        if (nonempty(BL)) Env[BL] = bd.gemm(Mtop, Qt[BR], hbL, vrB, hbR, hbR, 1, vrB, 1);
+        if (nonempty(BR)) Env[BR] = bd.gemm(Mtop, Qt[BL], hbR, vrB, hbL, 1, hbR, vrB, 1);
+        // environment sweeps
+        std::vector<int> G[4];
+        for (int q = 0; q < 4; ++q) {
+            const int T = (int)pl.corner[q].steps.size();
+            G[q].assign(T + 1, -1);
+            if (!T) continue;
+            G[q][T] = Env[q];
+            for (int t = T; t >= 2; --t) G[q][t - 1] = bd.absorb(G[q][t], E_at(q, t, PH_I), step_of(q, t), true);
+        }
+        // sites
+        pg.sx_slot.assign(nsite, -1);
+        for (int s = 0; s < nsite; ++s) {
+            const SiteRef& w = where[s];
+            const int v = bd.absorb_dot(F[w.q][w.t - 1], E_at(w.q, w.t, PH_X), G[w.q][w.t], step_of(w.q, w.t));
+            pg.sx_slot[s] = pg.tensors[v].slot;
+        }
+        // bonds, output order: horizontal row-major, then vertical row-major
+        std::vector<std::pair<int, int>> bonds;
+        for (int r = 0; r < L; ++r)
+            for (int c = 0; c + 1 < W; ++c) bonds.push_back({r * W + c, r * W + c + 1});
+        for (int r = 0; r + 1 < L; ++r)
+            for (int c = 0; c < W; ++c) bonds.push_back({r * W + c, (r + 1) * W + c});
+        int Xl = -1, Xr = -1;
+        auto regrow = [&](int q, int t) {
+            const int T = (int)pl.corner[q].steps.size();
+            int x = bd.absorb(F[q][t - 1], E_at(q, t, PH_Z), step_of(q, t), false);
+            for (int u = t + 1; u <= T; ++u) x = bd.absorb(x, E_at(q, u, PH_I), step_of(q, u), false);
+            return x;
+        };
+        pg.zz_slot.assign(bonds.size(), -1);
+        for (size_t bi = 0; bi < bonds.size(); ++bi) {
+            SiteRef a = where[bonds[bi].first], b = where[bonds[bi].second];
+            int v = -1;
+            if (a.q == b.q) {
+                if (a.t > b.t) std::swap(a, b);
+                const int q = a.q;
+                int x = bd.absorb(F[q][a.t - 1], E_at(q, a.t, PH_Z), step_of(q, a.t), false);
+                for (int u = a.t + 1; u < b.t; ++u) x = bd.absorb(x, E_at(q, u, PH_I), step_of(q, u), false);
+                v = bd.absorb_dot(x, E_at(q, b.t, PH_Z), G[q][b.t], step_of(q, b.t));
+            } else {
+                int qa = a.q, qb = b.q;
+                int ta = a.t, tb = b.t;
+                if (qa > qb) { std::swap(qa, qb); std::swap(ta, tb); }
+                const int Za = regrow(qa, ta), Zb = regrow(qb, tb);
+                if (qa == TL && qb == TR) {
+                    v = bd.gemm(Mbot, Zb, hbL, vrT, hbR, hbR, 1, vrT, 1, Za);
+                } else if (qa == BL && qb == BR) {
+                    v = bd.gemm(Mtop, Zb, hbL, vrB, hbR, hbR, 1, vrB, 1, Za);
+                } else if (qa == TL && qb == BL) {
+                    if (Xr < 0) Xr = bd.gemm(Qt[TR], Qt[BR], vrT, vrB, hbR, 1, vrT, vrB, 1);
+                    v = bd.gemm(Za, Zb, vrT, vrB, hbL, 1, vrT, vrB, 1, Xr);
+                } else if (qa == TR && qb == BR) {
+                    if (Xl < 0) Xl = bd.gemm(Qt[TL], Qt[BL], vrT, vrB, hbL, 1, vrT, vrB, 1);
+                    v = bd.gemm(Za, Zb, vrT, vrB, hbR, 1, vrT, vrB, 1, Xl);
+                } else {
+                    throw std::logic_error("bond between non-adjacent corners");
+                }
+            }
+            pg.zz_slot[bi] = pg.tensors[v].slot;
+        }
+    }
+    int nl = 0;
+    for (const auto& op : pg.ops) nl = std::max(nl, op.level);
+    pg.n_levels = nl + 1;
+    pg.arena_bytes = pack_arena(pg);
+    return pgp;
+}
+
+}  // namespace tn

@@ -1,0 +1,440 @@
+// Batch runtime: lays out one device buffer per batch (site inputs, tensor
+// arena, rescaling slots, dot partials, results, task tables), groups every
+// member's operations wave by wave into grouped launches, and replays the
+// launch sequence as a CUDA graph.
+#include <algorithm>
+#include <cstring>
+
+#include "runtime.h"
+
+namespace tn {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+const char* last_error() { return g_err.c_str(); }
+
+tn_status cuda_status(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return TN_OK;
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? TN_ERR_OOM : TN_ERR_CUDA;
+}
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct OpRef {
+    int member, op;
+};
+
+int family_of(int kind) {
+    switch (kind) {
+        case OP_ABSORB: return FAM_ABSORB;
+        case OP_ABSORB_DOT: return FAM_ABSORB_DOT;
+        case OP_GEMM: case OP_GEMM_DOT: return FAM_GEMM;
+        default: return FAM_OTHER;
+    }
+}
+
+long long gemm_tiles(long long M, long long N, int* tiles_n) {
+    const long long tm = (M + kGemmTile - 1) / kGemmTile, tn_ = (N + kGemmTile - 1) / kGemmTile;
+    *tiles_n = (int)tn_;
+    return tm * tn_;
+}
+
+// Build every launch and its task table.  With base == nullptr only sizes are
+// computed (footprint); otherwise task structs hold absolute device pointers.
+void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vector<int>* ints_out,
+                 std::vector<ConstOne>* ones_out) {
+    Layout& lay = b->lay;
+    const int esize = b->dt == 0 ? 8 : 4;
+    // --- regions that do not depend on tasks
+    int64_t nin = 0, nslots = 0, nres = 0;
+    size_t arena = 0;
+    for (auto& mb : b->m) {
+        mb.in_off = nin;
+        mb.in_elems = mb.pg->site_offset.back();
+        nin += mb.in_elems;
+        mb.arena_off = (int64_t)arena;
+        arena += up((size_t)mb.pg->arena_bytes);
+        mb.slot_base = nslots;
+        nslots += mb.pg->n_slots;
+        mb.res_off = nres;
+        mb.res_elems = 4 + (int64_t)mb.pg->sx_slot.size() + (int64_t)mb.pg->zz_slot.size();
+        nres += mb.res_elems;
+    }
+    lay.nin = nin;
+    lay.nslots = nslots;
+    lay.nres = nres;
+    // --- group operations: (level, kind, K, N) -> op refs (member-major order)
+    std::map<std::tuple<int, int, int, int>, std::vector<OpRef>> groups;
+    int64_t npart = 0;
+    for (int mi = 0; mi < (int)b->m.size(); ++mi) {
+        const Program& pg = *b->m[mi].pg;
+        for (int oi = 0; oi < (int)pg.ops.size(); ++oi) {
+            const Op& op = pg.ops[oi];
+            int K = 0, N = 0;
+            if (op.kind == OP_ABSORB || op.kind == OP_ABSORB_DOT) { K = op.K; N = op.N; }
+            groups[std::make_tuple(op.level, (int)op.kind, K, N)].push_back({mi, oi});
+        }
+    }
+    // --- device pointers of the fixed regions
+    lay.in_off = 0;
+    lay.arena_off = up(lay.in_off + (size_t)nin * 8);
+    lay.slots_off = up(lay.arena_off + arena);
+    auto ptr = [&](size_t off) -> char* { return base ? base + off : nullptr; };
+    Slot* slots_base = reinterpret_cast<Slot*>(ptr(lay.slots_off));
+    (void)slots_base;
+    // partial offsets are assigned while tasks are generated; region placed after slots
+    std::vector<char> tasks;
+    std::vector<int> ints;
+    std::vector<ConstOne> ones;
+    b->launches.clear();
+    auto tensor_ptr = [&](int mi, int tid) -> void* {
+        const Member& mb = b->m[mi];
+        const Tensor& t = mb.pg->tensors[tid];
+        if (!base) return nullptr;
+        return base + lay.arena_off + mb.arena_off + t.offset;
+    };
+    auto slot_of = [&](int mi, int tid) -> int {
+        return (int)(b->m[mi].slot_base + b->m[mi].pg->tensors[tid].slot);
+    };
+    // partial region placement needs npart first: count dot tiles
+    for (auto& kv : groups) {
+        const int kind = std::get<1>(kv.first);
+        for (const OpRef& r : kv.second) {
+            const Op& op = b->m[r.member].pg->ops[r.op];
+            if (kind == OP_ABSORB_DOT) npart += absorb_tiles(op.P, op.S, op.K, op.N);
+            else if (kind == OP_GEMM_DOT) { int tn_; npart += gemm_tiles(op.gm, op.gn, &tn_); }
+            else if (kind == OP_DOT) npart += (op.gm + kDotPerBlock - 1) / kDotPerBlock;
+        }
+    }
+    lay.npart = npart;
+    lay.part_off = up(lay.slots_off + (size_t)nslots * sizeof(Slot));
+    lay.res_off = up(lay.part_off + (size_t)npart * 8);
+    lay.tasks_off = up(lay.res_off + (size_t)nres * 8);
+    double* part_base = reinterpret_cast<double*>(ptr(lay.part_off));
+    int64_t part_cur = 0;
+    auto take_partial = [&](long long n) -> double* {
+        double* p = part_base ? part_base + part_cur : nullptr;
+        part_cur += n;
+        return p;
+    };
+    auto append = [&](const void* src, size_t n) -> size_t {
+        size_t off = (tasks.size() + 15) / 16 * 16;
+        tasks.resize(off + n);
+        std::memcpy(tasks.data() + off, src, n);
+        return off;
+    };
+    for (auto& kv : groups) {
+        const int kind = std::get<1>(kv.first);
+        Launch L;
+        L.kind = kind;
+        L.dt = b->dt;
+        L.K = std::get<2>(kv.first);
+        L.N = std::get<3>(kv.first);
+        const auto& refs = kv.second;
+        L.ntasks = (int)refs.size();
+        long long tile = 0;
+        size_t first = SIZE_MAX;
+        for (const OpRef& r : refs) {
+            const Member& mb = b->m[r.member];
+            const Program& pg = *mb.pg;
+            const Op& op = pg.ops[r.op];
+            L.bytes += op.bytes;
+            L.macs += op.macs;
+            size_t off = 0;
+            if (kind == OP_SITEMAT) {
+                SiteMatTask t{};
+                t.A = base ? reinterpret_cast<const double*>(base + lay.in_off) + mb.in_off + pg.site_offset[op.site]
+                           : nullptr;
+                t.E = tensor_ptr(r.member, op.out);
+                for (int k = 0; k < 4; ++k) { t.dims[k] = pg.site_dims[4 * op.site + k]; t.map[k] = op.map[k]; }
+                t.phys = op.phys;
+                t.slot_E = slot_of(r.member, op.out);
+                t.K = op.K; t.N = op.N;
+                off = append(&t, sizeof(t));
+                tile += 1;
+            } else if (kind == OP_ABSORB || kind == OP_ABSORB_DOT) {
+                AbsorbTask t{};
+                t.in = tensor_ptr(r.member, op.in);
+                t.E = tensor_ptr(r.member, op.E);
+                t.P = op.P; t.S = op.S; t.K = op.K; t.N = op.N;
+                t.transE = op.transE ? 1 : 0;
+                t.slot_in = slot_of(r.member, op.in);
+                t.slot_E = slot_of(r.member, op.E);
+                t.slot_out = slot_of(r.member, op.out);
+                t.tile0 = tile;
+                const long long nt = absorb_tiles(op.P, op.S, op.K, op.N);
+                t.ntiles = (int)nt;
+                if (kind == OP_ABSORB_DOT) {
+                    t.adj = tensor_ptr(r.member, op.adj);
+                    t.slot_adj = slot_of(r.member, op.adj);
+                    t.partial = take_partial(nt);
+                } else {
+                    t.out = tensor_ptr(r.member, op.out);
+                }
+                off = append(&t, sizeof(t));
+                tile += nt;
+            } else if (kind == OP_GEMM || kind == OP_GEMM_DOT) {
+                GemmTask t{};
+                t.A = tensor_ptr(r.member, op.A);
+                t.B = tensor_ptr(r.member, op.B);
+                t.M = op.gm; t.N = op.gn; t.K = op.gk;
+                t.sam = op.sam; t.sak = op.sak; t.sbk = op.sbk; t.sbn = op.sbn;
+                t.slot_A = slot_of(r.member, op.A);
+                t.slot_B = slot_of(r.member, op.B);
+                t.slot_C = slot_of(r.member, op.out);
+                int tn_ = 0;
+                const long long nt = gemm_tiles(op.gm, op.gn, &tn_);
+                t.tiles_n = tn_;
+                t.ntiles = (int)nt;
+                t.tile0 = tile;
+                if (kind == OP_GEMM_DOT) {
+                    t.Dm = tensor_ptr(r.member, op.C);
+                    t.slot_D = slot_of(r.member, op.C);
+                    t.partial = take_partial(nt);
+                } else {
+                    t.C = tensor_ptr(r.member, op.out);
+                }
+                off = append(&t, sizeof(t));
+                tile += nt;
+            } else if (kind == OP_DOT) {
+                DotTask t{};
+                t.A = tensor_ptr(r.member, op.A);
+                t.B = tensor_ptr(r.member, op.B);
+                t.n = op.gm;
+                t.slot_A = slot_of(r.member, op.A);
+                t.slot_B = slot_of(r.member, op.B);
+                t.slot_out = slot_of(r.member, op.out);
+                const long long nt = (op.gm + kDotPerBlock - 1) / kDotPerBlock;
+                t.ntiles = (int)nt;
+                t.tile0 = tile;
+                t.partial = take_partial(nt);
+                off = append(&t, sizeof(t));
+                tile += nt;
+            }
+            first = std::min(first, off);
+        }
+        L.task_off = first;
+        L.nblocks = tile;
+        b->launches.push_back(L);
+    }
+    // const-one tensors
+    for (int mi = 0; mi < (int)b->m.size(); ++mi) {
+        const Program& pg = *b->m[mi].pg;
+        for (int tid = 0; tid < (int)pg.tensors.size(); ++tid)
+            if (pg.tensors[tid].is_const_one) ones.push_back({tensor_ptr(mi, tid)});
+    }
+    // final tasks and their slot tables
+    b->h_final.clear();
+    std::vector<std::pair<size_t, size_t>> tbl;   // (sx offset, zz offset) in ints
+    for (int mi = 0; mi < (int)b->m.size(); ++mi) {
+        const Member& mb = b->m[mi];
+        const Program& pg = *mb.pg;
+        const size_t sx0 = ints.size();
+        for (int s : pg.sx_slot) ints.push_back((int)(mb.slot_base + s));
+        const size_t zz0 = ints.size();
+        for (int s : pg.zz_slot) ints.push_back((int)(mb.slot_base + s));
+        tbl.push_back({sx0, zz0});
+    }
+    lay.task_bytes = tasks.size();
+    lay.final_off = up(lay.tasks_off + tasks.size());
+    lay.ints_off = up(lay.final_off + b->m.size() * sizeof(FinalTask));
+    lay.ones_off = up(lay.ints_off + ints.size() * sizeof(int));
+    lay.total = up(lay.ones_off + ones.size() * sizeof(ConstOne));
+    lay.nones = (int64_t)ones.size();
+    lay.nints = (int64_t)ints.size();
+    for (int mi = 0; mi < (int)b->m.size(); ++mi) {
+        const Member& mb = b->m[mi];
+        FinalTask f{};
+        f.norm_slot = (int)(mb.slot_base + mb.pg->norm_slot);
+        f.n_sites = (int)mb.pg->sx_slot.size();
+        f.n_bonds = (int)mb.pg->zz_slot.size();
+        if (base) {
+            const int* ib = reinterpret_cast<const int*>(base + lay.ints_off);
+            f.sx_slots = ib + tbl[mi].first;
+            f.zz_slots = ib + tbl[mi].second;
+            f.out = reinterpret_cast<double*>(base + lay.res_off) + mb.res_off;
+        }
+        f.J = 1.0;
+        f.h = 0.0;
+        b->h_final.push_back(f);
+    }
+    (void)esize;
+    if (tasks_out) tasks_out->swap(tasks);
+    if (ints_out) ints_out->swap(ints);
+    if (ones_out) ones_out->swap(ones);
+}
+
+}  // namespace
+
+tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int* D,
+                       tn_precision prec, tn_schedule sched, tn_work work, bool alloc,
+                       tn_batch** out, size_t* bytes) {
+    if (n <= 0 || !L || !W || !D) { set_error("empty batch"); return TN_ERR_INVALID; }
+    if (prec < TN_FP64 || prec > TN_BF16X3 || sched < TN_SCHED_AUTO || sched > TN_SCHED_QUADRANT ||
+        work < TN_WORK_NORM || work > TN_WORK_ENERGY) {
+        set_error("bad enum"); return TN_ERR_INVALID;
+    }
+    for (int k = 0; k < n; ++k)
+        if (L[k] < 1 || L[k] > 16 || W[k] < 1 || W[k] > 16 || D[k] < 1 || D[k] > 4) {
+            set_error("lattice size out of range (1..16 x 1..16, D 1..4)");
+            return TN_ERR_INVALID;
+        }
+    auto b = std::make_unique<tn_batch>();
+    b->ctx = ctx;
+    b->dt = prec == TN_FP64 ? 0 : 1;
+    b->work = work;
+    b->sched = sched;
+    // programs are shared between members of the same shape
+    std::map<std::tuple<int, int, int>, std::shared_ptr<const Program>> cache;
+    for (int k = 0; k < n; ++k) {
+        auto key = std::make_tuple(L[k], W[k], D[k]);
+        auto it = cache.find(key);
+        if (it == cache.end()) {
+            try {
+                it = cache.emplace(key, program_build(L[k], W[k], D[k], sched, prec, work)).first;
+            } catch (const std::exception& e) {
+                set_error(e.what());
+                return TN_ERR_INVALID;
+            }
+        }
+        Member mb;
+        mb.pg = it->second;
+        mb.L = L[k]; mb.W = W[k]; mb.D = D[k];
+        b->m.push_back(mb);
+    }
+    materialize(b.get(), nullptr, nullptr, nullptr, nullptr);
+    if (bytes) *bytes = b->lay.total;
+    if (!alloc) { *out = b.release(); return TN_OK; }
+    if (!ctx || ctx->device < 0) { set_error("context has no device"); return TN_ERR_NO_DEVICE; }
+    const size_t need = b->lay.total;
+    size_t cur = ctx->used.load();
+    do {
+        if (cur + need > ctx->budget) {
+            set_error("footprint " + std::to_string(need) + " B exceeds the remaining budget");
+            return TN_ERR_OVER_BUDGET;
+        }
+    } while (!ctx->used.compare_exchange_weak(cur, cur + need));
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaMalloc(&b->buf, need);
+    if (e != cudaSuccess) {
+        ctx->used -= need;
+        return cuda_status(e, "cudaMalloc");
+    }
+    std::vector<char> tasks;
+    std::vector<int> ints;
+    std::vector<ConstOne> ones;
+    materialize(b.get(), b->buf, &tasks, &ints, &ones);
+    b->stream = ctx->stream;
+    e = cudaMemcpy(b->buf + b->lay.tasks_off, tasks.data(), tasks.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !ints.empty())
+        e = cudaMemcpy(b->buf + b->lay.ints_off, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !ones.empty())
+        e = cudaMemcpy(b->buf + b->lay.ones_off, ones.data(), ones.size() * sizeof(ConstOne), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->buf + b->lay.in_off, 0, (size_t)b->lay.nin * 8);
+    if (e != cudaSuccess) {
+        cudaFree(b->buf);
+        ctx->used -= need;
+        return cuda_status(e, "batch upload");
+    }
+    b->h_h.assign(b->m.size(), 0.0);
+    *out = b.release();
+    return TN_OK;
+}
+
+void batch_destroy(tn_batch* b) {
+    if (!b) return;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->buf) {
+        cudaFree(b->buf);
+        b->ctx->used -= b->lay.total;
+    }
+    delete b;
+}
+
+namespace {
+
+cudaError_t issue(tn_batch* b, cudaStream_t st, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev) {
+    char* base = b->buf;
+    Slot* slots = reinterpret_cast<Slot*>(base + b->lay.slots_off);
+    cudaError_t e = launch_init(slots, b->lay.nslots, reinterpret_cast<const ConstOne*>(base + b->lay.ones_off),
+                                (int)b->lay.nones, b->dt, st);
+    if (e != cudaSuccess) return e;
+    const char* tb = base + b->lay.tasks_off;
+    for (size_t li = 0; li < b->launches.size(); ++li) {
+        const Launch& L = b->launches[li];
+        if (ev) cudaEventRecord((*ev)[li].first, st);
+        const void* tp = tb + L.task_off;
+        switch (L.kind) {
+            case OP_SITEMAT:
+                e = launch_sitemat(L.dt, static_cast<const SiteMatTask*>(tp), L.ntasks, slots, st);
+                break;
+            case OP_ABSORB:
+            case OP_ABSORB_DOT:
+                e = launch_absorb(L.dt, L.kind == OP_ABSORB_DOT, L.K, L.N, static_cast<const AbsorbTask*>(tp),
+                                  L.ntasks, L.nblocks, slots, st);
+                break;
+            case OP_GEMM:
+            case OP_GEMM_DOT:
+                e = launch_gemm(L.dt, L.kind == OP_GEMM_DOT, static_cast<const GemmTask*>(tp), L.ntasks,
+                                L.nblocks, slots, st);
+                break;
+            case OP_DOT:
+                e = launch_dot(L.dt, static_cast<const DotTask*>(tp), L.ntasks, L.nblocks, slots, st);
+                break;
+        }
+        if (ev) cudaEventRecord((*ev)[li].second, st);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_final(reinterpret_cast<const FinalTask*>(base + b->lay.final_off), (int)b->m.size(), slots, st);
+}
+
+}  // namespace
+
+tn_status batch_run(tn_batch* b, cudaStream_t st) {
+    tn_ctx* ctx = b->ctx;
+    cudaSetDevice(ctx->device);
+    // the fields of the final step (J, h) change between runs: refresh them
+    cudaError_t e = cudaMemcpyAsync(b->buf + b->lay.final_off, b->h_final.data(),
+                                    b->h_final.size() * sizeof(FinalTask), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e, "final table upload");
+    if (ctx->profiling) {
+        std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev(b->launches.size());
+        for (auto& p : ev) { cudaEventCreate(&p.first); cudaEventCreate(&p.second); }
+        e = issue(b, st, &ev);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) {
+            std::lock_guard<std::mutex> g(ctx->mu);
+            for (size_t li = 0; li < b->launches.size(); ++li) {
+                float ms = 0;
+                cudaEventElapsedTime(&ms, ev[li].first, ev[li].second);
+                KStat& s = ctx->stats[family_of(b->launches[li].kind)];
+                s.launches += 1;
+                s.ms += ms;
+                s.bytes += b->launches[li].bytes;
+                s.macs += b->launches[li].macs;
+            }
+        }
+        for (auto& p : ev) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+        return cuda_status(e, "profiled run");
+    }
+    if (!b->use_graph) return cuda_status(issue(b, st, nullptr), "batch run");
+    if (!b->gexec) {
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_status(e, "begin capture");
+        cudaError_t ei = issue(b, st, nullptr);
+        e = cudaStreamEndCapture(st, &g);
+        if (ei != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_status(ei, "capture issue"); }
+        if (e != cudaSuccess) return cuda_status(e, "end capture");
+        e = cudaGraphInstantiate(&b->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { b->gexec = nullptr; return cuda_status(e, "graph instantiate"); }
+    }
+    return cuda_status(cudaGraphLaunch(b->gexec, st), "graph launch");
+}
+
+}  // namespace tn

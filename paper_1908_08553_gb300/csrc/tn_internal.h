@@ -1,0 +1,137 @@
+// Internal declarations of libtn (host side).  Not part of the C-ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/tn.h"
+
+namespace tn {
+
+constexpr int64_t kCap = int64_t(1) << 62;   // saturation bound of planner integers
+
+inline int64_t sat_mul(int64_t a, int64_t b) {
+    if (a == 0 || b == 0) return 0;
+    if (a > kCap / b) return kCap;
+    int64_t v = a * b;
+    return v > kCap ? kCap : v;
+}
+inline int64_t sat_add(int64_t a, int64_t b) {
+    int64_t v = a + b;
+    return v > kCap ? kCap : v;
+}
+
+// ------------------------------------------------------------------ plan --
+
+// Corners of the ring (Sec. 4, quadrant scheme) in the oriented lattice.
+enum Corner { TL = 0, TR = 1, BL = 2, BR = 3 };
+
+// One site absorption: boundary [P, K, S] -> [P, N, S].
+struct Step {
+    int corner, k, c;        // frame row / column inside the corner
+    int r, col;              // lattice site (original orientation)
+    int64_t P, S;
+    int K, N;
+    int64_t n_in, n_out, mac;
+};
+
+struct CornerPlan {
+    int a = 0, b = 0;        // frame rows / columns
+    int bottom = 1, right = 1;   // double-layer dims of the frame's bottom / right cut legs
+    int map[4] = {0, 1, 2, 3};   // frame leg role (u,l,dn,rt) -> original leg index
+    std::vector<Step> steps;     // chain order
+    int64_t size_b = 1, size_r = 1;   // final tensor as [size_b][size_r]
+};
+
+struct Plan {
+    int L = 0, W = 0, D = 0, d = 0;
+    int o = 0, i = 0, j = 0;     // orientation and cut
+    int Lp = 0, Wp = 0;          // oriented lattice dims
+    int64_t peak = 0, mac = 0;
+    int centre = 0;
+    CornerPlan corner[4];
+    int64_t hb_L = 1, hb_R = 1, vr_T = 1, vr_B = 1;   // ring leg-group sizes
+};
+
+Plan plan_evaluate(int L, int W, int D, int o, int i, int j);
+Plan plan_choose(int L, int W, int D, tn_schedule sched);
+// oriented coordinates (r', c') of lattice site (r, c)
+void orient(const Plan& p, int r, int c, int* rr, int* cc);
+
+// ---------------------------------------------------------------- program --
+
+enum DType { DT_F64 = 0, DT_F32 = 1 };
+
+enum OpKind {
+    OP_SITEMAT = 0,   // build a double-layer site matrix E (K x N)
+    OP_ABSORB,        // out = absorb(in, E)        [P,K,S] -> [P,N,S]
+    OP_ABSORB_DOT,    // scalar = <absorb(in, E), adj>
+    OP_GEMM,          // C = opA(A) opB(B)
+    OP_GEMM_DOT,      // scalar = <opA(A) opB(B), C>
+    OP_DOT,           // scalar = <A, B>
+};
+
+// Operator insertion on the physical leg.
+enum PhysOp { PH_I = 0, PH_X = 1, PH_Z = 2 };
+
+struct Tensor {
+    int64_t n = 0;           // entries (0 for a scalar result)
+    int64_t offset = -1;     // bytes into the arena
+    int slot = -1;           // exponent / max / scalar slot
+    int level = 0;           // wave that produces it
+    int last_use = -1;       // last wave that reads it
+    bool is_const_one = false;
+    bool is_site = false;    // raw FP64 site tensor (lattice input), offset into the input area
+    int site = -1;
+};
+
+struct Op {
+    OpKind kind;
+    int level = 0;
+    // absorb
+    int in = -1, E = -1, out = -1, adj = -1;
+    int64_t P = 0, S = 0;
+    int K = 0, N = 0;
+    bool transE = false;
+    // gemm: C[m][n] = sum_k A(m,k) B(k,n); A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn]
+    int A = -1, B = -1, C = -1;
+    int64_t gm = 0, gn = 0, gk = 0;
+    int64_t sam = 0, sak = 0, sbk = 0, sbn = 0;
+    // sitemat
+    int site = -1, phys = PH_I;
+    int map[4] = {0, 1, 2, 3};
+    int fdim[4] = {1, 1, 1, 1};  // frame dims (u, l, dn, rt), single layer
+    // algorithmic accounting
+    double bytes = 0, macs = 0;
+};
+
+// Result addressing inside one program: which scalar slots hold what.
+struct Program {
+    Plan plan;
+    tn_work work = TN_WORK_ENERGY;
+    DType dt = DT_F32;
+    int esize = 4;
+    std::vector<Tensor> tensors;
+    std::vector<Op> ops;
+    int n_levels = 0;
+    int norm_slot = -1;
+    std::vector<int> sx_slot;     // per site (row-major, original lattice)
+    std::vector<int> zz_slot;     // per bond (output order)
+    int n_slots = 0;
+    int64_t arena_bytes = 0;      // tensors + site matrices (typed)
+    int64_t input_bytes = 0;      // raw FP64 site tensors
+    std::vector<int64_t> site_offset;   // FP64 entries, per site
+    std::vector<int> site_dims;          // 4 per site
+};
+
+std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sched,
+                                             tn_precision prec, tn_work work);
+int64_t program_footprint(const Program& p);   // arena + inputs + slots + results + scratch
+
+}  // namespace tn

@@ -1,0 +1,113 @@
+// Plain-old-data task descriptors shared by the host executor and the CUDA
+// kernels, and the host-side launch wrappers.  Every kernel processes a list of
+// independent tasks (all members of a batch, all corners, all observables of a
+// wave) in one launch; a block finds its task by a binary search over the
+// tasks' first tile index.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace tn {
+
+// Per-tensor bookkeeping of the power-of-two rescaling.  A tensor's true value
+// is stored * 2^X.  maxbits collects max|stored| (as FP64 bits, atomicMax) while
+// the tensor is produced; a consumer multiplies every loaded entry by 2^-e with
+// e = frexp exponent of that max, so its inputs are in [-1, 1).  Scalar results
+// keep their FP64 mantissa in `mant`; `count` orders the deterministic final
+// reduction of per-tile partial sums.
+struct Slot {
+    long long X;
+    unsigned long long maxbits;
+    double mant;
+    unsigned int count;
+    unsigned int pad;
+};
+static_assert(sizeof(Slot) == 32, "slot layout");
+
+struct AbsorbTask {
+    const void* in;
+    const void* E;
+    void* out;            // unused in dot mode
+    const void* adj;      // dot mode: adjoint tensor [P][N][S]
+    double* partial;      // dot mode: one FP64 partial per tile
+    long long P, S;
+    long long tile0;      // first global tile of this task
+    int K, N;
+    int transE;           // 1: use E[n][k] as E[k][n] (backward / environment sweep)
+    int slot_in, slot_E, slot_out, slot_adj;
+    int ntiles;
+};
+
+struct GemmTask {
+    // C[m][n] = sum_k A(m,k) B(k,n), A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn]
+    const void* A;
+    const void* B;
+    void* C;              // row-major [M][N]; unused in dot mode
+    const void* Dm;       // dot mode: partner, row-major [M][N]
+    double* partial;
+    long long M, N, K;
+    long long sam, sak, sbk, sbn;
+    long long tile0;
+    int tiles_n, ntiles;
+    int slot_A, slot_B, slot_C, slot_D;
+};
+
+struct DotTask {
+    const void* A;
+    const void* B;
+    double* partial;
+    long long n;
+    long long tile0;
+    int ntiles;
+    int slot_A, slot_B, slot_out;
+};
+
+struct SiteMatTask {
+    const double* A;      // raw FP64 site tensor [p][u][l][dn][rt]
+    void* E;              // K x N, compute dtype
+    int dims[4];          // original leg dims u, l, dn, rt
+    int map[4];           // frame role (u, l, dn, rt) -> original leg
+    int phys;             // 0 I, 1 X, 2 Z
+    int slot_E;
+    int K, N;
+};
+
+struct FinalTask {
+    const int* sx_slots;  // n_sites
+    const int* zz_slots;  // n_bonds
+    double* out;          // 4 + n_sites + n_bonds
+    double J, h;
+    int norm_slot;
+    int n_sites, n_bonds;
+};
+
+struct ConstOne {
+    void* ptr;
+};
+
+// ----------------------------------------------------------- launchers ---
+// Each returns cudaSuccess or the launch error.  dt: 0 FP64, 1 FP32.
+cudaError_t launch_absorb(int dt, bool dot, int K, int N, const AbsorbTask* tasks, int ntasks,
+                          long long nblocks, Slot* slots, cudaStream_t st);
+cudaError_t launch_gemm(int dt, bool dot, const GemmTask* tasks, int ntasks, long long nblocks,
+                        Slot* slots, cudaStream_t st);
+cudaError_t launch_dot(int dt, const DotTask* tasks, int ntasks, long long nblocks, Slot* slots,
+                       cudaStream_t st);
+cudaError_t launch_sitemat(int dt, const SiteMatTask* tasks, int ntasks, Slot* slots,
+                           cudaStream_t st);
+cudaError_t launch_init(Slot* slots, long long nslots, const ConstOne* ones, int nones, int dt,
+                        cudaStream_t st);
+cudaError_t launch_final(const FinalTask* tasks, int ntasks, const Slot* slots, cudaStream_t st);
+cudaError_t launch_absorb_plain(int dt, const void* in, const void* E, void* out, long long P,
+                                int K, int N, long long S, cudaStream_t st);
+
+// Tiles per task, fixed by shape only (bit-identical results alone or batched).
+constexpr int kAbsorbThreads = 256;
+constexpr int kGemmTile = 64;
+constexpr int kDotPerBlock = 4096;
+long long absorb_tiles(long long P, long long S, int K, int N);
+bool absorb_has_fast_path(int K, int N);
+
+}  // namespace tn

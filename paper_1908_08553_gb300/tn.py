@@ -1,0 +1,333 @@
+"""Thin ctypes binding of libtn (include/tn.h): same names, argument marshalling only.
+
+Every computation happens inside libtn's CUDA kernels.  If the library cannot
+be loaded this module raises; there is no CPU fallback.  Device buffers may be
+passed as torch CUDA tensors (their data_ptr is used) or raw integer pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t, c_uint64, c_void_p
+
+import numpy as np
+
+from . import build as _build
+
+TN_OK, TN_NOT_READY = 0, 1
+TN_ERR_INVALID, TN_ERR_OVER_BUDGET, TN_ERR_OOM = -1, -2, -3
+TN_ERR_CUDA, TN_ERR_TIMEOUT, TN_ERR_NUMERIC, TN_ERR_NO_DEVICE = -4, -5, -6, -7
+TN_FP64, TN_FP32, TN_BF16X3 = 0, 1, 2
+TN_SCHED_AUTO, TN_SCHED_ROW, TN_SCHED_COL, TN_SCHED_QUADRANT = 0, 1, 2, 3
+TN_WORK_NORM, TN_WORK_ENERGY = 0, 1
+TN_OP_NORM, TN_OP_X, TN_OP_ZZ = 0, 1, 2
+
+PRECISIONS = {"fp64": TN_FP64, "fp32": TN_FP32, "bf16x3": TN_BF16X3}
+
+
+class tn_scalar(ctypes.Structure):
+    _fields_ = [("mant", c_double), ("exp2", c_int64)]
+
+
+class tn_result(ctypes.Structure):
+    _fields_ = [("energy", c_double), ("energy_per_site", c_double), ("norm", tn_scalar),
+                ("sx", POINTER(c_double)), ("szsz", POINTER(c_double)), ("err_bound_est", c_double),
+                ("precision", c_int), ("schedule_o", c_int), ("schedule_i", c_int), ("schedule_j", c_int)]
+
+
+class tn_job(ctypes.Structure):
+    _fields_ = [("L", c_int), ("W", c_int), ("D", c_int), ("precision", c_int), ("J", c_double),
+                ("h", c_double), ("tensors", POINTER(c_double)), ("seed", c_uint64)]
+
+
+# name -> (restype, argtypes): the complete exported surface of include/tn.h
+SIGNATURES = {
+    "tn_ctx_create": (c_int, [c_int, c_size_t, c_void_p, POINTER(c_void_p)]),
+    "tn_ctx_destroy": (c_int, [c_void_p]),
+    "tn_ctx_memory": (c_int, [c_void_p, POINTER(c_size_t), POINTER(c_size_t)]),
+    "tn_create_lattice": (c_int, [c_void_p, c_int, c_int, c_int, POINTER(c_void_p)]),
+    "tn_destroy_lattice": (c_int, [c_void_p]),
+    "tn_lattice_elems": (c_size_t, [c_int, c_int, c_int]),
+    "tn_set_site_tensors": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "tn_fill_random": (c_int, [c_void_p, c_uint64]),
+    "tn_get_site_tensors": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "tn_footprint": (c_int, [c_void_p, c_int, c_int, c_int, POINTER(c_size_t)]),
+    "tn_plan": (c_int, [c_void_p, c_int, c_void_p, c_size_t, POINTER(c_size_t)]),
+    "tn_contract_norm": (c_int, [c_void_p, c_int, c_int, POINTER(tn_scalar)]),
+    "tn_expectation": (c_int, [c_void_p, c_int, c_int, c_int, c_int, POINTER(c_double)]),
+    "tn_energy": (c_int, [c_void_p, c_double, c_double, c_int, POINTER(tn_result)]),
+    "tn_energy_sched": (c_int, [c_void_p, c_double, c_double, c_int, c_int, POINTER(tn_result)]),
+    "tn_batch_create": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int,
+                                POINTER(c_void_p)]),
+    "tn_batch_destroy": (c_int, [c_void_p]),
+    "tn_batch_elems": (c_size_t, [c_void_p]),
+    "tn_batch_set_tensors": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "tn_batch_set_tensors_device": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "tn_batch_fill_random": (c_int, [c_void_p, c_uint64]),
+    "tn_batch_run": (c_int, [c_void_p, c_double, c_void_p]),
+    "tn_batch_result_size": (c_size_t, [c_void_p]),
+    "tn_batch_results_host": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "tn_batch_results_device": (c_int, [c_void_p, POINTER(c_void_p)]),
+    "tn_batch_launch_count": (c_int, [c_void_p, POINTER(c_int64)]),
+    "tn_submit": (c_int, [c_void_p, POINTER(tn_job), POINTER(c_uint64)]),
+    "tn_poll": (c_int, [c_void_p, c_uint64, POINTER(tn_result)]),
+    "tn_wait": (c_int, [c_void_p, c_uint64, c_double, POINTER(tn_result)]),
+    "tn_absorb": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int64, c_void_p]),
+    "tn_status_string": (c_char_p, [c_int]),
+    "tn_last_error": (c_char_p, []),
+    "tn_ctx_set_profiling": (c_int, [c_void_p, c_int]),
+    "tn_ctx_kernel_stats": (c_int, [c_void_p, c_int, POINTER(c_int64), POINTER(c_double), POINTER(c_double),
+                                    POINTER(c_double)]),
+}
+
+_lib = None
+
+
+def lib(build_if_needed: bool = True):
+    """Load libtn (building it first if stale).  Raises if it cannot be loaded."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_needed else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libtn not built at {path}")
+        _lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(_lib, name)
+            f.restype = res
+            f.argtypes = args
+    return _lib
+
+
+class TNError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib().tn_last_error().decode() or lib().tn_status_string(status).decode()
+        super().__init__(f"{where}: {lib().tn_status_string(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def check(status: int, where: str):
+    if status not in (TN_OK,):
+        raise TNError(status, where)
+
+
+def _ptr(x):
+    """Device or host pointer from a torch tensor, numpy array or int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return c_void_p(x)
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data_as(c_void_p)
+    if hasattr(x, "data_ptr"):
+        return c_void_p(x.data_ptr())
+    raise TypeError(type(x))
+
+
+# -------------------------------------------------------------- wrappers
+
+def tn_ctx_create(device: int = 0, budget: int = 0, stream=None):
+    h = c_void_p()
+    st = None
+    if stream is not None:
+        st = c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    check(lib().tn_ctx_create(device, budget, st, byref(h)), "tn_ctx_create")
+    return h
+
+
+def tn_ctx_destroy(ctx):
+    check(lib().tn_ctx_destroy(ctx), "tn_ctx_destroy")
+
+
+def tn_ctx_memory(ctx):
+    u, b = c_size_t(), c_size_t()
+    check(lib().tn_ctx_memory(ctx, byref(u), byref(b)), "tn_ctx_memory")
+    return u.value, b.value
+
+
+def tn_create_lattice(ctx, L: int, W: int, D: int):
+    h = c_void_p()
+    check(lib().tn_create_lattice(ctx, L, W, D, byref(h)), "tn_create_lattice")
+    return h
+
+
+def tn_destroy_lattice(lat):
+    check(lib().tn_destroy_lattice(lat), "tn_destroy_lattice")
+
+
+def tn_lattice_elems(L: int, W: int, D: int) -> int:
+    return int(lib().tn_lattice_elems(L, W, D))
+
+
+def tn_set_site_tensors(lat, host: np.ndarray):
+    host = np.ascontiguousarray(host, dtype=np.float64)
+    check(lib().tn_set_site_tensors(lat, _ptr(host), host.size), "tn_set_site_tensors")
+
+
+def tn_get_site_tensors(lat, n: int) -> np.ndarray:
+    out = np.empty(n)
+    check(lib().tn_get_site_tensors(lat, _ptr(out), n), "tn_get_site_tensors")
+    return out
+
+
+def tn_fill_random(lat, seed: int):
+    check(lib().tn_fill_random(lat, c_uint64(seed)), "tn_fill_random")
+
+
+def tn_footprint(lat, sched: int, prec: int, work: int) -> int:
+    n = c_size_t()
+    check(lib().tn_footprint(lat, sched, prec, work, byref(n)), "tn_footprint")
+    return n.value
+
+
+def tn_plan(lat, sched: int = TN_SCHED_AUTO) -> np.ndarray:
+    n = c_size_t()
+    check(lib().tn_plan(lat, sched, None, 0, byref(n)), "tn_plan")
+    out = np.zeros(n.value, dtype=np.int64)
+    check(lib().tn_plan(lat, sched, _ptr(out), out.size, byref(n)), "tn_plan")
+    return out
+
+
+def tn_contract_norm(lat, prec: int = TN_FP64, sched: int = TN_SCHED_AUTO):
+    s = tn_scalar()
+    check(lib().tn_contract_norm(lat, prec, sched, byref(s)), "tn_contract_norm")
+    return s.mant, s.exp2
+
+
+def tn_expectation(lat, prec: int, op: int, i: int, j: int = 0) -> float:
+    v = c_double()
+    check(lib().tn_expectation(lat, prec, op, i, j, byref(v)), "tn_expectation")
+    return v.value
+
+
+def tn_energy(lat, J: float, h: float, prec: int = TN_FP64, sched: int = TN_SCHED_AUTO,
+              L: int | None = None, W: int | None = None):
+    """Returns (tn_result, sx array, szsz array) when L, W are given, else the result only."""
+    r = tn_result()
+    sx = zz = None
+    if L is not None:
+        nb = L * (W - 1) + W * (L - 1)
+        sx, zz = np.zeros(L * W), np.zeros(max(nb, 1))
+        r.sx = sx.ctypes.data_as(POINTER(c_double))
+        r.szsz = zz.ctypes.data_as(POINTER(c_double))
+    check(lib().tn_energy_sched(lat, J, h, prec, sched, byref(r)), "tn_energy")
+    if L is None:
+        return r
+    return r, sx, zz[:L * (W - 1) + W * (L - 1)]
+
+
+def tn_batch_create(ctx, Ls, Ws, Ds, prec: int, sched: int = TN_SCHED_AUTO, work: int = TN_WORK_ENERGY):
+    Ls, Ws, Ds = (np.ascontiguousarray(v, dtype=np.int32) for v in (Ls, Ws, Ds))
+    h = c_void_p()
+    check(lib().tn_batch_create(ctx, Ls.size, _ptr(Ls), _ptr(Ws), _ptr(Ds), prec, sched, work, byref(h)),
+          "tn_batch_create")
+    return h
+
+
+def tn_batch_destroy(b):
+    check(lib().tn_batch_destroy(b), "tn_batch_destroy")
+
+
+def tn_batch_elems(b) -> int:
+    return int(lib().tn_batch_elems(b))
+
+
+def tn_batch_set_tensors(b, host: np.ndarray):
+    check(lib().tn_batch_set_tensors(b, _ptr(host), host.size), "tn_batch_set_tensors")
+
+
+def tn_batch_set_tensors_device(b, dev, n: int):
+    check(lib().tn_batch_set_tensors_device(b, _ptr(dev), n), "tn_batch_set_tensors_device")
+
+
+def tn_batch_fill_random(b, seed: int):
+    check(lib().tn_batch_fill_random(b, c_uint64(seed)), "tn_batch_fill_random")
+
+
+def tn_batch_run(b, J: float, h: np.ndarray):
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    check(lib().tn_batch_run(b, J, _ptr(h)), "tn_batch_run")
+
+
+def tn_batch_result_size(b) -> int:
+    return int(lib().tn_batch_result_size(b))
+
+
+def tn_batch_results_host(b, out: np.ndarray | None = None) -> np.ndarray:
+    n = tn_batch_result_size(b)
+    if out is None:
+        out = np.empty(n)
+    check(lib().tn_batch_results_host(b, _ptr(out), n), "tn_batch_results_host")
+    return out
+
+
+def tn_batch_results_device(b) -> int:
+    p = c_void_p()
+    check(lib().tn_batch_results_device(b, byref(p)), "tn_batch_results_device")
+    return p.value
+
+
+def tn_batch_launch_count(b) -> int:
+    n = c_int64()
+    check(lib().tn_batch_launch_count(b, byref(n)), "tn_batch_launch_count")
+    return n.value
+
+
+def tn_submit(ctx, L, W, D, prec, J, h, tensors: np.ndarray | None = None, seed: int = 0):
+    job = tn_job(L, W, D, prec, J, h, None, seed)
+    keep = None
+    if tensors is not None:
+        keep = np.ascontiguousarray(tensors, dtype=np.float64)
+        job.tensors = keep.ctypes.data_as(POINTER(c_double))
+    t = c_uint64()
+    st = lib().tn_submit(ctx, byref(job), byref(t))
+    check(st, "tn_submit")
+    return t.value
+
+
+def _result_arrays(L, W):
+    nb = L * (W - 1) + W * (L - 1)
+    r = tn_result()
+    sx, zz = np.zeros(L * W), np.zeros(max(nb, 1))
+    r.sx = sx.ctypes.data_as(POINTER(c_double))
+    r.szsz = zz.ctypes.data_as(POINTER(c_double))
+    return r, sx, zz, nb
+
+
+def tn_poll(ctx, ticket: int, L: int, W: int):
+    """None while not ready, else (tn_result, sx, szsz)."""
+    r, sx, zz, nb = _result_arrays(L, W)
+    st = lib().tn_poll(ctx, c_uint64(ticket), byref(r))
+    if st == TN_NOT_READY:
+        return None
+    check(st, "tn_poll")
+    return r, sx, zz[:nb]
+
+
+def tn_wait(ctx, ticket: int, timeout_s: float, L: int, W: int):
+    r, sx, zz, nb = _result_arrays(L, W)
+    check(lib().tn_wait(ctx, c_uint64(ticket), timeout_s, byref(r)), "tn_wait")
+    return r, sx, zz[:nb]
+
+
+def tn_absorb(dtype: int, x_in, E, out, P: int, K: int, N: int, S: int, stream=None):
+    st = None if stream is None else c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    check(lib().tn_absorb(dtype, _ptr(x_in), _ptr(E), _ptr(out), P, K, N, S, st), "tn_absorb")
+
+
+def tn_ctx_set_profiling(ctx, on: bool):
+    check(lib().tn_ctx_set_profiling(ctx, 1 if on else 0), "tn_ctx_set_profiling")
+
+
+def tn_ctx_kernel_stats(ctx, family: int):
+    n, ms, by, mac = c_int64(), c_double(), c_double(), c_double()
+    check(lib().tn_ctx_kernel_stats(ctx, family, byref(n), byref(ms), byref(by), byref(mac)),
+          "tn_ctx_kernel_stats")
+    return dict(launches=n.value, ms=ms.value, bytes=by.value, macs=mac.value)
+
+
+def plan_steps(words: np.ndarray):
+    """Decode tn_plan's words into (header dict, steps array [n, 9])."""
+    hdr = dict(fmt=int(words[0]), o=int(words[1]), i=int(words[2]), j=int(words[3]),
+               n_steps=int(words[4]), peak=int(words[5]), mac=int(words[6]))
+    steps = words[7:7 + 9 * hdr["n_steps"]].reshape(-1, 9)
+    return hdr, steps

@@ -1,0 +1,128 @@
+"""Host-only checks of the C-ABI library (no kernel is launched here).
+
+* libtn loads and exports every function include/tn.h declares;
+* the planner inside libtn reproduces the oracle's independent planner
+  bit-exactly (partition, orientation, per-step P, K, N, S, bottleneck, MACs);
+* tn_fill_random reproduces the published SplitMix64 definition in inputs.py;
+* argument validation and planning-only contexts behave as documented.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle.planner as planner
+from paper_1908_08553_gb300 import inputs, tn
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "tn.h")
+
+
+def _declared():
+    txt = open(HDR).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = set(re.findall(r"\b(tn_[a-z0-9_]+)\s*\(", txt))
+    return {n for n in names if not n.endswith("_t")}
+
+
+def test_header_symbols_exported():
+    lib = tn.lib()
+    names = _declared()
+    assert len(names) >= 30
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+    # the binding covers the same surface
+    assert names == set(tn.SIGNATURES), sorted(names ^ set(tn.SIGNATURES))
+
+
+@pytest.fixture(scope="module")
+def cpu_ctx():
+    ctx = tn.tn_ctx_create(-1)
+    yield ctx
+    tn.tn_ctx_destroy(ctx)
+
+
+SHAPES = [(1, 1, 2), (1, 5, 2), (5, 1, 3), (2, 2, 1), (3, 3, 2), (4, 4, 2), (4, 10, 2), (10, 4, 3),
+          (5, 7, 3), (7, 5, 2), (8, 8, 2), (8, 8, 3), (9, 10, 3), (10, 10, 3), (12, 12, 2), (6, 6, 4),
+          (12, 11, 2), (16, 16, 2)]
+
+
+@pytest.mark.parametrize("L,W,D", SHAPES)
+def test_planner_bit_exact_vs_oracle(cpu_ctx, L, W, D):
+    lat = tn.tn_create_lattice(cpu_ctx, L, W, D)
+    try:
+        for sched in (tn.TN_SCHED_AUTO, tn.TN_SCHED_ROW, tn.TN_SCHED_COL, tn.TN_SCHED_QUADRANT):
+            hdr, steps = tn.plan_steps(tn.tn_plan(lat, sched))
+            p = planner.plan(L, W, D, sched)
+            assert (hdr["o"], hdr["i"], hdr["j"]) == (p["o"], p["i"], p["j"])
+            assert hdr["peak"] == p["peak"] and hdr["mac"] == p["mac"]
+            ref = np.array([[s["corner"], s["k"], s["c"], s["r"], s["col"], s["P"], s["K"], s["N"], s["S"]]
+                            for s in p["steps"]], dtype=np.int64).reshape(-1, 9)
+            assert np.array_equal(steps, ref)
+            # every site is absorbed exactly once
+            sites = sorted((int(r), int(c)) for r, c in steps[:, 3:5])
+            assert sites == [(r, c) for r in range(L) for c in range(W)]
+    finally:
+        tn.tn_destroy_lattice(lat)
+
+
+@pytest.mark.parametrize("L,W,D", [(4, 4, 2), (8, 8, 2), (3, 5, 3)])
+@pytest.mark.parametrize("seed", [0, 1, 12345, 2 ** 63 + 7])
+def test_fill_random_matches_generator(cpu_ctx, L, W, D, seed):
+    lat = tn.tn_create_lattice(cpu_ctx, L, W, D)
+    try:
+        tn.tn_fill_random(lat, seed)
+        got = tn.tn_get_site_tensors(lat, tn.tn_lattice_elems(L, W, D))
+        assert np.array_equal(got, inputs.random_lattice(L, W, D, seed))
+        assert got.min() >= -1.0 and got.max() < 1.0
+    finally:
+        tn.tn_destroy_lattice(lat)
+
+
+def test_lattice_elems_matches_layout():
+    for L, W, D in SHAPES:
+        assert tn.tn_lattice_elems(L, W, D) == inputs.n_elems(L, W, D)
+    assert tn.tn_lattice_elems(4, 4, 2) == 288
+    assert tn.tn_lattice_elems(12, 12, 2) == 3872
+    assert tn.tn_lattice_elems(8, 8, 3) == 7200
+    assert tn.tn_lattice_elems(0, 4, 2) == 0
+
+
+def test_invalid_arguments(cpu_ctx):
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_create_lattice(cpu_ctx, 0, 4, 2)
+    assert e.value.status == tn.TN_ERR_INVALID
+    with pytest.raises(tn.TNError):
+        tn.tn_create_lattice(cpu_ctx, 4, 4, 5)
+    lat = tn.tn_create_lattice(cpu_ctx, 3, 3, 2)
+    try:
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_set_site_tensors(lat, np.zeros(7))
+        assert e.value.status == tn.TN_ERR_INVALID
+        # planning works without a device, contraction does not
+        assert tn.tn_footprint(lat, tn.TN_SCHED_AUTO, tn.TN_FP32, tn.TN_WORK_ENERGY) > 0
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_contract_norm(lat, tn.TN_FP64)
+        assert e.value.status == tn.TN_ERR_NO_DEVICE
+    finally:
+        tn.tn_destroy_lattice(lat)
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_absorb(1, 0, 0, 0, 1, 16, 16, 1)
+    assert e.value.status == tn.TN_ERR_INVALID
+    assert tn.lib().tn_status_string(tn.TN_ERR_OVER_BUDGET).decode().startswith("footprint")
+
+
+def test_footprint_monotone_in_precision(cpu_ctx):
+    lat = tn.tn_create_lattice(cpu_ctx, 8, 8, 2)
+    try:
+        f64 = tn.tn_footprint(lat, tn.TN_SCHED_AUTO, tn.TN_FP64, tn.TN_WORK_ENERGY)
+        f32 = tn.tn_footprint(lat, tn.TN_SCHED_AUTO, tn.TN_FP32, tn.TN_WORK_ENERGY)
+        nrm = tn.tn_footprint(lat, tn.TN_SCHED_AUTO, tn.TN_FP32, tn.TN_WORK_NORM)
+        row = tn.tn_footprint(lat, tn.TN_SCHED_ROW, tn.TN_FP32, tn.TN_WORK_NORM)
+        assert f64 > f32 > nrm > 0
+        assert row > nrm          # the row scheme's bottleneck is d times the quadrant's
+        # the footprint holds at least the bottleneck tensor in and out (Sec. 4)
+        p = planner.plan(8, 8, 2)
+        assert nrm >= 2 * p["peak"] * 4
+    finally:
+        tn.tn_destroy_lattice(lat)
