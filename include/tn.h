@@ -181,9 +181,10 @@ tn_status tn_batch_fill_random(tn_batch *b, uint64_t batch_seed);
 /* Run the whole batch (asynchronous on the ctx stream).  h holds one field per
  * member; J is shared. */
 tn_status tn_batch_run(tn_batch *b, double J, const double *h);
-/* Per member: 4 + L*W + nb doubles [energy, log2 norm, norm mantissa, norm
- * exponent, <X_k>..., <Z_i Z_j>...] (work = ENERGY) or 4 doubles (NORM),
- * members concatenated.  _size gives the total; _host synchronises and copies;
+/* Per member: 6 + L*W + nb doubles [energy, log2 norm, norm mantissa, norm
+ * exponent, sum_k <X_k>, sum_<ij> <Z_i Z_j>, <X_k>..., <Z_i Z_j>...]
+ * (work = ENERGY) or 6 doubles (NORM), members concatenated.  E at any other
+ * field is -J * [5] - h * [4].  _size gives the total; _host synchronises and copies;
  * _device returns the device pointer of the same array (valid until the next
  * run). */
 size_t tn_batch_result_size(const tn_batch *b);

@@ -96,8 +96,8 @@ tn_status fill_result(const std::vector<double>& r, const tn_batch* b, tn_precis
     out->energy_per_site = r[0] / N;
     out->norm.mant = r[2];
     out->norm.exp2 = (int64_t)r[3];
-    if (out->sx) std::memcpy(out->sx, r.data() + 4, sizeof(double) * N);
-    if (out->szsz) std::memcpy(out->szsz, r.data() + 4 + N, sizeof(double) * nb);
+    if (out->sx) std::memcpy(out->sx, r.data() + kResultHeader, sizeof(double) * N);
+    if (out->szsz) std::memcpy(out->szsz, r.data() + kResultHeader + N, sizeof(double) * nb);
     const Plan& p = b->m[0].pg->plan;
     out->err_bound_est = unit_roundoff(prec) * (double)(2 * N + 4);
     out->precision = (int)prec;
@@ -293,12 +293,12 @@ tn_status tn_expectation(tn_lattice* lat, tn_precision prec, int op, int i, int 
     std::vector<double> r;
     tn_status s = run_single(lat, prec, TN_SCHED_AUTO, TN_WORK_ENERGY, 1.0, 0.0, &r, nullptr);
     if (s != TN_OK) return s;
-    if (op == TN_OP_X) { *out = r[4 + i]; return TN_OK; }
+    if (op == TN_OP_X) { *out = r[kResultHeader + i]; return TN_OK; }
     const int ri = i / W, ci = i % W;
     int bi;
     if (j == i + 1 && ri == j / W) bi = ri * (W - 1) + ci;
     else bi = L * (W - 1) + ri * W + ci;
-    *out = r[4 + N + bi];
+    *out = r[kResultHeader + N + bi];
     return TN_OK;
     TN_GUARD_END
 }

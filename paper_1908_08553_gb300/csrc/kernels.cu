@@ -536,28 +536,36 @@ cudaError_t launch_init(Slot* slots, long long nslots, const ConstOne* ones, int
 // ------------------------------------------------------------ final ------
 
 // <O> = (m_O / m_norm) 2^(X_O - X_norm) in FP64; E = -J sum <zz> - h sum <x>.
+// Output per member: [E, log2 norm, norm mantissa, norm exponent, sum <X>,
+// sum <ZZ>, <X_k>..., <Z_i Z_j>...].
 __global__ void k_final(const FinalTask* __restrict__ tasks, const Slot* __restrict__ slots) {
     const FinalTask& t = tasks[blockIdx.x];
     const Slot& nz = slots[t.norm_slot];
     const double mn = nz.mant;
     const long long Xn = nz.X;
-    double sxx = 0.0, szz = 0.0;
+    double* v = t.out + kResultHeader;
     for (int k = threadIdx.x; k < t.n_sites; k += blockDim.x) {
         const Slot& s = slots[t.sx_slots[k]];
-        t.out[4 + k] = ldexp(s.mant / mn, (int)(s.X - Xn));
+        v[k] = ldexp(s.mant / mn, (int)(s.X - Xn));
     }
     for (int k = threadIdx.x; k < t.n_bonds; k += blockDim.x) {
         const Slot& s = slots[t.zz_slots[k]];
-        t.out[4 + t.n_sites + k] = ldexp(s.mant / mn, (int)(s.X - Xn));
+        v[t.n_sites + k] = ldexp(s.mant / mn, (int)(s.X - Xn));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 0; k < t.n_sites; ++k) sxx += t.out[4 + k];
-        for (int k = 0; k < t.n_bonds; ++k) szz += t.out[4 + t.n_sites + k];
+        double sxx = 0.0, szz = 0.0;
+        for (int k = 0; k < t.n_sites; ++k) sxx += v[k];
+        for (int k = 0; k < t.n_bonds; ++k) szz += v[t.n_sites + k];
         t.out[0] = -t.J * szz - t.h * sxx;
+        // canonical form: mantissa in [0.5, 1), exponent integral
+        int e = 0;
+        const double m = (mn != 0.0 && isfinite(mn)) ? frexp(mn, &e) : mn;
         t.out[1] = log2(fabs(mn)) + (double)Xn;
-        t.out[2] = mn;
-        t.out[3] = (double)Xn;
+        t.out[2] = m;
+        t.out[3] = (double)(Xn + e);
+        t.out[4] = sxx;
+        t.out[5] = szz;
     }
 }
 

@@ -61,7 +61,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         mb.slot_base = nslots;
         nslots += mb.pg->n_slots;
         mb.res_off = nres;
-        mb.res_elems = 4 + (int64_t)mb.pg->sx_slot.size() + (int64_t)mb.pg->zz_slot.size();
+        mb.res_elems = kResultHeader + (int64_t)mb.pg->sx_slot.size() + (int64_t)mb.pg->zz_slot.size();
         nres += mb.res_elems;
     }
     lay.nin = nin;
@@ -121,8 +121,11 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         part_cur += n;
         return p;
     };
+    // Tasks of one launch are packed back to back (the kernel indexes them as
+    // an array of the task type); only the start of each launch is aligned.
+    auto align_group = [&]() { tasks.resize((tasks.size() + 63) / 64 * 64); };
     auto append = [&](const void* src, size_t n) -> size_t {
-        size_t off = (tasks.size() + 15) / 16 * 16;
+        const size_t off = tasks.size();
         tasks.resize(off + n);
         std::memcpy(tasks.data() + off, src, n);
         return off;
@@ -137,6 +140,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         const auto& refs = kv.second;
         L.ntasks = (int)refs.size();
         long long tile = 0;
+        align_group();
         size_t first = SIZE_MAX;
         for (const OpRef& r : refs) {
             const Member& mb = b->m[r.member];

@@ -74,10 +74,14 @@ struct SiteMatTask {
     int K, N;
 };
 
+// Result header per member: E, log2 norm, norm mantissa, norm exponent,
+// sum <X>, sum <ZZ>; then <X_k> and <Z_i Z_j>.
+constexpr int kResultHeader = 6;
+
 struct FinalTask {
     const int* sx_slots;  // n_sites
     const int* zz_slots;  // n_bonds
-    double* out;          // 4 + n_sites + n_bonds
+    double* out;          // kResultHeader + n_sites + n_bonds
     double J, h;
     int norm_slot;
     int n_sites, n_bonds;
