@@ -223,6 +223,21 @@ tn_status tn_wait(tn_ctx *ctx, uint64_t ticket, double timeout_s, tn_result *out
 tn_status tn_absorb(int dtype, const void *in, const void *E, void *out,
                     int64_t P, int32_t K, int32_t N, int64_t S, void *stream);
 
+/* The same absorption fused with a dot product against a tensor of the output
+ * shape -- the last step of every observable of Sec. 5, where the state with
+ * an operator inserted meets its environment:
+ *   *result = sum_{p,n,s} (sum_k in[p][k][s] E[k][n]) * adj[p][n][s]
+ * in, E, adj: device arrays of dtype 0 = FP64 / 1 = FP32 (C order, shapes as
+ * tn_absorb, adj [P][N][S]); result: device pointer to one double.  Each tile
+ * of 256 outer positions adds its products into one FP64 partial; the last
+ * tile sums the partials in index order, so the result is bit-reproducible.
+ * The partials (8 bytes per tile, plus a 16-byte counter) are scratch the call
+ * takes with cudaMallocAsync on `stream` and returns with cudaFreeAsync.
+ * Returns TN_ERR_INVALID for bad sizes or NULL pointers, TN_ERR_OOM if the
+ * scratch cannot be allocated. */
+tn_status tn_absorb_dot(int dtype, const void *in, const void *E, const void *adj,
+                        int64_t P, int32_t K, int32_t N, int64_t S, double *result, void *stream);
+
 /* ------------------------------------------------------------ misc -------- */
 
 const char *tn_status_string(tn_status s);

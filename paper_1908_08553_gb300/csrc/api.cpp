@@ -1,5 +1,6 @@
 // extern "C" entry points of libtn (declared in include/tn.h).  Every function
 // catches exceptions and returns a tn_status; no exception crosses the ABI.
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -392,6 +393,27 @@ tn_status tn_absorb(int dtype, const void* in, const void* E, void* out, int64_t
     if (!absorb_has_fast_path(K, N)) { set_error("K, N must be in {1, 4, 16} or {1, 9, 81}"); return TN_ERR_INVALID; }
     return cuda_status(launch_absorb_plain(dtype, in, E, out, P, K, N, S, static_cast<cudaStream_t>(stream)),
                        "absorb launch");
+}
+
+tn_status tn_absorb_dot(int dtype, const void* in, const void* E, const void* adj, int64_t P, int32_t K,
+                        int32_t N, int64_t S, double* result, void* stream) {
+    if ((dtype != 0 && dtype != 1) || !in || !E || !adj || !result || P <= 0 || K <= 0 || N <= 0 || S <= 0) {
+        set_error("bad absorb-dot arguments");
+        return TN_ERR_INVALID;
+    }
+    if (!absorb_has_fast_path(K, N)) { set_error("K, N must be in {1, 4, 16} or {1, 9, 81}"); return TN_ERR_INVALID; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long tiles = absorb_tiles(P, S, K, N);
+    if (tiles > INT32_MAX) { set_error("too many tiles"); return TN_ERR_INVALID; }
+    const size_t bytes = 16 + (size_t)tiles * sizeof(double);
+    void* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, bytes, st);
+    if (e != cudaSuccess) return cuda_status(e, "scratch allocation");
+    e = cudaMemsetAsync(scratch, 0, 16, st);
+    if (e == cudaSuccess) e = launch_absorb_dot_plain(dtype, in, E, adj, P, K, N, S, result, scratch, st);
+    const cudaError_t ef = cudaFreeAsync(scratch, st);
+    if (e == cudaSuccess) e = ef;
+    return cuda_status(e, "absorb-dot launch");
 }
 
 // ---------------------------------------------------------------- misc --

@@ -85,13 +85,13 @@ __device__ __forceinline__ void record_max(Slot* s, double m) {
 
 // Deterministic completion of a per-tile FP64 sum: every tile writes its
 // partial; the last tile to arrive sums all partials in index order.
-__device__ void finish_sum(double part, double* partial, int ntiles, long long local,
-                           Slot* out, long long X, double* red) {
+__device__ void finish_sum_to(double part, double* partial, int ntiles, long long local,
+                              unsigned* count, double* out, long long* outX, long long X, double* red) {
     __shared__ int is_last;
     if (threadIdx.x == 0) {
         partial[local] = part;
         __threadfence();
-        const unsigned prev = atomicAdd(&out->count, 1u);
+        const unsigned prev = atomicAdd(count, 1u);
         is_last = (prev == (unsigned)(ntiles - 1));
     }
     __syncthreads();
@@ -101,9 +101,14 @@ __device__ void finish_sum(double part, double* partial, int ntiles, long long l
     for (int k = threadIdx.x; k < ntiles; k += blockDim.x) acc += __ldcg(partial + k);
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) {
-        out->mant = acc;
-        out->X = X;
+        *out = acc;
+        if (outX) *outX = X;
     }
+}
+
+__device__ __forceinline__ void finish_sum(double part, double* partial, int ntiles, long long local,
+                                           Slot* out, long long X, double* red) {
+    finish_sum_to(part, partial, ntiles, local, &out->count, &out->mant, &out->X, X, red);
 }
 
 }  // namespace
@@ -111,7 +116,8 @@ __device__ void finish_sum(double part, double* partial, int ntiles, long long l
 // ------------------------------------------------------------ absorption --
 
 // One tile (kAbsorbThreads outer positions (p, s)) of a site absorption.
-// MODE 0: plain (no slots, tn_absorb); 1: absorb with rescale; 2: absorb-dot.
+// MODE 0: plain (no slots, tn_absorb); 1: absorb with rescale; 2: absorb-dot;
+// 3: plain absorb-dot (no slots, result into t.out, counter in t.counter).
 template <typename T, int K, int N, int MODE>
 __device__ __forceinline__ void absorb_tile(const AbsorbTask& t, long long local,
                                             Slot* __restrict__ slots, T* Es, double* red) {
@@ -120,9 +126,11 @@ __device__ __forceinline__ void absorb_tile(const AbsorbTask& t, long long local
         const int k = idx / N, n = idx - k * N;
         Es[idx] = t.transE ? E[n * K + k] : E[idx];
     }
+    // Only modes 1 and 2 have rescaling slots; modes 0 and 3 get slots == nullptr.
+    constexpr bool kSlots = (MODE == 1 || MODE == 2);
     int e_in = 0, e_adj = 0;
     T sc_in = T(1), sc_adj = T(1);
-    if (MODE >= 1) {
+    if (kSlots) {
         e_in = slot_shift(&slots[t.slot_in]);
         sc_in = pow2<T>(-e_in);
     }
@@ -173,6 +181,9 @@ __device__ __forceinline__ void absorb_tile(const AbsorbTask& t, long long local
         const double part = block_sum(ldot, red);
         const long long X = slots[t.slot_in].X + e_in + slots[t.slot_E].X + slots[t.slot_adj].X + e_adj;
         finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_out], X, red);
+    } else if (MODE == 3) {
+        const double part = block_sum(ldot, red);
+        finish_sum_to(part, t.partial, t.ntiles, local, t.counter, static_cast<double*>(t.out), nullptr, 0, red);
     }
 }
 
@@ -186,13 +197,13 @@ k_absorb(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ sl
     absorb_tile<T, K, N, MODE>(t, tile - t.tile0, slots, reinterpret_cast<T*>(smem_raw), red);
 }
 
-// Single task passed by value (the plain kernel entry point allocates nothing).
-template <typename T, int K, int N>
+// Single task passed by value (the kernel-level entry points).
+template <typename T, int K, int N, int MODE>
 __global__ void __launch_bounds__(kAbsorbThreads)
 k_absorb_one(const __grid_constant__ AbsorbTask t) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
-    absorb_tile<T, K, N, 0>(t, (long long)blockIdx.x, nullptr, reinterpret_cast<T*>(smem_raw), red);
+    absorb_tile<T, K, N, MODE>(t, (long long)blockIdx.x, nullptr, reinterpret_cast<T*>(smem_raw), red);
 }
 
 // Generic sizes (D = 4 and anything outside the unrolled set): E read from
@@ -207,7 +218,7 @@ k_absorb_generic(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restr
     const T* E = static_cast<const T*>(t.E);
     int e_in = 0, e_adj = 0;
     T sc_in = T(1), sc_adj = T(1);
-    if (MODE >= 1) { e_in = slot_shift(&slots[t.slot_in]); sc_in = pow2<T>(-e_in); }
+    if (MODE == 1 || MODE == 2) { e_in = slot_shift(&slots[t.slot_in]); sc_in = pow2<T>(-e_in); }
     if (MODE == 2) { e_adj = slot_shift(&slots[t.slot_adj]); sc_adj = pow2<T>(-e_adj); }
     const long long local = tile - t.tile0;
     const long long S = t.S;
@@ -578,13 +589,13 @@ cudaError_t launch_final(const FinalTask* tasks, int ntasks, const Slot* slots, 
 // ---------------------------------------------------- plain absorption ---
 
 namespace {
-template <typename T>
+template <typename T, int MODE>
 cudaError_t absorb_plain(const AbsorbTask& t, long long nblocks, cudaStream_t st) {
     const int K = t.K, N = t.N;
     const size_t smem = (size_t)K * N * sizeof(T);
 #define TN_PLAIN_CASE(KK, NN)                                                               \
     if (K == KK && N == NN) {                                                               \
-        auto fn = k_absorb_one<T, KK, NN>;                                                  \
+        auto fn = k_absorb_one<T, KK, NN, MODE>;                                            \
         if (smem > 48 * 1024)                                                               \
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         fn<<<(unsigned)nblocks, kAbsorbThreads, smem, st>>>(t);                             \
@@ -611,7 +622,22 @@ cudaError_t launch_absorb_plain(int dt, const void* in, const void* E, void* out
     const long long nb = absorb_tiles(P, S, K, N);
     t.ntiles = (int)nb;
     if (nb <= 0) return cudaSuccess;
-    return dt == 0 ? absorb_plain<double>(t, nb, st) : absorb_plain<float>(t, nb, st);
+    return dt == 0 ? absorb_plain<double, 0>(t, nb, st) : absorb_plain<float, 0>(t, nb, st);
+}
+
+cudaError_t launch_absorb_dot_plain(int dt, const void* in, const void* E, const void* adj, long long P,
+                                    int K, int N, long long S, double* result, void* scratch,
+                                    cudaStream_t st) {
+    AbsorbTask t{};
+    t.in = in; t.E = E; t.adj = adj; t.out = result;
+    t.P = P; t.S = S; t.K = K; t.N = N;
+    t.counter = static_cast<unsigned*>(scratch);
+    t.partial = reinterpret_cast<double*>(static_cast<char*>(scratch) + 16);
+    t.tile0 = 0;
+    const long long nb = absorb_tiles(P, S, K, N);
+    t.ntiles = (int)nb;
+    if (nb <= 0) return cudaSuccess;
+    return dt == 0 ? absorb_plain<double, 3>(t, nb, st) : absorb_plain<float, 3>(t, nb, st);
 }
 
 }  // namespace tn

@@ -32,6 +32,7 @@ struct AbsorbTask {
     void* out;            // unused in dot mode
     const void* adj;      // dot mode: adjoint tensor [P][N][S]
     double* partial;      // dot mode: one FP64 partial per tile
+    unsigned* counter;    // plain dot mode: tile arrival counter (zeroed before launch)
     long long P, S;
     long long tile0;      // first global tile of this task
     int K, N;
@@ -106,6 +107,11 @@ cudaError_t launch_init(Slot* slots, long long nslots, const ConstOne* ones, int
 cudaError_t launch_final(const FinalTask* tasks, int ntasks, const Slot* slots, cudaStream_t st);
 cudaError_t launch_absorb_plain(int dt, const void* in, const void* E, void* out, long long P,
                                 int K, int N, long long S, cudaStream_t st);
+// <absorb(in, E), adj> into *result (device).  scratch: 16 B counter header
+// followed by one double per tile; the caller zeroes the header first.
+cudaError_t launch_absorb_dot_plain(int dt, const void* in, const void* E, const void* adj, long long P,
+                                    int K, int N, long long S, double* result, void* scratch,
+                                    cudaStream_t st);
 
 // Tiles per task, fixed by shape only (bit-identical results alone or batched).
 constexpr int kAbsorbThreads = 256;

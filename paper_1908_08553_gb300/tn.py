@@ -73,6 +73,8 @@ SIGNATURES = {
     "tn_poll": (c_int, [c_void_p, c_uint64, POINTER(tn_result)]),
     "tn_wait": (c_int, [c_void_p, c_uint64, c_double, POINTER(tn_result)]),
     "tn_absorb": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int64, c_void_p]),
+    "tn_absorb_dot": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int64, c_void_p,
+                              c_void_p]),
     "tn_status_string": (c_char_p, [c_int]),
     "tn_last_error": (c_char_p, []),
     "tn_ctx_set_profiling": (c_int, [c_void_p, c_int]),
@@ -312,6 +314,12 @@ def tn_wait(ctx, ticket: int, timeout_s: float, L: int, W: int):
 def tn_absorb(dtype: int, x_in, E, out, P: int, K: int, N: int, S: int, stream=None):
     st = None if stream is None else c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
     check(lib().tn_absorb(dtype, _ptr(x_in), _ptr(E), _ptr(out), P, K, N, S, st), "tn_absorb")
+
+
+def tn_absorb_dot(dtype: int, x_in, E, adj, P: int, K: int, N: int, S: int, result, stream=None):
+    st = None if stream is None else c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    check(lib().tn_absorb_dot(dtype, _ptr(x_in), _ptr(E), _ptr(adj), P, K, N, S, _ptr(result), st),
+          "tn_absorb_dot")
 
 
 def tn_ctx_set_profiling(ctx, on: bool):

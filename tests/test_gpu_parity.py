@@ -219,3 +219,27 @@ def test_tn_absorb_matches_reference(K, N, P, S, dtype):
     torch.cuda.synchronize()
     tol = 1e-13 if dtype == 0 else 2e-6 * K
     assert torch.allclose(out.double().cpu(), ref, atol=tol, rtol=0)
+
+
+@pytest.mark.parametrize("K,N,P,S", [(16, 16, 7, 1000), (4, 16, 1, 4096), (16, 4, 33, 1),
+                                     (81, 81, 3, 300), (9, 81, 5, 81), (1, 1, 5000, 3)])
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_tn_absorb_dot_matches_reference(K, N, P, S, dtype):
+    import torch
+    tdt = torch.float64 if dtype == 0 else torch.float32
+    g = torch.Generator().manual_seed(3 * K + N + P + S)
+    x = torch.rand(P, K, S, generator=g, dtype=torch.float64) * 2 - 1
+    E = torch.rand(K, N, generator=g, dtype=torch.float64) * 2 - 1
+    adj = torch.rand(P, N, S, generator=g, dtype=torch.float64) * 2 - 1
+    ref = float(torch.einsum("pks,kn,pns->", x, E, adj))
+    scale = float(torch.einsum("pks,kn,pns->", x.abs(), E.abs(), adj.abs()))
+    xd, Ed, ad = x.to(tdt).cuda(), E.to(tdt).cuda(), adj.to(tdt).cuda()
+    res = torch.zeros(2, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    tn.tn_absorb_dot(dtype, xd, Ed, ad, P, K, N, S, res[0:1], st)
+    tn.tn_absorb_dot(dtype, xd, Ed, ad, P, K, N, S, res[1:2], st)
+    torch.cuda.synchronize()
+    tol = 1e-13 if dtype == 0 else 1e-6
+    got = res.cpu().numpy()
+    assert abs(got[0] - ref) <= tol * scale
+    assert got[0] == got[1]          # deterministic finish of the tile partials
