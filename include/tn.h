@@ -238,6 +238,29 @@ tn_status tn_absorb(int dtype, const void *in, const void *E, void *out,
 tn_status tn_absorb_dot(int dtype, const void *in, const void *E, const void *adj,
                         int64_t P, int32_t K, int32_t N, int64_t S, double *result, void *stream);
 
+/* tn_absorb_dot without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not call the CUDA allocator
+ * where they call us -- a latency-critical loop (cudaMalloc / cudaFree may
+ * synchronise the whole device), or a process whose device memory is already
+ * held by another allocator, so a new allocation could fail.  Arguments,
+ * result and errors are those of tn_absorb_dot; the caller still owns every
+ * input and the output.
+ *   Scratch: one fixed array of 16 + 8 * 65536 bytes (about 512 KiB) compiled
+ *   into the library; every GPU that loads libtn holds it until the process
+ *   exits.  Its size caps the problem: P * S <= 16,777,216 (65,536 tiles of
+ *   256 outer positions); larger calls return TN_ERR_INVALID without touching
+ *   the GPU.
+ *   Set-up: the first call on a device (the calling thread's current device,
+ *   which `stream` must belong to) looks up the array's device address; make
+ *   that first call before any stream capture.
+ *   Sharing: every call on a device uses the same array and the array keeps
+ *   the last call's contents; each call clears the part that must start at
+ *   zero.  Calls whose executions overlap on the GPU (different streams, no
+ *   ordering between them) race on the array and give wrong results. */
+tn_status tn_absorb_dot_noalloc(int dtype, const void *in, const void *E, const void *adj,
+                                int64_t P, int32_t K, int32_t N, int64_t S, double *result,
+                                void *stream);
+
 /* ------------------------------------------------------------ misc -------- */
 
 const char *tn_status_string(tn_status s);

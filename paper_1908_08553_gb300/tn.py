@@ -75,6 +75,8 @@ SIGNATURES = {
     "tn_absorb": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int64, c_void_p]),
     "tn_absorb_dot": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int64, c_void_p,
                               c_void_p]),
+    "tn_absorb_dot_noalloc": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int64,
+                                      c_void_p, c_void_p]),
     "tn_status_string": (c_char_p, [c_int]),
     "tn_last_error": (c_char_p, []),
     "tn_ctx_set_profiling": (c_int, [c_void_p, c_int]),
@@ -320,6 +322,13 @@ def tn_absorb_dot(dtype: int, x_in, E, adj, P: int, K: int, N: int, S: int, resu
     st = None if stream is None else c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
     check(lib().tn_absorb_dot(dtype, _ptr(x_in), _ptr(E), _ptr(adj), P, K, N, S, _ptr(result), st),
           "tn_absorb_dot")
+
+
+def tn_absorb_dot_noalloc(dtype: int, x_in, E, adj, P: int, K: int, N: int, S: int, result, stream=None):
+    """tn_absorb_dot with its scratch in a fixed array inside the library (no allocation)."""
+    st = None if stream is None else c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    check(lib().tn_absorb_dot_noalloc(dtype, _ptr(x_in), _ptr(E), _ptr(adj), P, K, N, S, _ptr(result), st),
+          "tn_absorb_dot_noalloc")
 
 
 def tn_ctx_set_profiling(ctx, on: bool):
