@@ -24,12 +24,6 @@ uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-void fill_uniform(uint64_t seed, double* out, size_t n) {
-    for (size_t k = 0; k < n; ++k) {
-        const uint64_t z = mix64(seed + (uint64_t)(k + 1) * kGamma);
-        out[k] = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
-    }
-}
 
 size_t lattice_elems(int L, int W, int D) {
     size_t n = 0;
@@ -51,6 +45,40 @@ double unit_roundoff(tn_precision p) {
         default: return 0x1.0p-16;
     }
 }
+
+}  // namespace
+
+namespace tn {
+
+// Counter-based SplitMix64 fill, uniform on [-1, 1) (definition in tn.h).
+void fill_uniform(uint64_t seed, double* out, size_t n) {
+    for (size_t k = 0; k < n; ++k) {
+        const uint64_t z = mix64(seed + (uint64_t)(k + 1) * kGamma);
+        out[k] = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+    }
+}
+
+// tn_result from one member's result array [header | <X_k> | <Z_i Z_j>].
+tn_status result_from_array(const double* r, int L, int W, tn_precision prec, const Plan& p, tn_result* out) {
+    const int N = L * W, nb = L * (W - 1) + W * (L - 1);
+    out->energy = r[0];
+    out->energy_per_site = r[0] / N;
+    out->norm.mant = r[2];
+    out->norm.exp2 = (int64_t)r[3];
+    if (out->sx) std::memcpy(out->sx, r + kResultHeader, sizeof(double) * N);
+    if (out->szsz) std::memcpy(out->szsz, r + kResultHeader + N, sizeof(double) * nb);
+    out->err_bound_est = unit_roundoff(prec) * (double)(2 * N + 4);
+    out->precision = (int)prec;
+    out->schedule_o = p.o;
+    out->schedule_i = p.i;
+    out->schedule_j = p.j;
+    if (!std::isfinite(r[0]) || !(r[2] != 0.0)) { set_error("non-finite result or zero norm"); return TN_ERR_NUMERIC; }
+    return TN_OK;
+}
+
+}  // namespace tn
+
+namespace {
 
 #define TN_GUARD_BEGIN try {
 #define TN_GUARD_END                                                    \
@@ -92,21 +120,7 @@ tn_status run_single(tn_lattice* lat, tn_precision prec, tn_schedule sched, tn_w
 
 tn_status fill_result(const std::vector<double>& r, const tn_batch* b, tn_precision prec, int L, int W,
                       tn_result* out) {
-    const int N = L * W, nb = L * (W - 1) + W * (L - 1);
-    out->energy = r[0];
-    out->energy_per_site = r[0] / N;
-    out->norm.mant = r[2];
-    out->norm.exp2 = (int64_t)r[3];
-    if (out->sx) std::memcpy(out->sx, r.data() + kResultHeader, sizeof(double) * N);
-    if (out->szsz) std::memcpy(out->szsz, r.data() + kResultHeader + N, sizeof(double) * nb);
-    const Plan& p = b->m[0].pg->plan;
-    out->err_bound_est = unit_roundoff(prec) * (double)(2 * N + 4);
-    out->precision = (int)prec;
-    out->schedule_o = p.o;
-    out->schedule_i = p.i;
-    out->schedule_j = p.j;
-    if (!std::isfinite(r[0]) || !(r[2] != 0.0)) { set_error("non-finite result or zero norm"); return TN_ERR_NUMERIC; }
-    return TN_OK;
+    return result_from_array(r.data(), L, W, prec, b->m[0].pg->plan, out);
 }
 
 }  // namespace

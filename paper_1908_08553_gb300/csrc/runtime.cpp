@@ -274,9 +274,26 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
 
 }  // namespace
 
+std::shared_ptr<const Program> program_cached(int L, int W, int D, tn_schedule sched, tn_precision prec,
+                                              tn_work work) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, int, int>, std::shared_ptr<const Program>> cache;
+    const auto key = std::make_tuple(L, W, D, (int)sched, (int)(prec == TN_FP64 ? 0 : 1), (int)work);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    auto pg = program_build(L, W, D, sched, prec, work);
+    std::lock_guard<std::mutex> g(mu);
+    return cache.emplace(key, pg).first->second;
+}
+
 tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int* D,
                        tn_precision prec, tn_schedule sched, tn_work work, bool alloc,
-                       tn_batch** out, size_t* bytes) {
+                       tn_batch** out, size_t* bytes, const BatchOpts* opts) {
+    const BatchOpts defaults;
+    if (!opts) opts = &defaults;
     if (n <= 0 || !L || !W || !D) { set_error("empty batch"); return TN_ERR_INVALID; }
     if (prec < TN_FP64 || prec > TN_BF16X3 || sched < TN_SCHED_AUTO || sched > TN_SCHED_QUADRANT ||
         work < TN_WORK_NORM || work > TN_WORK_ENERGY) {
@@ -292,21 +309,17 @@ tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int
     b->dt = prec == TN_FP64 ? 0 : 1;
     b->work = work;
     b->sched = sched;
-    // programs are shared between members of the same shape
-    std::map<std::tuple<int, int, int>, std::shared_ptr<const Program>> cache;
+    // programs are shared between members (and batches) of the same shape
     for (int k = 0; k < n; ++k) {
-        auto key = std::make_tuple(L[k], W[k], D[k]);
-        auto it = cache.find(key);
-        if (it == cache.end()) {
-            try {
-                it = cache.emplace(key, program_build(L[k], W[k], D[k], sched, prec, work)).first;
-            } catch (const std::exception& e) {
-                set_error(e.what());
-                return TN_ERR_INVALID;
-            }
+        std::shared_ptr<const Program> pg;
+        try {
+            pg = program_cached(L[k], W[k], D[k], sched, prec, work);
+        } catch (const std::exception& e) {
+            set_error(e.what());
+            return TN_ERR_INVALID;
         }
         Member mb;
-        mb.pg = it->second;
+        mb.pg = pg;
         mb.L = L[k]; mb.W = W[k]; mb.D = D[k];
         b->m.push_back(mb);
     }
@@ -323,24 +336,35 @@ tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int
         }
     } while (!ctx->used.compare_exchange_weak(cur, cur + need));
     cudaSetDevice(ctx->device);
-    cudaError_t e = cudaMalloc(&b->buf, need);
+    b->stream = opts->stream ? opts->stream : ctx->stream;
+    b->async_alloc = opts->async_alloc;
+    b->use_graph = opts->use_graph;
+    cudaError_t e = b->async_alloc ? cudaMallocAsync(reinterpret_cast<void**>(&b->buf), need, b->stream)
+                                   : cudaMalloc(&b->buf, need);
     if (e != cudaSuccess) {
+        b->buf = nullptr;
         ctx->used -= need;
-        return cuda_status(e, "cudaMalloc");
+        return cuda_status(e, "device allocation");
     }
-    std::vector<char> tasks;
     std::vector<int> ints;
     std::vector<ConstOne> ones;
-    materialize(b.get(), b->buf, &tasks, &ints, &ones);
-    b->stream = ctx->stream;
-    e = cudaMemcpy(b->buf + b->lay.tasks_off, tasks.data(), tasks.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !ints.empty())
-        e = cudaMemcpy(b->buf + b->lay.ints_off, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !ones.empty())
-        e = cudaMemcpy(b->buf + b->lay.ones_off, ones.data(), ones.size() * sizeof(ConstOne), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(b->buf + b->lay.in_off, 0, (size_t)b->lay.nin * 8);
+    materialize(b.get(), b->buf, &b->h_tasks, &ints, &ones);
+    b->h_ints.swap(ints);
+    b->h_ones.swap(ones);
+    // stream-ordered uploads; the host copies live in the batch until it is destroyed
+    e = cudaMemcpyAsync(b->buf + b->lay.tasks_off, b->h_tasks.data(), b->h_tasks.size(), cudaMemcpyHostToDevice,
+                        b->stream);
+    if (e == cudaSuccess && !b->h_ints.empty())
+        e = cudaMemcpyAsync(b->buf + b->lay.ints_off, b->h_ints.data(), b->h_ints.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !b->h_ones.empty())
+        e = cudaMemcpyAsync(b->buf + b->lay.ones_off, b->h_ones.data(), b->h_ones.size() * sizeof(ConstOne),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->buf + b->lay.in_off, 0, (size_t)b->lay.nin * 8, b->stream);
+    if (e == cudaSuccess && !b->async_alloc) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
-        cudaFree(b->buf);
+        if (b->async_alloc) cudaFreeAsync(b->buf, b->stream); else cudaFree(b->buf);
+        b->buf = nullptr;
         ctx->used -= need;
         return cuda_status(e, "batch upload");
     }
@@ -353,7 +377,8 @@ void batch_destroy(tn_batch* b) {
     if (!b) return;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->buf) {
-        cudaFree(b->buf);
+        if (b->async_alloc) cudaFreeAsync(b->buf, b->stream);
+        else cudaFree(b->buf);
         b->ctx->used -= b->lay.total;
     }
     delete b;

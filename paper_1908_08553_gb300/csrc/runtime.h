@@ -82,7 +82,10 @@ struct tn_batch {
     cudaGraphExec_t gexec = nullptr;
     bool use_graph = true;
     cudaStream_t stream = nullptr;    // ctx stream unless the server assigns one
-    double last_J = 0;
+    bool async_alloc = false;         // buffer from the stream-ordered pool (served batches)
+    std::vector<char> h_tasks;        // host copies of the uploaded tables
+    std::vector<int> h_ints;
+    std::vector<tn::ConstOne> h_ones;
 };
 
 struct tn_lattice {
@@ -93,9 +96,16 @@ struct tn_lattice {
 };
 
 namespace tn {
+struct BatchOpts {
+    cudaStream_t stream = nullptr;   // default: the context's stream
+    bool async_alloc = false;        // cudaMallocAsync / cudaFreeAsync on that stream
+    bool use_graph = true;           // capture the launch sequence on the first run
+};
 tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int* D,
                        tn_precision prec, tn_schedule sched, tn_work work, bool alloc,
-                       tn_batch** out, size_t* bytes);
+                       tn_batch** out, size_t* bytes, const BatchOpts* opts = nullptr);
+std::shared_ptr<const Program> program_cached(int L, int W, int D, tn_schedule sched, tn_precision prec,
+                                              tn_work work);
 tn_status batch_run(tn_batch* b, cudaStream_t st);
 void batch_destroy(tn_batch* b);
 tn_status cuda_status(cudaError_t e, const char* what);

@@ -126,3 +126,9 @@ def test_footprint_monotone_in_precision(cpu_ctx):
         assert nrm >= 2 * p["peak"] * 4
     finally:
         tn.tn_destroy_lattice(lat)
+
+
+def test_submit_needs_a_device(cpu_ctx):
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_submit(cpu_ctx, 4, 4, 2, tn.TN_FP32, 1.0, 3.04, seed=1)
+    assert e.value.status == tn.TN_ERR_NO_DEVICE
