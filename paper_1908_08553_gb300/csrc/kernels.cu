@@ -206,6 +206,156 @@ k_absorb_one(const __grid_constant__ AbsorbTask t) {
     absorb_tile<T, K, N, MODE>(t, (long long)blockIdx.x, nullptr, reinterpret_cast<T*>(smem_raw), red);
 }
 
+// ---- v2 (FP32, K, N in {1, 4, 16}): four outer positions per thread -------
+//
+// Each thread owns a group of 4 outer positions: 4 consecutive s of one p when
+// S % 4 == 0 (ALONG_P = false), or 4 consecutive p when S == 1 (ALONG_P =
+// true).  All K input vectors of the group are loaded (16-byte loads) before
+// the first FMA, so a thread has K loads in flight; E rows are read from
+// shared memory as 16-byte broadcasts, one per 16 FMAs; outputs leave as
+// 16-byte stores.  128 threads per block, 512 outer positions per tile.
+constexpr int kV2Threads = 128;
+
+template <int K, int N, int MODE, bool ALONG_P>
+__global__ void __launch_bounds__(kV2Threads, 3)
+k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+    __shared__ __align__(16) float Es[K * N];
+    __shared__ double red[32];
+    const long long tile = blockIdx.x;
+    const AbsorbTask& t = tasks[find_task(tasks, ntasks, tile)];
+    const long long local = tile - t.tile0;
+    const float* E = static_cast<const float*>(t.E);
+    for (int idx = threadIdx.x; idx < K * N; idx += blockDim.x) {
+        const int k = idx / N, n = idx - k * N;
+        Es[idx] = t.transE ? E[n * K + k] : E[idx];
+    }
+    const int e_in = slot_shift(&slots[t.slot_in]);
+    const float sc_in = pow2<float>(-e_in);
+    int e_adj = 0;
+    float sc_adj = 1.0f;
+    if (MODE == 2) {
+        e_adj = slot_shift(&slots[t.slot_adj]);
+        sc_adj = pow2<float>(-e_adj);
+    }
+    __syncthreads();
+    const long long S = t.S;
+    const long long ngroups = ALONG_P ? t.P / 4 : t.P * (S / 4);
+    const long long g = local * kV2Threads + threadIdx.x;
+    float lmax = 0.0f;
+    double ldot = 0.0;
+    if (g < ngroups) {
+        long long p, s;
+        if (ALONG_P) { p = 4 * g; s = 0; }
+        else { const long long sq = S / 4; p = g / sq; s = (g - p * sq) * 4; }
+        const float* in = static_cast<const float*>(t.in);
+        float x[4][K];
+        if (!ALONG_P) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float4 v = __ldg(reinterpret_cast<const float4*>(in + (p * K + k) * S + s));
+                x[0][k] = v.x; x[1][k] = v.y; x[2][k] = v.z; x[3][k] = v.w;
+            }
+        } else if (K == 1) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(in + p));
+            x[0][0] = v.x; x[1][0] = v.y; x[2][0] = v.z; x[3][0] = v.w;
+        } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+#pragma unroll
+                for (int kq = 0; kq < K / 4; ++kq) {
+                    const float4 w = __ldg(reinterpret_cast<const float4*>(in + (p + v) * K + 4 * kq));
+                    x[v][4 * kq] = w.x; x[v][4 * kq + 1] = w.y; x[v][4 * kq + 2] = w.z; x[v][4 * kq + 3] = w.w;
+                }
+        }
+        float y[4][N];
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int n = 0; n < N; ++n) y[v][n] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (N >= 4) {
+#pragma unroll
+                for (int nq = 0; nq < N / 4; ++nq) {
+                    const float4 e = *reinterpret_cast<const float4*>(&Es[k * N + 4 * nq]);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const float xv = x[v][k] * sc_in;
+                        y[v][4 * nq] = fmaf(xv, e.x, y[v][4 * nq]);
+                        y[v][4 * nq + 1] = fmaf(xv, e.y, y[v][4 * nq + 1]);
+                        y[v][4 * nq + 2] = fmaf(xv, e.z, y[v][4 * nq + 2]);
+                        y[v][4 * nq + 3] = fmaf(xv, e.w, y[v][4 * nq + 3]);
+                    }
+                }
+            } else {
+                const float e = Es[k];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) y[v][0] = fmaf(x[v][k] * sc_in, e, y[v][0]);
+            }
+        }
+        if (MODE == 1) {
+            float* out = static_cast<float*>(t.out);
+            if (!ALONG_P) {
+#pragma unroll
+                for (int n = 0; n < N; ++n)
+                    *reinterpret_cast<float4*>(out + (p * N + n) * S + s) = make_float4(y[0][n], y[1][n], y[2][n], y[3][n]);
+            } else if (N == 1) {
+                *reinterpret_cast<float4*>(out + p) = make_float4(y[0][0], y[1][0], y[2][0], y[3][0]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+#pragma unroll
+                    for (int nq = 0; nq < N / 4; ++nq)
+                        *reinterpret_cast<float4*>(out + (p + v) * N + 4 * nq) =
+                            make_float4(y[v][4 * nq], y[v][4 * nq + 1], y[v][4 * nq + 2], y[v][4 * nq + 3]);
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+#pragma unroll
+                for (int n = 0; n < N; ++n) lmax = fmaxf(lmax, fabsf(y[v][n]));
+        } else {
+            const float* adj = static_cast<const float*>(t.adj);
+            float acc = 0.0f;
+            if (!ALONG_P) {
+#pragma unroll
+                for (int n = 0; n < N; ++n) {
+                    const float4 a = __ldg(reinterpret_cast<const float4*>(adj + (p * N + n) * S + s));
+                    acc = fmaf(y[0][n], a.x * sc_adj, acc);
+                    acc = fmaf(y[1][n], a.y * sc_adj, acc);
+                    acc = fmaf(y[2][n], a.z * sc_adj, acc);
+                    acc = fmaf(y[3][n], a.w * sc_adj, acc);
+                }
+            } else if (N == 1) {
+                const float4 a = __ldg(reinterpret_cast<const float4*>(adj + p));
+                acc = y[0][0] * a.x * sc_adj + y[1][0] * a.y * sc_adj + y[2][0] * a.z * sc_adj + y[3][0] * a.w * sc_adj;
+            } else {
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+#pragma unroll
+                    for (int nq = 0; nq < N / 4; ++nq) {
+                        const float4 a = __ldg(reinterpret_cast<const float4*>(adj + (p + v) * N + 4 * nq));
+                        acc = fmaf(y[v][4 * nq], a.x * sc_adj, acc);
+                        acc = fmaf(y[v][4 * nq + 1], a.y * sc_adj, acc);
+                        acc = fmaf(y[v][4 * nq + 2], a.z * sc_adj, acc);
+                        acc = fmaf(y[v][4 * nq + 3], a.w * sc_adj, acc);
+                    }
+            }
+            ldot = (double)acc;
+        }
+    }
+    if (MODE == 1) {
+        const double m = block_max((double)lmax, red);
+        if (threadIdx.x == 0) {
+            record_max(&slots[t.slot_out], m);
+            if (local == 0) slots[t.slot_out].X = slots[t.slot_in].X + e_in + slots[t.slot_E].X;
+        }
+    } else {
+        const double part = block_sum(ldot, red);
+        const long long X = slots[t.slot_in].X + e_in + slots[t.slot_E].X + slots[t.slot_adj].X + e_adj;
+        finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_out], X, red);
+    }
+}
+
 // Generic sizes (D = 4 and anything outside the unrolled set): E read from
 // global memory, one output leg at a time.
 template <typename T, int MODE>
@@ -259,6 +409,20 @@ long long absorb_tiles(long long P, long long S, int K, int N) {
     return (P * S + kAbsorbThreads - 1) / kAbsorbThreads;
 }
 
+int absorb_variant(int dt, long long P, long long S, int K, int N) {
+    auto small = [](int x) { return x == 1 || x == 4 || x == 16; };
+    if (dt != 1 || !small(K) || !small(N)) return 0;
+    if (S % 4 == 0) return 1;
+    if (S == 1 && P % 4 == 0) return 2;
+    return 0;
+}
+
+long long absorb_tiles_v(int variant, long long P, long long S, int K, int N) {
+    if (variant == 0) return absorb_tiles(P, S, K, N);
+    const long long groups = variant == 2 ? P / 4 : P * (S / 4);
+    return (groups + kV2Threads - 1) / kV2Threads;
+}
+
 namespace {
 
 bool kn_fast(int K, int N) {
@@ -298,9 +462,31 @@ cudaError_t absorb_dispatch(int K, int N, const AbsorbTask* tasks, int ntasks, l
 
 bool absorb_has_fast_path(int K, int N) { return kn_fast(K, N); }
 
+namespace {
+template <int MODE, bool ALONG_P>
+cudaError_t absorb4_dispatch(int K, int N, const AbsorbTask* tasks, int ntasks, long long nblocks, Slot* slots,
+                             cudaStream_t st) {
+#define TN_A4_CASE(KK, NN)                                                                        \
+    if (K == KK && N == NN) {                                                                     \
+        k_absorb4<KK, NN, MODE, ALONG_P><<<(unsigned)nblocks, kV2Threads, 0, st>>>(tasks, ntasks, slots); \
+        return cudaGetLastError();                                                                \
+    }
+    TN_A4_CASE(1, 1) TN_A4_CASE(1, 4) TN_A4_CASE(4, 1) TN_A4_CASE(4, 4)
+    TN_A4_CASE(1, 16) TN_A4_CASE(16, 1) TN_A4_CASE(4, 16) TN_A4_CASE(16, 4) TN_A4_CASE(16, 16)
+#undef TN_A4_CASE
+    return cudaErrorInvalidValue;
+}
+}  // namespace
+
 cudaError_t launch_absorb(int dt, bool dot, int K, int N, const AbsorbTask* tasks, int ntasks,
-                          long long nblocks, Slot* slots, cudaStream_t st) {
+                          long long nblocks, Slot* slots, cudaStream_t st, int variant) {
     if (nblocks <= 0) return cudaSuccess;
+    if (variant == 1)
+        return dot ? absorb4_dispatch<2, false>(K, N, tasks, ntasks, nblocks, slots, st)
+                   : absorb4_dispatch<1, false>(K, N, tasks, ntasks, nblocks, slots, st);
+    if (variant == 2)
+        return dot ? absorb4_dispatch<2, true>(K, N, tasks, ntasks, nblocks, slots, st)
+                   : absorb4_dispatch<1, true>(K, N, tasks, ntasks, nblocks, slots, st);
     if (dt == 0)
         return dot ? absorb_dispatch<double, 2>(K, N, tasks, ntasks, nblocks, slots, st)
                    : absorb_dispatch<double, 1>(K, N, tasks, ntasks, nblocks, slots, st);
@@ -408,9 +594,206 @@ k_gemm(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots)
     }
 }
 
+// ---- v2 FP32 SIMT product: 128 x 128 tile, 8-deep k slices, double buffered.
+//
+// 256 threads; thread (ty, tx) owns rows {4ty..4ty+3, 64+4ty..} and columns
+// {4tx..4tx+3, 64+4tx..}, so every shared-memory read is a conflict-free
+// 16-byte load and each k step is 4 loads for 64 FMAs.  The next k slice is
+// fetched into registers while the current one is multiplied.  Operands are
+// read through their strides; VEC4 (all contiguous extents multiples of 4,
+// 16-byte aligned) uses 16-byte global loads, otherwise scalar loads.
+constexpr int kG2M = 128, kG2N = 128, kG2K = 8;
+
+template <bool DOT, bool VEC4>
+__global__ void __launch_bounds__(256)
+k_gemm2(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+    __shared__ __align__(16) float As[2][kG2K][kG2M + 4];
+    __shared__ __align__(16) float Bs[2][kG2K][kG2N + 4];
+    __shared__ double red[32];
+    const long long tile = blockIdx.x;
+    const GemmTask& t = tasks[find_task(tasks, ntasks, tile)];
+    const long long local = tile - t.tile0;
+    const long long m0 = (local / t.tiles_n) * kG2M, n0 = (local % t.tiles_n) * kG2N;
+    const int eA = slot_shift(&slots[t.slot_A]), eB = slot_shift(&slots[t.slot_B]);
+    const float sA = pow2<float>(-eA), sB = pow2<float>(-eB);
+    const float* A = static_cast<const float*>(t.A);
+    const float* B = static_cast<const float*>(t.B);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const bool a_k = (t.sak == 1);    // A contiguous along k, else along m
+    const bool b_n = (t.sbn == 1);    // B contiguous along n, else along k
+    // this thread's 4 loaded values of the A and B slices and where they go
+    int a_mm, a_kk, b_nn, b_kk;
+    if (a_k) { a_mm = tid >> 1; a_kk = (tid & 1) * 4; } else { a_kk = tid >> 5; a_mm = (tid & 31) * 4; }
+    if (b_n) { b_kk = tid >> 5; b_nn = (tid & 31) * 4; } else { b_nn = tid >> 1; b_kk = (tid & 1) * 4; }
+    float ra[4], rb[4];
+    auto load_a = [&](long long k0) {
+        const long long gm = m0 + a_mm, gk = k0 + a_kk;
+        if (a_k) {
+            if (VEC4 && gm < t.M && gk + 3 < t.K) {
+                const float4 v = __ldg(reinterpret_cast<const float4*>(A + gm * t.sam + gk));
+                ra[0] = v.x; ra[1] = v.y; ra[2] = v.z; ra[3] = v.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) ra[i] = (gm < t.M && gk + i < t.K) ? A[gm * t.sam + (gk + i)] : 0.0f;
+            }
+        } else {
+            if (VEC4 && gk < t.K && gm + 3 < t.M) {
+                const float4 v = __ldg(reinterpret_cast<const float4*>(A + gk * t.sak + gm));
+                ra[0] = v.x; ra[1] = v.y; ra[2] = v.z; ra[3] = v.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) ra[i] = (gk < t.K && gm + i < t.M) ? A[(gm + i) * t.sam + gk * t.sak] : 0.0f;
+            }
+        }
+    };
+    auto load_b = [&](long long k0) {
+        const long long gn = n0 + b_nn, gk = k0 + b_kk;
+        if (b_n) {
+            if (VEC4 && gk < t.K && gn + 3 < t.N) {
+                const float4 v = __ldg(reinterpret_cast<const float4*>(B + gk * t.sbk + gn));
+                rb[0] = v.x; rb[1] = v.y; rb[2] = v.z; rb[3] = v.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) rb[i] = (gk < t.K && gn + i < t.N) ? B[gk * t.sbk + (gn + i)] : 0.0f;
+            }
+        } else {
+            if (VEC4 && gn < t.N && gk + 3 < t.K) {
+                const float4 v = __ldg(reinterpret_cast<const float4*>(B + gn * t.sbn + gk));
+                rb[0] = v.x; rb[1] = v.y; rb[2] = v.z; rb[3] = v.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) rb[i] = (gn < t.N && gk + i < t.K) ? B[(gk + i) * t.sbk + gn * t.sbn] : 0.0f;
+            }
+        }
+    };
+    auto store = [&](int buf) {
+        if (a_k) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) As[buf][a_kk + i][a_mm] = ra[i] * sA;
+        } else {
+            *reinterpret_cast<float4*>(&As[buf][a_kk][a_mm]) = make_float4(ra[0] * sA, ra[1] * sA, ra[2] * sA, ra[3] * sA);
+        }
+        if (b_n) {
+            *reinterpret_cast<float4*>(&Bs[buf][b_kk][b_nn]) = make_float4(rb[0] * sB, rb[1] * sB, rb[2] * sB, rb[3] * sB);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) Bs[buf][b_kk + i][b_nn] = rb[i] * sB;
+        }
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    const long long nk = (t.K + kG2K - 1) / kG2K;
+    load_a(0);
+    load_b(0);
+    store(0);
+    __syncthreads();
+    for (long long kt = 0; kt < nk; ++kt) {
+        const int cur = (int)(kt & 1);
+        if (kt + 1 < nk) { load_a((kt + 1) * kG2K); load_b((kt + 1) * kG2K); }
+#pragma unroll
+        for (int kk = 0; kk < kG2K; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][4 * ty]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + 4 * ty]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][4 * tx]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + 4 * tx]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (kt + 1 < nk) store(cur ^ 1);
+        __syncthreads();
+    }
+    auto row = [&](int i) { return m0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + (i - 4)); };
+    auto col = [&](int j) { return n0 + (j < 4 ? 4 * tx + j : 64 + 4 * tx + (j - 4)); };
+    if (!DOT) {
+        float* C = static_cast<float*>(t.C);
+        float m = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const long long gm = row(i);
+            if (gm >= t.M) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const long long gn = col(4 * h);
+                if (VEC4 && gn + 3 < t.N) {
+                    *reinterpret_cast<float4*>(C + gm * t.N + gn) =
+                        make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
+                    m = fmaxf(m, fmaxf(fmaxf(fabsf(acc[i][4 * h]), fabsf(acc[i][4 * h + 1])),
+                                       fmaxf(fabsf(acc[i][4 * h + 2]), fabsf(acc[i][4 * h + 3]))));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (gn + j < t.N) {
+                            C[gm * t.N + gn + j] = acc[i][4 * h + j];
+                            m = fmaxf(m, fabsf(acc[i][4 * h + j]));
+                        }
+                }
+            }
+        }
+        const double mm = block_max((double)m, red);
+        if (threadIdx.x == 0) {
+            record_max(&slots[t.slot_C], mm);
+            if (local == 0) slots[t.slot_C].X = slots[t.slot_A].X + eA + slots[t.slot_B].X + eB;
+        }
+    } else {
+        const int eD = slot_shift(&slots[t.slot_D]);
+        const float sD = pow2<float>(-eD);
+        const float* Dm = static_cast<const float*>(t.Dm);
+        float sum = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const long long gm = row(i);
+            if (gm >= t.M) continue;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const long long gn = col(j);
+                if (gn < t.N) sum = fmaf(acc[i][j], Dm[gm * t.N + gn] * sD, sum);
+            }
+        }
+        const double part = block_sum((double)sum, red);
+        const long long X = slots[t.slot_A].X + eA + slots[t.slot_B].X + eB + slots[t.slot_D].X + eD;
+        finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_C], X, red);
+    }
+}
+
+long long gemm_tiles_v(int variant, long long M, long long N, int* tiles_n) {
+    const int bm = variant == 0 ? kGemmTile : kG2M, bn = variant == 0 ? kGemmTile : kG2N;
+    const long long tm = (M + bm - 1) / bm, tn_ = (N + bn - 1) / bn;
+    *tiles_n = (int)tn_;
+    return tm * tn_;
+}
+
+// 0: v1 (64x64, any dtype); 1: v2 FP32 with 16-byte loads; 2: v2 FP32 scalar loads.
+int gemm_variant(int dt, long long M, long long N, long long K, long long sam, long long sak, long long sbk,
+                 long long sbn) {
+    if (dt != 1) return 0;
+    // 16-byte loads: the contiguous axis of each operand has unit stride, its
+    // extent and the other stride are multiples of 4 (k0, m0, n0 and the
+    // per-thread offsets are multiples of 4), and C rows are 16-byte aligned.
+    const bool a_ok = sak == 1 ? (sam % 4 == 0 && K % 4 == 0) : (sam == 1 && sak % 4 == 0 && M % 4 == 0);
+    const bool b_ok = sbn == 1 ? (sbk % 4 == 0 && N % 4 == 0) : (sbk == 1 && sbn % 4 == 0 && K % 4 == 0);
+    return (a_ok && b_ok && N % 4 == 0) ? 1 : 2;
+}
+
 cudaError_t launch_gemm(int dt, bool dot, const GemmTask* tasks, int ntasks, long long nblocks,
-                        Slot* slots, cudaStream_t st) {
+                        Slot* slots, cudaStream_t st, int variant) {
     if (nblocks <= 0) return cudaSuccess;
+    if (variant == 1) {
+        if (dot) k_gemm2<true, true><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+        else k_gemm2<false, true><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+        return cudaGetLastError();
+    }
+    if (variant == 2) {
+        if (dot) k_gemm2<true, false><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+        else k_gemm2<false, false><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+        return cudaGetLastError();
+    }
     if (dt == 0) {
         if (dot) k_gemm<double, true><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
         else k_gemm<double, false><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);

@@ -37,12 +37,6 @@ int family_of(int kind) {
     }
 }
 
-long long gemm_tiles(long long M, long long N, int* tiles_n) {
-    const long long tm = (M + kGemmTile - 1) / kGemmTile, tn_ = (N + kGemmTile - 1) / kGemmTile;
-    *tiles_n = (int)tn_;
-    return tm * tn_;
-}
-
 // Build every launch and its task table.  With base == nullptr only sizes are
 // computed (footprint); otherwise task structs hold absolute device pointers.
 void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vector<int>* ints_out,
@@ -68,15 +62,20 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
     lay.nslots = nslots;
     lay.nres = nres;
     // --- group operations: (level, kind, K, N) -> op refs (member-major order)
-    std::map<std::tuple<int, int, int, int>, std::vector<OpRef>> groups;
+    std::map<std::tuple<int, int, int, int, int>, std::vector<OpRef>> groups;
     int64_t npart = 0;
     for (int mi = 0; mi < (int)b->m.size(); ++mi) {
         const Program& pg = *b->m[mi].pg;
         for (int oi = 0; oi < (int)pg.ops.size(); ++oi) {
             const Op& op = pg.ops[oi];
-            int K = 0, N = 0;
-            if (op.kind == OP_ABSORB || op.kind == OP_ABSORB_DOT) { K = op.K; N = op.N; }
-            groups[std::make_tuple(op.level, (int)op.kind, K, N)].push_back({mi, oi});
+            int K = 0, N = 0, var = 0;
+            if (op.kind == OP_ABSORB || op.kind == OP_ABSORB_DOT) {
+                K = op.K; N = op.N;
+                var = absorb_variant(b->dt, op.P, op.S, op.K, op.N);
+            } else if (op.kind == OP_GEMM || op.kind == OP_GEMM_DOT) {
+                var = gemm_variant(b->dt, op.gm, op.gn, op.gk, op.sam, op.sak, op.sbk, op.sbn);
+            }
+            groups[std::make_tuple(op.level, (int)op.kind, K, N, var)].push_back({mi, oi});
         }
     }
     // --- device pointers of the fixed regions
@@ -105,8 +104,9 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         const int kind = std::get<1>(kv.first);
         for (const OpRef& r : kv.second) {
             const Op& op = b->m[r.member].pg->ops[r.op];
-            if (kind == OP_ABSORB_DOT) npart += absorb_tiles(op.P, op.S, op.K, op.N);
-            else if (kind == OP_GEMM_DOT) { int tn_; npart += gemm_tiles(op.gm, op.gn, &tn_); }
+            if (kind == OP_ABSORB_DOT)
+                npart += absorb_tiles_v(std::get<4>(kv.first), op.P, op.S, op.K, op.N);
+            else if (kind == OP_GEMM_DOT) { int tn_; npart += gemm_tiles_v(std::get<4>(kv.first), op.gm, op.gn, &tn_); }
             else if (kind == OP_DOT) npart += (op.gm + kDotPerBlock - 1) / kDotPerBlock;
         }
     }
@@ -137,6 +137,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         L.dt = b->dt;
         L.K = std::get<2>(kv.first);
         L.N = std::get<3>(kv.first);
+        L.variant = std::get<4>(kv.first);
         const auto& refs = kv.second;
         L.ntasks = (int)refs.size();
         long long tile = 0;
@@ -170,7 +171,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 t.slot_E = slot_of(r.member, op.E);
                 t.slot_out = slot_of(r.member, op.out);
                 t.tile0 = tile;
-                const long long nt = absorb_tiles(op.P, op.S, op.K, op.N);
+                const long long nt = absorb_tiles_v(L.variant, op.P, op.S, op.K, op.N);
                 t.ntiles = (int)nt;
                 if (kind == OP_ABSORB_DOT) {
                     t.adj = tensor_ptr(r.member, op.adj);
@@ -191,7 +192,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 t.slot_B = slot_of(r.member, op.B);
                 t.slot_C = slot_of(r.member, op.out);
                 int tn_ = 0;
-                const long long nt = gemm_tiles(op.gm, op.gn, &tn_);
+                const long long nt = gemm_tiles_v(L.variant, op.gm, op.gn, &tn_);
                 t.tiles_n = tn_;
                 t.ntiles = (int)nt;
                 t.tile0 = tile;
@@ -404,12 +405,12 @@ cudaError_t issue(tn_batch* b, cudaStream_t st, std::vector<std::pair<cudaEvent_
             case OP_ABSORB:
             case OP_ABSORB_DOT:
                 e = launch_absorb(L.dt, L.kind == OP_ABSORB_DOT, L.K, L.N, static_cast<const AbsorbTask*>(tp),
-                                  L.ntasks, L.nblocks, slots, st);
+                                  L.ntasks, L.nblocks, slots, st, L.variant);
                 break;
             case OP_GEMM:
             case OP_GEMM_DOT:
                 e = launch_gemm(L.dt, L.kind == OP_GEMM_DOT, static_cast<const GemmTask*>(tp), L.ntasks,
-                                L.nblocks, slots, st);
+                                L.nblocks, slots, st, L.variant);
                 break;
             case OP_DOT:
                 e = launch_dot(L.dt, static_cast<const DotTask*>(tp), L.ntasks, L.nblocks, slots, st);

@@ -31,6 +31,7 @@ struct Launch {
     int kind = 0;         // OpKind
     int dt = 0;
     int K = 0, N = 0;
+    int variant = 0;      // absorption kernel variant (see launch_absorb)
     size_t task_off = 0;  // bytes into the task region
     int ntasks = 0;
     long long nblocks = 0;

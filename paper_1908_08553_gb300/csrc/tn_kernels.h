@@ -94,10 +94,20 @@ struct ConstOne {
 
 // ----------------------------------------------------------- launchers ---
 // Each returns cudaSuccess or the launch error.  dt: 0 FP64, 1 FP32.
+// variant 0: one outer position per thread (any dtype, K, N); 1 / 2: FP32 with
+// K, N in {1, 4, 16}, four outer positions per thread along s (S % 4 == 0) or
+// along p (S == 1, P % 4 == 0).  All tasks of one launch share (K, N, variant).
 cudaError_t launch_absorb(int dt, bool dot, int K, int N, const AbsorbTask* tasks, int ntasks,
-                          long long nblocks, Slot* slots, cudaStream_t st);
+                          long long nblocks, Slot* slots, cudaStream_t st, int variant = 0);
+int absorb_variant(int dt, long long P, long long S, int K, int N);
+long long absorb_tiles_v(int variant, long long P, long long S, int K, int N);
+// variant 0: 64x64 tiles, any dtype; 1: FP32 128x128 double-buffered with
+// 16-byte loads; 2: the same with scalar loads (odd extents, e.g. D = 3).
 cudaError_t launch_gemm(int dt, bool dot, const GemmTask* tasks, int ntasks, long long nblocks,
-                        Slot* slots, cudaStream_t st);
+                        Slot* slots, cudaStream_t st, int variant = 0);
+int gemm_variant(int dt, long long M, long long N, long long K, long long sam, long long sak, long long sbk,
+                 long long sbn);
+long long gemm_tiles_v(int variant, long long M, long long N, int* tiles_n);
 cudaError_t launch_dot(int dt, const DotTask* tasks, int ntasks, long long nblocks, Slot* slots,
                        cudaStream_t st);
 cudaError_t launch_sitemat(int dt, const SiteMatTask* tasks, int ntasks, Slot* slots,
