@@ -59,8 +59,10 @@ typedef enum {
 typedef enum {
     TN_FP64 = 0,      /* FP64 storage and arithmetic */
     TN_FP32 = 1,      /* FP32 storage and arithmetic, FP64 reductions and ratios */
-    TN_BF16X3 = 2     /* FP32 storage; dense products on tcgen05 tensor cores with
-                         split-BF16 operands and FP32 accumulation */
+    TN_BF16X3 = 2,    /* FP32 storage; dense ring products on tcgen05 tensor cores,
+                         operands split x = x0 + x1 into BF16, 3 products, FP32
+                         accumulation (Henry, Tang & Heinecke, ARITH 2019) */
+    TN_BF16X6 = 3     /* as TN_BF16X3 with x = x0 + x1 + x2 and 6 products */
 } tn_precision;
 
 typedef enum {

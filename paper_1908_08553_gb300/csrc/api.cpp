@@ -42,6 +42,7 @@ double unit_roundoff(tn_precision p) {
     switch (p) {
         case TN_FP64: return 0x1.0p-53;
         case TN_FP32: return 0x1.0p-24;
+        case TN_BF16X6: return 0x1.0p-24;
         default: return 0x1.0p-16;
     }
 }
@@ -111,9 +112,13 @@ tn_status run_single(tn_lattice* lat, tn_precision prec, tn_schedule sched, tn_w
     tn_status s = batch_run(b, st);
     if (s != TN_OK) return s;
     res->resize((size_t)b->lay.nres);
+    int status = 0;
     e = cudaMemcpyAsync(res->data(), b->buf + b->lay.res_off, res->size() * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&status, b->buf + b->lay.status_off, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e, "result read");
+    if (status) { set_error("a bounded wait in a kernel timed out"); return TN_ERR_TIMEOUT; }
     if (used) *used = b;
     return TN_OK;
 }
@@ -378,9 +383,13 @@ tn_status tn_batch_run(tn_batch* b, double J, const double* h) {
 
 tn_status tn_batch_results_host(tn_batch* b, double* host, size_t cap) {
     if (!b || !host || cap < (size_t)b->lay.nres) return TN_ERR_INVALID;
+    int status = 0;
     cudaError_t e = cudaMemcpyAsync(host, b->buf + b->lay.res_off, (size_t)b->lay.nres * 8, cudaMemcpyDeviceToHost,
                                     b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&status, b->buf + b->lay.status_off, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess && status) { set_error("a bounded wait in a kernel timed out"); return TN_ERR_TIMEOUT; }
     return cuda_status(e, "result read");
 }
 

@@ -79,6 +79,25 @@ __device__ __forceinline__ double block_max(double v, double* red) {
     return r;
 }
 
+// Compensated sum (Neumaier's variant of Kahan summation) for the per-thread
+// FP32 parts of every dot product; FP64 sums are plain.
+template <typename T>
+struct CSum {
+    T s = T(0), c = T(0);
+    __device__ __forceinline__ void add(T x) {
+        const T t = s + x;
+        c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ T value() const { return s + c; }
+};
+template <>
+struct CSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
 __device__ __forceinline__ void record_max(Slot* s, double m) {
     atomicMax(&s->maxbits, (unsigned long long)__double_as_longlong(m));
 }
@@ -165,10 +184,10 @@ __device__ __forceinline__ void absorb_tile(const AbsorbTask& t, long long local
             lmax = (double)m;
         } else {
             const T* adj = static_cast<const T*>(t.adj) + p * N * S + s;
-            T acc = T(0);
+            CSum<T> acc;
 #pragma unroll
-            for (int n = 0; n < N; ++n) acc = fma(y[n], adj[n * S] * sc_adj, acc);
-            ldot = (double)acc;
+            for (int n = 0; n < N; ++n) acc.add(y[n] * (adj[n * S] * sc_adj));
+            ldot = (double)acc.value();
         }
     }
     if (MODE == 1) {
@@ -315,32 +334,35 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
                 for (int n = 0; n < N; ++n) lmax = fmaxf(lmax, fabsf(y[v][n]));
         } else {
             const float* adj = static_cast<const float*>(t.adj);
-            float acc = 0.0f;
+            CSum<float> acc;
             if (!ALONG_P) {
 #pragma unroll
                 for (int n = 0; n < N; ++n) {
                     const float4 a = __ldg(reinterpret_cast<const float4*>(adj + (p * N + n) * S + s));
-                    acc = fmaf(y[0][n], a.x * sc_adj, acc);
-                    acc = fmaf(y[1][n], a.y * sc_adj, acc);
-                    acc = fmaf(y[2][n], a.z * sc_adj, acc);
-                    acc = fmaf(y[3][n], a.w * sc_adj, acc);
+                    acc.add(y[0][n] * (a.x * sc_adj));
+                    acc.add(y[1][n] * (a.y * sc_adj));
+                    acc.add(y[2][n] * (a.z * sc_adj));
+                    acc.add(y[3][n] * (a.w * sc_adj));
                 }
             } else if (N == 1) {
                 const float4 a = __ldg(reinterpret_cast<const float4*>(adj + p));
-                acc = y[0][0] * a.x * sc_adj + y[1][0] * a.y * sc_adj + y[2][0] * a.z * sc_adj + y[3][0] * a.w * sc_adj;
+                acc.add(y[0][0] * (a.x * sc_adj));
+                acc.add(y[1][0] * (a.y * sc_adj));
+                acc.add(y[2][0] * (a.z * sc_adj));
+                acc.add(y[3][0] * (a.w * sc_adj));
             } else {
 #pragma unroll
                 for (int v = 0; v < 4; ++v)
 #pragma unroll
                     for (int nq = 0; nq < N / 4; ++nq) {
                         const float4 a = __ldg(reinterpret_cast<const float4*>(adj + (p + v) * N + 4 * nq));
-                        acc = fmaf(y[v][4 * nq], a.x * sc_adj, acc);
-                        acc = fmaf(y[v][4 * nq + 1], a.y * sc_adj, acc);
-                        acc = fmaf(y[v][4 * nq + 2], a.z * sc_adj, acc);
-                        acc = fmaf(y[v][4 * nq + 3], a.w * sc_adj, acc);
+                        acc.add(y[v][4 * nq] * (a.x * sc_adj));
+                        acc.add(y[v][4 * nq + 1] * (a.y * sc_adj));
+                        acc.add(y[v][4 * nq + 2] * (a.z * sc_adj));
+                        acc.add(y[v][4 * nq + 3] * (a.w * sc_adj));
                     }
             }
-            ldot = (double)acc;
+            ldot = (double)acc.value();
         }
     }
     if (MODE == 1) {
@@ -577,7 +599,7 @@ k_gemm(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots)
         const int eD = slot_shift(&slots[t.slot_D]);
         const T sD = pow2<T>(-eD);
         const T* Dm = static_cast<const T*>(t.Dm);
-        T s = T(0);
+        CSum<T> s;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const long long gm = m0 + ty * 4 + i;
@@ -585,10 +607,10 @@ k_gemm(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const long long gn = n0 + tx * 4 + j;
-                if (gn < t.N) s = fma(acc[i][j], Dm[gm * t.N + gn] * sD, s);
+                if (gn < t.N) s.add(acc[i][j] * (Dm[gm * t.N + gn] * sD));
             }
         }
-        const double part = block_sum((double)s, red);
+        const double part = block_sum((double)s.value(), red);
         const long long X = slots[t.slot_A].X + eA + slots[t.slot_B].X + eB + slots[t.slot_D].X + eD;
         finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_C], X, red);
     }
@@ -613,7 +635,10 @@ k_gemm2(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots
     const long long tile = blockIdx.x;
     const GemmTask& t = tasks[find_task(tasks, ntasks, tile)];
     const long long local = tile - t.tile0;
-    const long long m0 = (local / t.tiles_n) * kG2M, n0 = (local % t.tiles_n) * kG2N;
+    // dot mode splits k into slices of t.kslice (one FP64 partial each)
+    const long long mn = local / t.ksplit, ks = local % t.ksplit;
+    const long long m0 = (mn / t.tiles_n) * kG2M, n0 = (mn % t.tiles_n) * kG2N;
+    const long long kbeg = ks * t.kslice, kend = min(t.K, kbeg + t.kslice);
     const int eA = slot_shift(&slots[t.slot_A]), eB = slot_shift(&slots[t.slot_B]);
     const float sA = pow2<float>(-eA), sB = pow2<float>(-eB);
     const float* A = static_cast<const float*>(t.A);
@@ -685,14 +710,14 @@ k_gemm2(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots
     for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
-    const long long nk = (t.K + kG2K - 1) / kG2K;
-    load_a(0);
-    load_b(0);
+    const long long nk = (kend - kbeg + kG2K - 1) / kG2K;
+    load_a(kbeg);
+    load_b(kbeg);
     store(0);
     __syncthreads();
     for (long long kt = 0; kt < nk; ++kt) {
         const int cur = (int)(kt & 1);
-        if (kt + 1 < nk) { load_a((kt + 1) * kG2K); load_b((kt + 1) * kG2K); }
+        if (kt + 1 < nk) { load_a(kbeg + (kt + 1) * kG2K); load_b(kbeg + (kt + 1) * kG2K); }
 #pragma unroll
         for (int kk = 0; kk < kG2K; ++kk) {
             const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][4 * ty]);
@@ -745,7 +770,7 @@ k_gemm2(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots
         const int eD = slot_shift(&slots[t.slot_D]);
         const float sD = pow2<float>(-eD);
         const float* Dm = static_cast<const float*>(t.Dm);
-        float sum = 0.0f;
+        CSum<float> sum;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const long long gm = row(i);
@@ -753,10 +778,10 @@ k_gemm2(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const long long gn = col(j);
-                if (gn < t.N) sum = fmaf(acc[i][j], Dm[gm * t.N + gn] * sD, sum);
+                if (gn < t.N) sum.add(acc[i][j] * (Dm[gm * t.N + gn] * sD));
             }
         }
-        const double part = block_sum((double)sum, red);
+        const double part = block_sum((double)sum.value(), red);
         const long long X = slots[t.slot_A].X + eA + slots[t.slot_B].X + eB + slots[t.slot_D].X + eD;
         finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_C], X, red);
     }
@@ -767,6 +792,11 @@ long long gemm_tiles_v(int variant, long long M, long long N, int* tiles_n) {
     const long long tm = (M + bm - 1) / bm, tn_ = (N + bn - 1) / bn;
     *tiles_n = (int)tn_;
     return tm * tn_;
+}
+
+long long gemm_ksplit(int variant, bool dot, long long K) {
+    if (!dot || variant == 0) return 1;
+    return (K + kGemmKSlice - 1) / kGemmKSlice;
 }
 
 // 0: v1 (64x64, any dtype); 1: v2 FP32 with 16-byte loads; 2: v2 FP32 scalar loads.
@@ -818,12 +848,12 @@ k_dot(const DotTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
     const T* A = static_cast<const T*>(t.A);
     const T* B = static_cast<const T*>(t.B);
     const long long base = local * kDotPerBlock;
-    T s = T(0);
+    CSum<T> s;
     for (int k = threadIdx.x; k < kDotPerBlock; k += 256) {
         const long long g = base + k;
-        if (g < t.n) s = fma(A[g] * sA, B[g] * sB, s);
+        if (g < t.n) s.add((A[g] * sA) * (B[g] * sB));
     }
-    const double part = block_sum((double)s, red);
+    const double part = block_sum((double)s.value(), red);
     const long long X = slots[t.slot_A].X + eA + slots[t.slot_B].X + eB;
     finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_out], X, red);
 }
@@ -938,13 +968,16 @@ __global__ void k_final(const FinalTask* __restrict__ tasks, const Slot* __restr
     const double mn = nz.mant;
     const long long Xn = nz.X;
     double* v = t.out + kResultHeader;
+    // each ratio uses the norm evaluated along the same contraction path
     for (int k = threadIdx.x; k < t.n_sites; k += blockDim.x) {
         const Slot& s = slots[t.sx_slots[k]];
-        v[k] = ldexp(s.mant / mn, (int)(s.X - Xn));
+        const Slot& d = slots[t.sx_den[k]];
+        v[k] = ldexp(s.mant / d.mant, (int)(s.X - d.X));
     }
     for (int k = threadIdx.x; k < t.n_bonds; k += blockDim.x) {
         const Slot& s = slots[t.zz_slots[k]];
-        v[t.n_sites + k] = ldexp(s.mant / mn, (int)(s.X - Xn));
+        const Slot& d = slots[t.zz_den[k]];
+        v[t.n_sites + k] = ldexp(s.mant / d.mant, (int)(s.X - d.X));
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -129,9 +129,54 @@ public:
         return out;
     }
 
+    // Tiled BF16 planes of the operand X[r][k] = src[r*sr + k*sk] (one per view).
+    int tc_split(int src, int64_t R, int64_t Kd, int64_t sr, int64_t sk) {
+        auto key = std::make_tuple(src, R, Kd, sr, sk);
+        auto it = split_.find(key);
+        if (it != split_.end()) return it->second;
+        const int64_t Rp = (R + 127) / 128 * 128, Kp = (Kd + 63) / 64 * 64;
+        const int level = level_of(src) + 1;
+        // BF16 planes counted in 4-byte units of the FP32 arena
+        const int out = tensor((int64_t)pg_.nsplit * Rp * Kp / 2, level);
+        Op op;
+        op.kind = OP_TC_SPLIT;
+        op.level = level;
+        op.A = src; op.out = out;
+        op.gm = R; op.gk = Kd; op.sam = sr; op.sak = sk;
+        op.Rp = Rp; op.Kp = Kp; op.nsplit = pg_.nsplit;
+        op.bytes = (double)R * Kd * 4 + (double)pg_.nsplit * Rp * Kp * 2;
+        use(src, level);
+        add(op);
+        split_[key] = out;
+        return out;
+    }
+
     // C[m][n] = sum_k A(m,k) B(k,n); dot partner Cd -> scalar.
     int gemm(int A, int B, int64_t M, int64_t N, int64_t K, int64_t sam, int64_t sak,
              int64_t sbk, int64_t sbn, int Cd = -1) {
+        if (pg_.nsplit && M >= 128 && N >= 128 && K >= 64) {
+            // tensor cores: C = A' B'^T with A'[m][k] = A(m,k) and B'[n][k] = B(k,n)
+            const int Ap = tc_split(A, M, K, sam, sak);
+            const int Bp = tc_split(B, N, K, sbn, sbk);
+            int lv = std::max(level_of(Ap), level_of(Bp)) + 1;
+            if (Cd >= 0) lv = std::max(lv, level_of(Cd) + 1);
+            const int o = Cd >= 0 ? scalar(lv) : tensor(M * N, lv);
+            Op op;
+            op.kind = Cd >= 0 ? OP_TC_GEMM_DOT : OP_TC_GEMM;
+            op.level = lv;
+            op.A = Ap; op.B = Bp; op.C = Cd; op.out = o;
+            op.A_src = A; op.B_src = B;
+            op.gm = M; op.gn = N; op.gk = K;
+            op.Kp = (K + 63) / 64 * 64;
+            op.nsplit = pg_.nsplit;
+            op.bytes = (double)pg_.nsplit * ((M + 127) / 128 * 128 + (N + 127) / 128 * 128) * op.Kp * 2 +
+                       (double)M * N * 4;
+            op.macs = (double)M * N * K;
+            use(Ap, lv); use(Bp, lv); use(A, lv); use(B, lv);
+            if (Cd >= 0) use(Cd, lv);
+            add(op);
+            return o;
+        }
         int level = std::max(level_of(A), level_of(B)) + 1;
         if (Cd >= 0) level = std::max(level, level_of(Cd) + 1);
         const int out = Cd >= 0 ? scalar(level) : tensor(M * N, level);
@@ -168,6 +213,7 @@ private:
     Program& pg_;
     int one_ = -1;
     std::map<std::pair<int, int>, int> E_;
+    std::map<std::tuple<int, int64_t, int64_t, int64_t, int64_t>, int> split_;
 };
 
 // Greedy first-fit interval packing of tensor lifetimes, wave by wave.
@@ -239,6 +285,7 @@ std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sc
     pg.plan = plan_choose(L, W, D, sched);
     pg.work = work;
     pg.dt = prec == TN_FP64 ? DT_F64 : DT_F32;
+    pg.nsplit = prec == TN_BF16X3 ? 2 : (prec == TN_BF16X6 ? 3 : 0);
     pg.esize = pg.dt == DT_F64 ? 8 : 4;
     const Plan& pl = pg.plan;
     const int nsite = L * W;
@@ -306,12 +353,25 @@ std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sc
             G[q][T] = Env[q];
             for (int t = T; t >= 2; --t) G[q][t - 1] = bd.absorb(G[q][t], E_at(q, t, PH_I), step_of(q, t), true);
         }
+        // norm along each step's path: <F[q][t], G[q][t]> (built on demand)
+        std::map<std::pair<int, int>, int> local_norm;
+        auto norm_at = [&](int q, int t) {
+            auto key = std::make_pair(q, t);
+            auto it = local_norm.find(key);
+            if (it != local_norm.end()) return it->second;
+            const int v = bd.dot(F[q][t], G[q][t], step_of(q, t).n_out);
+            const int sl = pg.tensors[v].slot;
+            local_norm[key] = sl;
+            return sl;
+        };
         // sites
         pg.sx_slot.assign(nsite, -1);
+        pg.sx_den.assign(nsite, -1);
         for (int s = 0; s < nsite; ++s) {
             const SiteRef& w = where[s];
             const int v = bd.absorb_dot(F[w.q][w.t - 1], E_at(w.q, w.t, PH_X), G[w.q][w.t], step_of(w.q, w.t));
             pg.sx_slot[s] = pg.tensors[v].slot;
+            pg.sx_den[s] = norm_at(w.q, w.t);
         }
         // bonds, output order: horizontal row-major, then vertical row-major
         std::vector<std::pair<int, int>> bonds;
@@ -320,6 +380,7 @@ std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sc
         for (int r = 0; r + 1 < L; ++r)
             for (int c = 0; c < W; ++c) bonds.push_back({r * W + c, (r + 1) * W + c});
         int Xl = -1, Xr = -1;
+        int den_cross[4] = {-1, -1, -1, -1};
         auto regrow = [&](int q, int t) {
             const int T = (int)pl.corner[q].steps.size();
             int x = bd.absorb(F[q][t - 1], E_at(q, t, PH_Z), step_of(q, t), false);
@@ -327,6 +388,7 @@ std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sc
             return x;
         };
         pg.zz_slot.assign(bonds.size(), -1);
+        pg.zz_den.assign(bonds.size(), pg.norm_slot);
         for (size_t bi = 0; bi < bonds.size(); ++bi) {
             SiteRef a = where[bonds[bi].first], b = where[bonds[bi].second];
             int v = -1;
@@ -336,21 +398,36 @@ std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sc
                 int x = bd.absorb(F[q][a.t - 1], E_at(q, a.t, PH_Z), step_of(q, a.t), false);
                 for (int u = a.t + 1; u < b.t; ++u) x = bd.absorb(x, E_at(q, u, PH_I), step_of(q, u), false);
                 v = bd.absorb_dot(x, E_at(q, b.t, PH_Z), G[q][b.t], step_of(q, b.t));
+                pg.zz_den[bi] = norm_at(q, b.t);
             } else {
                 int qa = a.q, qb = b.q;
                 int ta = a.t, tb = b.t;
                 if (qa > qb) { std::swap(qa, qb); std::swap(ta, tb); }
                 const int Za = regrow(qa, ta), Zb = regrow(qb, tb);
+                // each class of cut-crossing bond is normalised by the same fused
+                // product on the unmodified corners (the norm through the same path)
                 if (qa == TL && qb == TR) {
                     v = bd.gemm(Mbot, Zb, hbL, vrT, hbR, hbR, 1, vrT, 1, Za);
+                    if (den_cross[0] < 0)
+                        den_cross[0] = pg.tensors[bd.gemm(Mbot, Qt[TR], hbL, vrT, hbR, hbR, 1, vrT, 1, Qt[TL])].slot;
+                    pg.zz_den[bi] = den_cross[0];
                 } else if (qa == BL && qb == BR) {
                     v = bd.gemm(Mtop, Zb, hbL, vrB, hbR, hbR, 1, vrB, 1, Za);
+                    if (den_cross[1] < 0)
+                        den_cross[1] = pg.tensors[bd.gemm(Mtop, Qt[BR], hbL, vrB, hbR, hbR, 1, vrB, 1, Qt[BL])].slot;
+                    pg.zz_den[bi] = den_cross[1];
                 } else if (qa == TL && qb == BL) {
                     if (Xr < 0) Xr = bd.gemm(Qt[TR], Qt[BR], vrT, vrB, hbR, 1, vrT, vrB, 1);
                     v = bd.gemm(Za, Zb, vrT, vrB, hbL, 1, vrT, vrB, 1, Xr);
+                    if (den_cross[2] < 0)
+                        den_cross[2] = pg.tensors[bd.gemm(Qt[TL], Qt[BL], vrT, vrB, hbL, 1, vrT, vrB, 1, Xr)].slot;
+                    pg.zz_den[bi] = den_cross[2];
                 } else if (qa == TR && qb == BR) {
                     if (Xl < 0) Xl = bd.gemm(Qt[TL], Qt[BL], vrT, vrB, hbL, 1, vrT, vrB, 1);
                     v = bd.gemm(Za, Zb, vrT, vrB, hbR, 1, vrT, vrB, 1, Xl);
+                    if (den_cross[3] < 0)
+                        den_cross[3] = pg.tensors[bd.gemm(Qt[TR], Qt[BR], vrT, vrB, hbR, 1, vrT, vrB, 1, Xl)].slot;
+                    pg.zz_den[bi] = den_cross[3];
                 } else {
                     throw std::logic_error("bond between non-adjacent corners");
                 }

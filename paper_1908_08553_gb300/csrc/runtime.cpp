@@ -33,6 +33,7 @@ int family_of(int kind) {
         case OP_ABSORB: return FAM_ABSORB;
         case OP_ABSORB_DOT: return FAM_ABSORB_DOT;
         case OP_GEMM: case OP_GEMM_DOT: return FAM_GEMM;
+        case OP_TC_GEMM: case OP_TC_GEMM_DOT: return FAM_TC;
         default: return FAM_OTHER;
     }
 }
@@ -74,6 +75,8 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 var = absorb_variant(b->dt, op.P, op.S, op.K, op.N);
             } else if (op.kind == OP_GEMM || op.kind == OP_GEMM_DOT) {
                 var = gemm_variant(b->dt, op.gm, op.gn, op.gk, op.sam, op.sak, op.sbk, op.sbn);
+            } else if (op.kind == OP_TC_GEMM || op.kind == OP_TC_GEMM_DOT) {
+                var = op.nsplit;
             }
             groups[std::make_tuple(op.level, (int)op.kind, K, N, var)].push_back({mi, oi});
         }
@@ -106,8 +109,14 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
             const Op& op = b->m[r.member].pg->ops[r.op];
             if (kind == OP_ABSORB_DOT)
                 npart += absorb_tiles_v(std::get<4>(kv.first), op.P, op.S, op.K, op.N);
-            else if (kind == OP_GEMM_DOT) { int tn_; npart += gemm_tiles_v(std::get<4>(kv.first), op.gm, op.gn, &tn_); }
+            else if (kind == OP_GEMM_DOT) {
+                int tn_;
+                const int var = std::get<4>(kv.first);
+                npart += gemm_tiles_v(var, op.gm, op.gn, &tn_) * gemm_ksplit(var, true, op.gk);
+            }
             else if (kind == OP_DOT) npart += (op.gm + kDotPerBlock - 1) / kDotPerBlock;
+            else if (kind == OP_TC_GEMM_DOT)
+                npart += ((op.gm + 127) / 128) * ((op.gn + 127) / 128) * ((op.Kp + kGemmKSlice - 1) / kGemmKSlice);
         }
     }
     lay.npart = npart;
@@ -192,11 +201,55 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 t.slot_B = slot_of(r.member, op.B);
                 t.slot_C = slot_of(r.member, op.out);
                 int tn_ = 0;
-                const long long nt = gemm_tiles_v(L.variant, op.gm, op.gn, &tn_);
+                const long long ksp = gemm_ksplit(L.variant, kind == OP_GEMM_DOT, op.gk);
+                const long long nt = gemm_tiles_v(L.variant, op.gm, op.gn, &tn_) * ksp;
                 t.tiles_n = tn_;
                 t.ntiles = (int)nt;
+                t.ksplit = (int)ksp;
+                t.kslice = ksp > 1 ? kGemmKSlice : op.gk;
                 t.tile0 = tile;
                 if (kind == OP_GEMM_DOT) {
+                    t.Dm = tensor_ptr(r.member, op.C);
+                    t.slot_D = slot_of(r.member, op.C);
+                    t.partial = take_partial(nt);
+                } else {
+                    t.C = tensor_ptr(r.member, op.out);
+                }
+                off = append(&t, sizeof(t));
+                tile += nt;
+            } else if (kind == OP_TC_SPLIT) {
+                TcSplitTask t{};
+                t.src = tensor_ptr(r.member, op.A);
+                t.dst = tensor_ptr(r.member, op.out);
+                t.R = op.gm; t.Kd = op.gk; t.sr = op.sam; t.sk = op.sak;
+                t.Rp = op.Rp; t.Kp = op.Kp;
+                t.plane_bytes = op.Rp * op.Kp * 2;
+                t.nsplit = op.nsplit;
+                t.slot_src = slot_of(r.member, op.A);
+                const long long nt = tc_split_tiles(op.Rp, op.Kp);
+                t.ntiles = (int)nt;
+                t.tile0 = tile;
+                off = append(&t, sizeof(t));
+                tile += nt;
+            } else if (kind == OP_TC_GEMM || kind == OP_TC_GEMM_DOT) {
+                TcGemmTask t{};
+                t.A = tensor_ptr(r.member, op.A);
+                t.B = tensor_ptr(r.member, op.B);
+                const long long Mp = (op.gm + 127) / 128 * 128, Np = (op.gn + 127) / 128 * 128;
+                t.a_plane_bytes = Mp * op.Kp * 2;
+                t.b_plane_bytes = Np * op.Kp * 2;
+                t.M = op.gm; t.N = op.gn; t.Kp = op.Kp;
+                t.slot_A = slot_of(r.member, op.A_src);
+                t.slot_B = slot_of(r.member, op.B_src);
+                t.slot_C = slot_of(r.member, op.out);
+                t.tiles_n = (int)(Np / 128);
+                const long long ksp = kind == OP_TC_GEMM_DOT ? (op.Kp + kGemmKSlice - 1) / kGemmKSlice : 1;
+                t.ksplit = (int)ksp;
+                t.kchunks = ksp > 1 ? kGemmKSlice / 64 : op.Kp / 64;
+                const long long nt = (Mp / 128) * (Np / 128) * ksp;
+                t.ntiles = (int)nt;
+                t.tile0 = tile;
+                if (kind == OP_TC_GEMM_DOT) {
                     t.Dm = tensor_ptr(r.member, op.C);
                     t.slot_D = slot_of(r.member, op.C);
                     t.partial = take_partial(nt);
@@ -234,18 +287,25 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
     }
     // final tasks and their slot tables
     b->h_final.clear();
-    std::vector<std::pair<size_t, size_t>> tbl;   // (sx offset, zz offset) in ints
+    struct Tbl { size_t sx, zz, sxd, zzd; };
+    std::vector<Tbl> tbl;   // offsets in ints
     for (int mi = 0; mi < (int)b->m.size(); ++mi) {
         const Member& mb = b->m[mi];
         const Program& pg = *mb.pg;
-        const size_t sx0 = ints.size();
+        Tbl tb;
+        tb.sx = ints.size();
         for (int s : pg.sx_slot) ints.push_back((int)(mb.slot_base + s));
-        const size_t zz0 = ints.size();
+        tb.zz = ints.size();
         for (int s : pg.zz_slot) ints.push_back((int)(mb.slot_base + s));
-        tbl.push_back({sx0, zz0});
+        tb.sxd = ints.size();
+        for (int s : pg.sx_den) ints.push_back((int)(mb.slot_base + s));
+        tb.zzd = ints.size();
+        for (int s : pg.zz_den) ints.push_back((int)(mb.slot_base + s));
+        tbl.push_back(tb);
     }
     lay.task_bytes = tasks.size();
-    lay.final_off = up(lay.tasks_off + tasks.size());
+    lay.status_off = up(lay.tasks_off + tasks.size());
+    lay.final_off = up(lay.status_off + sizeof(int));
     lay.ints_off = up(lay.final_off + b->m.size() * sizeof(FinalTask));
     lay.ones_off = up(lay.ints_off + ints.size() * sizeof(int));
     lay.total = up(lay.ones_off + ones.size() * sizeof(ConstOne));
@@ -259,8 +319,10 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         f.n_bonds = (int)mb.pg->zz_slot.size();
         if (base) {
             const int* ib = reinterpret_cast<const int*>(base + lay.ints_off);
-            f.sx_slots = ib + tbl[mi].first;
-            f.zz_slots = ib + tbl[mi].second;
+            f.sx_slots = ib + tbl[mi].sx;
+            f.zz_slots = ib + tbl[mi].zz;
+            f.sx_den = ib + tbl[mi].sxd;
+            f.zz_den = ib + tbl[mi].zzd;
             f.out = reinterpret_cast<double*>(base + lay.res_off) + mb.res_off;
         }
         f.J = 1.0;
@@ -279,7 +341,7 @@ std::shared_ptr<const Program> program_cached(int L, int W, int D, tn_schedule s
                                               tn_work work) {
     static std::mutex mu;
     static std::map<std::tuple<int, int, int, int, int, int>, std::shared_ptr<const Program>> cache;
-    const auto key = std::make_tuple(L, W, D, (int)sched, (int)(prec == TN_FP64 ? 0 : 1), (int)work);
+    const auto key = std::make_tuple(L, W, D, (int)sched, (int)prec, (int)work);
     {
         std::lock_guard<std::mutex> g(mu);
         auto it = cache.find(key);
@@ -296,7 +358,7 @@ tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int
     const BatchOpts defaults;
     if (!opts) opts = &defaults;
     if (n <= 0 || !L || !W || !D) { set_error("empty batch"); return TN_ERR_INVALID; }
-    if (prec < TN_FP64 || prec > TN_BF16X3 || sched < TN_SCHED_AUTO || sched > TN_SCHED_QUADRANT ||
+    if (prec < TN_FP64 || prec > TN_BF16X6 || sched < TN_SCHED_AUTO || sched > TN_SCHED_QUADRANT ||
         work < TN_WORK_NORM || work > TN_WORK_ENERGY) {
         set_error("bad enum"); return TN_ERR_INVALID;
     }
@@ -390,8 +452,11 @@ namespace {
 cudaError_t issue(tn_batch* b, cudaStream_t st, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev) {
     char* base = b->buf;
     Slot* slots = reinterpret_cast<Slot*>(base + b->lay.slots_off);
-    cudaError_t e = launch_init(slots, b->lay.nslots, reinterpret_cast<const ConstOne*>(base + b->lay.ones_off),
-                                (int)b->lay.nones, b->dt, st);
+    int* status = reinterpret_cast<int*>(base + b->lay.status_off);
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    e = launch_init(slots, b->lay.nslots, reinterpret_cast<const ConstOne*>(base + b->lay.ones_off),
+                    (int)b->lay.nones, b->dt, st);
     if (e != cudaSuccess) return e;
     const char* tb = base + b->lay.tasks_off;
     for (size_t li = 0; li < b->launches.size(); ++li) {
@@ -414,6 +479,14 @@ cudaError_t issue(tn_batch* b, cudaStream_t st, std::vector<std::pair<cudaEvent_
                 break;
             case OP_DOT:
                 e = launch_dot(L.dt, static_cast<const DotTask*>(tp), L.ntasks, L.nblocks, slots, st);
+                break;
+            case OP_TC_SPLIT:
+                e = launch_tc_split(static_cast<const TcSplitTask*>(tp), L.ntasks, L.nblocks, slots, st);
+                break;
+            case OP_TC_GEMM:
+            case OP_TC_GEMM_DOT:
+                e = launch_tc_gemm(L.variant, L.kind == OP_TC_GEMM_DOT, static_cast<const TcGemmTask*>(tp),
+                                   L.ntasks, L.nblocks, slots, status, st);
                 break;
         }
         if (ev) cudaEventRecord((*ev)[li].second, st);

@@ -50,7 +50,7 @@ struct Member {
 // Byte layout of a batch's single device buffer.
 struct Layout {
     size_t in_off = 0, arena_off = 0, slots_off = 0, part_off = 0, res_off = 0;
-    size_t tasks_off = 0, final_off = 0, ints_off = 0, ones_off = 0, total = 0;
+    size_t tasks_off = 0, status_off = 0, final_off = 0, ints_off = 0, ones_off = 0, total = 0;
     int64_t nslots = 0, npart = 0, nres = 0, nin = 0, nones = 0, nints = 0;
     size_t task_bytes = 0;
 };

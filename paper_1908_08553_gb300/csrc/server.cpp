@@ -246,7 +246,7 @@ tn_status tn_submit(tn_ctx* ctx, const tn_job* job, uint64_t* ticket) {
         if (!ctx || !job || !ticket) return TN_ERR_INVALID;
         if (ctx->device < 0) { set_error("context has no device"); return TN_ERR_NO_DEVICE; }
         if (job->L < 1 || job->L > 16 || job->W < 1 || job->W > 16 || job->D < 1 || job->D > 4 ||
-            job->precision < TN_FP64 || job->precision > TN_BF16X3) {
+            job->precision < TN_FP64 || job->precision > TN_BF16X6) {
             set_error("bad job");
             return TN_ERR_INVALID;
         }

@@ -1,0 +1,417 @@
+// Ring products on the 5th-generation tensor cores (tcgen05, sm_103a), FP32
+// operands split into BF16 planes, FP32 accumulation in tensor memory.
+//
+// Split (Henry, Tang & Heinecke, "Leveraging the bfloat16 artificial
+// intelligence datatype for higher-precision computations", ARITH 2019):
+// x = x0 + x1 (+ x2) with x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1);
+// a product keeps the terms whose planes sum to at most NSPLIT - 1:
+//   NSPLIT = 2: x0 y0 + x0 y1 + x1 y0              (3 tensor-core products)
+//   NSPLIT = 3: ... + x0 y2 + x1 y1 + x2 y0         (6 products)
+// the smallest terms are accumulated first.
+//
+// Operand layout ("tiled planes", written by k_tc_split): an R x K operand
+// (row r, reduction index k) is padded to multiples of 128 rows and 64 k and
+// stored per plane as blocks of 128 rows x 64 k (16 KiB), block (rb, c) at
+// ((rb * nchunks) + c) * 16 KiB.  Inside a block the 8x8 core matrices (8 rows
+// of 8 consecutive k, 16 bytes per row) are laid out k-fastest: core (ri, ki)
+// at (ri * 8 + ki) * 128 bytes.  That is the canonical K-major layout without
+// swizzling, so one 16 KiB bulk copy stages a block and the shared-memory
+// descriptor uses LBO = 128 B (next core along k) and SBO = 1024 B (next
+// 8-row group).
+//
+// One CTA (128 threads) computes one 128 x 128 output tile: thread 0 of warp 0
+// stages k-chunks with cp.async.bulk into a ring of shared-memory stages,
+// thread 0 of warp 1 issues the tcgen05.mma and commits each stage back to the
+// producer, and all four warps read the accumulator from tensor memory
+// (lane = output row) for the epilogue.  Every wait is bounded: on time-out
+// the kernel records an error code, drains, frees its tensor memory and exits.
+#include <cstdint>
+
+#include <cuda_bf16.h>
+
+#include "tn_kernels.h"
+
+namespace tn {
+
+namespace {
+
+constexpr int kTcM = 128, kTcN = 128, kTcK = 64;      // tile rows, tile cols, k per chunk
+constexpr uint32_t kBlockBytes = kTcM * kTcK * 2;     // one 128 x 64 BF16 block
+constexpr long long kWaitCycles = 4000000000LL;       // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on one phase of an mbarrier; false after ~2 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, M = 128, N = 128, K = 16, BF16 in, FP32 acc.
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// Arrive on `bar` once every tcgen05 operation issued so far by this thread completes.
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive 32-bit accumulator columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: canonical K-major layout, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);             // start address
+    d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;        // LBO: next core matrix along k
+    d |= (uint64_t)((1024u >> 4) & 0x3FFF) << 32;       // SBO: next 8-row group
+    d |= (uint64_t)1 << 46;                             // descriptor version (tcgen05)
+    return d;                                           // base offset 0, no swizzle
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                            ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ int slot_shift_tc(const Slot* s) {
+    const double m = __longlong_as_double((long long)s->maxbits);
+    if (!(m > 0.0)) return 0;
+    int e;
+    frexp(m, &e);
+    return e;
+}
+
+__device__ __forceinline__ float pow2f(int e) {
+    e = e < -125 ? -125 : (e > 125 ? 125 : e);
+    return __int_as_float((127 + e) << 23);
+}
+
+template <typename Task>
+__device__ __forceinline__ int find_task_tc(const Task* __restrict__ tasks, int ntasks, long long tile) {
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ double block_reduce(double v, double* red, bool is_max) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = is_max ? fmax(v, w) : v + w;
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = is_max ? 0.0 : 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r = is_max ? fmax(r, red[k]) : r + red[k];
+    return r;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- split --
+
+// One thread per (row, 8-wide k group) of the padded operand.
+__global__ void __launch_bounds__(256)
+k_tc_split(const TcSplitTask* __restrict__ tasks, int ntasks, const Slot* __restrict__ slots) {
+    const long long tile = blockIdx.x;
+    const TcSplitTask& t = tasks[find_task_tc(tasks, ntasks, tile)];
+    const long long idx = (tile - t.tile0) * 256 + threadIdx.x;
+    const long long nko = t.Kp / 8;
+    if (idx >= t.Rp * nko) return;
+    const long long r = idx % t.Rp, ko = idx / t.Rp;   // consecutive threads: consecutive rows
+    const float sc = pow2f(-slot_shift_tc(&slots[t.slot_src]));
+    const float* src = static_cast<const float*>(t.src);
+    float x[8];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        const long long k = ko * 8 + kk;
+        x[kk] = (r < t.R && k < t.Kd) ? src[r * t.sr + k * t.sk] * sc : 0.0f;
+    }
+    const long long nchunks = t.Kp / kTcK;
+    const long long rb = r / kTcM, rr = r % kTcM, c = ko / 8, ki = ko % 8;
+    const long long off = (rb * nchunks + c) * (long long)kBlockBytes + (((rr / 8) * 8 + ki) * 8 + (rr % 8)) * 16;
+    __align__(16) __nv_bfloat16 p0[8], p1[8], p2[8];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(x[kk]);
+        const float r1 = x[kk] - __bfloat162float(h0);
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(h1);
+        p0[kk] = h0;
+        p1[kk] = h1;
+        p2[kk] = __float2bfloat16_rn(r2);
+    }
+    char* dst = static_cast<char*>(t.dst);
+    *reinterpret_cast<uint4*>(dst + off) = *reinterpret_cast<const uint4*>(p0);
+    *reinterpret_cast<uint4*>(dst + t.plane_bytes + off) = *reinterpret_cast<const uint4*>(p1);
+    if (t.nsplit == 3) *reinterpret_cast<uint4*>(dst + 2 * t.plane_bytes + off) = *reinterpret_cast<const uint4*>(p2);
+}
+
+// ------------------------------------------------------------------ mma ---
+
+template <int NSPLIT, bool DOT>
+__global__ void __launch_bounds__(128, 1)
+k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, int* __restrict__ status) {
+    constexpr int STAGES = NSPLIT == 2 ? 3 : 2;
+    constexpr uint32_t kStageBytes = 2u * NSPLIT * kBlockBytes;    // A planes then B planes
+    constexpr int NPROD = NSPLIT == 2 ? 3 : 6;
+    // products (plane of A, plane of B), smallest terms first
+    constexpr int PA[6] = {NSPLIT == 2 ? 1 : 2, NSPLIT == 2 ? 0 : 1, NSPLIT == 2 ? 0 : 0, 1, 0, 0};
+    constexpr int PB[6] = {NSPLIT == 2 ? 0 : 0, NSPLIT == 2 ? 1 : 1, NSPLIT == 2 ? 0 : 2, 0, 1, 0};
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int fail_sh;
+    __shared__ double red[32];
+
+    const long long tile = blockIdx.x;
+    const TcGemmTask& t = tasks[find_task_tc(tasks, ntasks, tile)];
+    const long long local = tile - t.tile0;
+    const long long mn = local / t.ksplit, ks = local % t.ksplit;
+    const long long tm = mn / t.tiles_n, tn_ = mn % t.tiles_n;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long nchunks_all = t.Kp / kTcK;       // chunks of the whole k range (layout)
+    const long long cbeg = ks * t.kchunks;
+    const long long nchunks = min(nchunks_all, cbeg + t.kchunks) - cbeg;
+    // 1024-byte aligned start of the stage ring
+    unsigned char* ring = smem + ((1024 - (smem_u32(smem) & 1023)) & 1023);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+        mbar_init(&done_bar, 1);
+        fail_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_base_sh, kTcN);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    const char* Ab = static_cast<const char*>(t.A) + (tm * nchunks_all + cbeg) * (long long)kBlockBytes;
+    const char* Bb = static_cast<const char*>(t.B) + (tn_ * nchunks_all + cbeg) * (long long)kBlockBytes;
+    int my_fail = 0;
+    int armed[STAGES];
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) armed[s] = 0;
+    if (warp == 0 && lane == 0) {
+        // producer: stage k-chunk c into ring slot c % STAGES
+        for (long long c = 0; c < nchunks && !my_fail; ++c) {
+            const int s = (int)(c % STAGES);
+            if (c >= STAGES && !mbar_wait(&empty_bar[s], (uint32_t)((c / STAGES - 1) & 1))) { my_fail = 1; break; }
+            unsigned char* st = ring + s * kStageBytes;
+            armed[s] += 1;
+            mbar_expect_tx(&full_bar[s], kStageBytes);
+            for (int p = 0; p < NSPLIT; ++p) {
+                bulk_g2s(st + p * kBlockBytes, Ab + p * t.a_plane_bytes + c * kBlockBytes, kBlockBytes, &full_bar[s]);
+                bulk_g2s(st + (NSPLIT + p) * kBlockBytes, Bb + p * t.b_plane_bytes + c * kBlockBytes, kBlockBytes,
+                         &full_bar[s]);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        for (long long c = 0; c < nchunks; ++c) {
+            const int s = (int)(c % STAGES);
+            if (!mbar_wait(&full_bar[s], (uint32_t)((c / STAGES) & 1))) { my_fail = 1; break; }
+            tc_fence_after();
+            const uint32_t st = smem_u32(ring + s * kStageBytes);
+#pragma unroll
+            for (int ks = 0; ks < kTcK / 16; ++ks) {
+#pragma unroll
+                for (int q = 0; q < NPROD; ++q) {
+                    const uint64_t da = smem_desc(st + PA[q] * kBlockBytes + ks * 256);
+                    const uint64_t db = smem_desc(st + (NSPLIT + PB[q]) * kBlockBytes + ks * 256);
+                    tc_mma(tmem, da, db, kIdesc, (c > 0 || ks > 0 || q > 0) ? 1u : 0u);
+                }
+            }
+            tc_commit(&empty_bar[s]);
+        }
+        tc_commit(&done_bar);
+    }
+    if (my_fail) atomicExch(&fail_sh, 1);
+    // epilogue: wait for the last MMA (bounded), then read the accumulator
+    bool ok = mbar_wait(&done_bar, 0u);
+    __syncthreads();
+    if (!ok || fail_sh) {
+        if (threadIdx.x == 0) atomicExch(status, 1);
+        // never leave with our own bulk copies in flight: wait (bounded) for the
+        // last phase the producer armed on every stage
+        if (warp == 0 && lane == 0)
+            for (int s = 0; s < STAGES; ++s)
+                if (armed[s] > 0) (void)mbar_wait(&full_bar[s], (uint32_t)((armed[s] - 1) & 1));
+    }
+    __syncthreads();
+    tc_fence_after();
+    const long long row = tm * kTcM + warp * 32 + lane;
+    const long long n0 = tn_ * kTcN;
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    const int eA = slot_shift_tc(&slots[t.slot_A]), eB = slot_shift_tc(&slots[t.slot_B]);
+    double mx = 0.0, dsum = 0.0;
+    const bool good = ok && !fail_sh;
+    float sD = 1.0f;
+    int eD = 0;
+    if (DOT) { eD = slot_shift_tc(&slots[t.slot_D]); sD = pow2f(-eD); }
+    for (int cb = 0; cb < kTcN; cb += 16) {
+        float v[16];
+        tmem_ld16(lane_addr + (uint32_t)cb, v);
+        if (!good || row >= t.M) continue;
+        if (!DOT) {
+            float* C = static_cast<float*>(t.C) + row * t.N;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const long long n = n0 + cb + i;
+                if (n < t.N) { C[n] = v[i]; mx = fmax(mx, (double)fabsf(v[i])); }
+            }
+        } else {
+            const float* Dm = static_cast<const float*>(t.Dm) + row * t.N;
+            float s = 0.0f, comp = 0.0f;    // compensated (Neumaier) sum of 16 products
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const long long n = n0 + cb + i;
+                if (n < t.N) {
+                    const float x = v[i] * (Dm[n] * sD), tt = s + x;
+                    comp += (fabsf(s) >= fabsf(x)) ? (s - tt) + x : (x - tt) + s;
+                    s = tt;
+                }
+            }
+            dsum += (double)s + (double)comp;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTcN);
+    if (!DOT) {
+        const double m = block_reduce(mx, red, true);
+        if (threadIdx.x == 0) {
+            atomicMax(&slots[t.slot_C].maxbits, (unsigned long long)__double_as_longlong(m));
+            if (local == 0) slots[t.slot_C].X = slots[t.slot_A].X + eA + slots[t.slot_B].X + eB;
+        }
+    } else {
+        const double part = block_reduce(dsum, red, false);
+        __shared__ int is_last;
+        if (threadIdx.x == 0) {
+            t.partial[local] = part;
+            __threadfence();
+            const unsigned prev = atomicAdd(&slots[t.slot_C].count, 1u);
+            is_last = (prev == (unsigned)(t.ntiles - 1));
+        }
+        __syncthreads();
+        if (is_last) {
+            __threadfence();
+            double acc = 0.0;
+            for (int k = threadIdx.x; k < t.ntiles; k += blockDim.x) acc += __ldcg(t.partial + k);
+            acc = block_reduce(acc, red, false);
+            if (threadIdx.x == 0) {
+                slots[t.slot_C].mant = acc;
+                slots[t.slot_C].X = slots[t.slot_A].X + eA + slots[t.slot_B].X + eB + slots[t.slot_D].X + eD;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------- launchers --
+
+long long tc_split_tiles(long long Rp, long long Kp) { return (Rp * (Kp / 8) + 255) / 256; }
+
+cudaError_t launch_tc_split(const TcSplitTask* tasks, int ntasks, long long nblocks, const Slot* slots,
+                            cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    k_tc_split<<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_gemm(int nsplit, bool dot, const TcGemmTask* tasks, int ntasks, long long nblocks,
+                           Slot* slots, int* status, cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    const int stages = nsplit == 2 ? 3 : 2;
+    const size_t smem = (size_t)stages * 2 * nsplit * kBlockBytes + 1024;
+#define TN_TC_LAUNCH(NS, DT)                                                                   \
+    {                                                                                          \
+        auto fn = k_tc_gemm<NS, DT>;                                                           \
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                        \
+        fn<<<(unsigned)nblocks, 128, smem, st>>>(tasks, ntasks, slots, status);                \
+        return cudaGetLastError();                                                             \
+    }
+    if (nsplit == 2) { if (dot) TN_TC_LAUNCH(2, true) else TN_TC_LAUNCH(2, false) }
+    if (dot) TN_TC_LAUNCH(3, true) else TN_TC_LAUNCH(3, false)
+#undef TN_TC_LAUNCH
+}
+
+}  // namespace tn

@@ -75,6 +75,9 @@ enum OpKind {
     OP_GEMM,          // C = opA(A) opB(B)
     OP_GEMM_DOT,      // scalar = <opA(A) opB(B), C>
     OP_DOT,           // scalar = <A, B>
+    OP_TC_SPLIT,      // FP32 operand -> tiled BF16 planes (tensor-core input)
+    OP_TC_GEMM,       // C = A B^T on tensor cores from split planes
+    OP_TC_GEMM_DOT,   // scalar = <A B^T, C> on tensor cores
 };
 
 // Operator insertion on the physical leg.
@@ -103,6 +106,10 @@ struct Op {
     int A = -1, B = -1, C = -1;
     int64_t gm = 0, gn = 0, gk = 0;
     int64_t sam = 0, sak = 0, sbk = 0, sbn = 0;
+    // tensor cores: source tensors of the split operands (their slots carry the scale)
+    int A_src = -1, B_src = -1;
+    int nsplit = 0;
+    long long Rp = 0, Kp = 0;
     // sitemat
     int site = -1, phys = PH_I;
     int map[4] = {0, 1, 2, 3};
@@ -116,6 +123,7 @@ struct Program {
     Plan plan;
     tn_work work = TN_WORK_ENERGY;
     DType dt = DT_F32;
+    int nsplit = 0;               // 2 or 3: dense products on tensor cores (BF16 split)
     int esize = 4;
     std::vector<Tensor> tensors;
     std::vector<Op> ops;
@@ -123,6 +131,10 @@ struct Program {
     int norm_slot = -1;
     std::vector<int> sx_slot;     // per site (row-major, original lattice)
     std::vector<int> zz_slot;     // per bond (output order)
+    // denominator of each ratio: <F[q][t], G[q][t]> at the step where the
+    // observable meets its environment (the norm along the same rounding path),
+    // or norm_slot for bonds across a cut
+    std::vector<int> sx_den, zz_den;
     int n_slots = 0;
     int64_t arena_bytes = 0;      // tensors + site matrices (typed)
     int64_t input_bytes = 0;      // raw FP64 site tensors

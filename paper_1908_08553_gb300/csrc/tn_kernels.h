@@ -51,9 +51,15 @@ struct GemmTask {
     long long M, N, K;
     long long sam, sak, sbk, sbn;
     long long tile0;
+    long long kslice;     // k per tile (= K unless the product is split along k)
     int tiles_n, ntiles;
+    int ksplit;           // tiles along k (dot mode: one FP64 partial each)
     int slot_A, slot_B, slot_C, slot_D;
 };
+
+// k-slice of the products fused with a dot: partial sums of at most this
+// many FP32 terms before the FP64 accumulation.
+constexpr long long kGemmKSlice = 512;
 
 struct DotTask {
     const void* A;
@@ -82,6 +88,8 @@ constexpr int kResultHeader = 6;
 struct FinalTask {
     const int* sx_slots;  // n_sites
     const int* zz_slots;  // n_bonds
+    const int* sx_den;    // n_sites: slot of each ratio's denominator
+    const int* zz_den;    // n_bonds
     double* out;          // kResultHeader + n_sites + n_bonds
     double J, h;
     int norm_slot;
@@ -90,6 +98,34 @@ struct FinalTask {
 
 struct ConstOne {
     void* ptr;
+};
+
+// FP32 operand X[r][k] = src[r*sr + k*sk] (rescaled by its slot) split into
+// BF16 planes in the tiled tensor-core layout (see tc_gemm.cu).
+struct TcSplitTask {
+    const void* src;
+    void* dst;
+    long long R, Kd, sr, sk;      // logical rows, reduction length, strides
+    long long Rp, Kp;             // padded to 128 rows, 64 k
+    long long plane_bytes;
+    long long tile0;
+    int ntiles, nsplit, slot_src, pad;
+};
+
+// C[m][n] = sum_k A[m][k] B[n][k] from tiled BF16 planes, 128 x 128 tiles.
+struct TcGemmTask {
+    const void* A;                // tiled planes of A (rows m)
+    const void* B;                // tiled planes of B (rows n)
+    void* C;                      // FP32 [M][N] (store mode)
+    const void* Dm;               // FP32 [M][N] dot partner (dot mode)
+    double* partial;
+    long long a_plane_bytes, b_plane_bytes;
+    long long M, N, Kp;
+    long long tile0;
+    long long kchunks;            // 64-wide k chunks per tile (split along k in dot mode)
+    int tiles_n, ntiles;
+    int ksplit;
+    int slot_A, slot_B, slot_C, slot_D;   // slots of the FP32 sources / result
 };
 
 // ----------------------------------------------------------- launchers ---
@@ -108,6 +144,7 @@ cudaError_t launch_gemm(int dt, bool dot, const GemmTask* tasks, int ntasks, lon
 int gemm_variant(int dt, long long M, long long N, long long K, long long sam, long long sak, long long sbk,
                  long long sbn);
 long long gemm_tiles_v(int variant, long long M, long long N, int* tiles_n);
+long long gemm_ksplit(int variant, bool dot, long long K);
 cudaError_t launch_dot(int dt, const DotTask* tasks, int ntasks, long long nblocks, Slot* slots,
                        cudaStream_t st);
 cudaError_t launch_sitemat(int dt, const SiteMatTask* tasks, int ntasks, Slot* slots,
@@ -115,6 +152,12 @@ cudaError_t launch_sitemat(int dt, const SiteMatTask* tasks, int ntasks, Slot* s
 cudaError_t launch_init(Slot* slots, long long nslots, const ConstOne* ones, int nones, int dt,
                         cudaStream_t st);
 cudaError_t launch_final(const FinalTask* tasks, int ntasks, const Slot* slots, cudaStream_t st);
+long long tc_split_tiles(long long Rp, long long Kp);
+cudaError_t launch_tc_split(const TcSplitTask* tasks, int ntasks, long long nblocks, const Slot* slots,
+                            cudaStream_t st);
+// status: set to 1 if a bounded wait inside the kernel timed out.
+cudaError_t launch_tc_gemm(int nsplit, bool dot, const TcGemmTask* tasks, int ntasks, long long nblocks,
+                           Slot* slots, int* status, cudaStream_t st);
 cudaError_t launch_absorb_plain(int dt, const void* in, const void* E, void* out, long long P,
                                 int K, int N, long long S, cudaStream_t st);
 // <absorb(in, E), adj> into *result (device).  scratch: 16 B counter header

@@ -17,12 +17,12 @@ from . import build as _build
 TN_OK, TN_NOT_READY = 0, 1
 TN_ERR_INVALID, TN_ERR_OVER_BUDGET, TN_ERR_OOM = -1, -2, -3
 TN_ERR_CUDA, TN_ERR_TIMEOUT, TN_ERR_NUMERIC, TN_ERR_NO_DEVICE = -4, -5, -6, -7
-TN_FP64, TN_FP32, TN_BF16X3 = 0, 1, 2
+TN_FP64, TN_FP32, TN_BF16X3, TN_BF16X6 = 0, 1, 2, 3
 TN_SCHED_AUTO, TN_SCHED_ROW, TN_SCHED_COL, TN_SCHED_QUADRANT = 0, 1, 2, 3
 TN_WORK_NORM, TN_WORK_ENERGY = 0, 1
 TN_OP_NORM, TN_OP_X, TN_OP_ZZ = 0, 1, 2
 
-PRECISIONS = {"fp64": TN_FP64, "fp32": TN_FP32, "bf16x3": TN_BF16X3}
+PRECISIONS = {"fp64": TN_FP64, "fp32": TN_FP32, "bf16x3": TN_BF16X3, "bf16x6": TN_BF16X6}
 
 
 class tn_scalar(ctypes.Structure):

@@ -17,7 +17,7 @@ from paper_1908_08553_gb300 import inputs, tn
 
 pytestmark = pytest.mark.gpu
 
-TOL = {tn.TN_FP64: 1e-10, tn.TN_FP32: 1e-6, tn.TN_BF16X3: 1e-6}
+TOL = {tn.TN_FP64: 1e-10, tn.TN_FP32: 1e-6, tn.TN_BF16X3: 1e-6, tn.TN_BF16X6: 1e-6}
 PRECS = [tn.TN_FP64, tn.TN_FP32]
 SCHEDS = [tn.TN_SCHED_AUTO, tn.TN_SCHED_ROW, tn.TN_SCHED_COL, tn.TN_SCHED_QUADRANT]
 
@@ -243,3 +243,46 @@ def test_tn_absorb_dot_matches_reference(K, N, P, S, dtype):
     got = res.cpu().numpy()
     assert abs(got[0] - ref) <= tol * scale
     assert got[0] == got[1]          # deterministic finish of the tile partials
+
+
+# ------------------------------------------------ tensor-core ring products
+
+@pytest.mark.parametrize("prec", [tn.TN_BF16X3, tn.TN_BF16X6])
+def test_c2_8x8_d2_tensor_core_precisions(ctx, prec):
+    """256-wide ring products on tcgen05 (split BF16, FP32 accumulation)."""
+    L, W, D = 8, 8, 2
+    A = inputs.random_lattice(L, W, D, 88)
+    ref = oracle.observables(L, W, D, A)
+    lat = tn.tn_create_lattice(ctx, L, W, D)
+    try:
+        tn.tn_set_site_tensors(lat, A)
+        for h in (2.0, 3.04, 4.0):
+            r, sx, zz = tn.tn_energy(lat, 1.0, h, prec, tn.TN_SCHED_AUTO, L, W)
+            _check(r, sx, zz, ref, prec, 1.0, h)
+        # the tensor-core result is not the FP32 SIMT result bit for bit
+        r32, _, _ = tn.tn_energy(lat, 1.0, 3.04, tn.TN_FP32, tn.TN_SCHED_AUTO, L, W)
+        r16, _, _ = tn.tn_energy(lat, 1.0, 3.04, prec, tn.TN_SCHED_AUTO, L, W)
+        assert r32.energy != r16.energy
+    finally:
+        tn.tn_destroy_lattice(lat)
+
+
+def test_tensor_core_d3_5x5(ctx):
+    """D = 3: 729 x 729 ring products (odd extents, padded tiles) on tcgen05."""
+    L, W, D = 5, 5, 3
+    A = inputs.random_lattice(L, W, D, 5353)
+    ref = oracle.observables(L, W, D, A)
+    for prec in (tn.TN_BF16X3, tn.TN_BF16X6, tn.TN_FP32):
+        r, sx, zz = _energy(ctx, L, W, D, A, prec, tn.TN_SCHED_AUTO)
+        _check(r, sx, zz, ref, prec)
+
+
+def test_tensor_core_all_ones_exact(ctx):
+    """All-ones D = 2: every split plane beyond the first is zero, products exact."""
+    L, W = 8, 8
+    A = inputs.ones_lattice(L, W, 2)
+    for prec in (tn.TN_BF16X3, tn.TN_BF16X6):
+        r, sx, zz = _energy(ctx, L, W, 2, A, prec, tn.TN_SCHED_AUTO)
+        N, nb = L * W, L * (W - 1) + W * (L - 1)
+        assert r.norm.mant == 0.5 and r.norm.exp2 == N + 2 * nb + 1
+        assert np.all(sx == 1.0) and np.all(zz == 0.0)
