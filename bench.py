@@ -158,6 +158,66 @@ def run_reference(args):
     return 0
 
 
+def run_large(args):
+    """Large single instances: 12x12 D=2 and 8x8 D=3 (forced row scheme for the
+    absorption roofline, AUTO for energies), one line of JSON."""
+    import numpy as np
+    import torch
+
+    from paper_1908_08553_gb300 import inputs, tn
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    ctx = tn.tn_ctx_create(0, 0, stream)
+    hbm, bf16, sm_max, src = _peaks()
+    out = {"workload": "large single instances (12x12 D=2, 8x8 D=3)", "peak_hbm_gbs": hbm}
+    for (L, W, D) in [(12, 12, 2), (8, 8, 3)]:
+        A = inputs.random_lattice(L, W, D, 1000 + L + D)
+        key = f"{L}x{W}_D{D}"
+        res = {}
+        for label, sched, prec, work in [("row_norm_fp32", tn.TN_SCHED_ROW, tn.TN_FP32, tn.TN_WORK_NORM),
+                                         ("auto_norm_fp32", tn.TN_SCHED_AUTO, tn.TN_FP32, tn.TN_WORK_NORM),
+                                         ("auto_energy_fp32", tn.TN_SCHED_AUTO, tn.TN_FP32, tn.TN_WORK_ENERGY),
+                                         ("auto_energy_bf16x3", tn.TN_SCHED_AUTO, tn.TN_BF16X3, tn.TN_WORK_ENERGY),
+                                         ("auto_energy_fp64", tn.TN_SCHED_AUTO, tn.TN_FP64, tn.TN_WORK_ENERGY)]:
+            b = tn.tn_batch_create(ctx, [L], [W], [D], prec, sched, work)
+            tn.tn_batch_set_tensors(b, A)
+            hs = np.array([3.04])
+            for _ in range(2):
+                tn.tn_batch_run(b, 1.0, hs)
+            torch.cuda.synchronize()
+            reps = 3
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                tn.tn_batch_run(b, 1.0, hs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            tn.tn_ctx_set_profiling(ctx, True)
+            tn.tn_batch_run(b, 1.0, hs)
+            torch.cuda.synchronize()
+            fam = {n: tn.tn_ctx_kernel_stats(ctx, k) for k, n in
+                   enumerate(["absorb", "absorb_dot", "gemm_simt", "gemm_tc", "other"])}
+            tn.tn_ctx_set_profiling(ctx, False)
+            r = tn.tn_batch_results_host(b)
+            entry = {"ms": ms, "evals_per_s": 1000.0 / ms, "log2_norm": float(r[1])}
+            if work == tn.TN_WORK_ENERGY:
+                entry["energy_per_site"] = float(r[0]) / (L * W)
+            a = fam["absorb"]
+            if a["ms"]:
+                gbs = a["bytes"] / (a["ms"] / 1e3) / 1e9
+                entry["absorb"] = {"ms": a["ms"], "launches": a["launches"], "GBps": gbs, "frac_hbm": gbs / hbm,
+                                   "TFLOPs": 2 * a["macs"] / (a["ms"] / 1e3) / 1e12}
+            entry["families_ms"] = {n: v["ms"] for n, v in fam.items() if v["launches"]}
+            res[label] = entry
+            tn.tn_batch_destroy(b)
+        out[key] = res
+    tn.tn_ctx_destroy(ctx)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -169,9 +229,13 @@ def main():
     ap.add_argument("--ref-lattices", type=int, default=2)
     ap.add_argument("--cpu-lattices", type=int, default=3)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 line and the CPU baseline")
+    ap.add_argument("--workload", default="8x8", choices=["8x8", "large"],
+                    help="8x8: the bench line; large: 12x12 D=2 / 8x8 D=3 measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "large":
+        return run_large(args)
 
     import numpy as np
     import torch
