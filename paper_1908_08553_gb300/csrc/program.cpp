@@ -106,6 +106,8 @@ public:
         op.K = trans ? s.N : s.K;
         op.N = trans ? s.K : s.N;
         op.transE = trans;
+        // wide double-layer steps (D = 3 interior, K = N = 81) go to the tensor cores
+        if (pg_.nsplit && op.K == 81 && op.N == 81) op.nsplit = pg_.nsplit;
         op.bytes = (double)(s.n_in + s.n_out) * pg_.esize;
         op.macs = (double)s.mac;
         use(in, level); use(E, level);
@@ -122,6 +124,7 @@ public:
         op.level = level;
         op.in = in; op.E = E; op.adj = adj; op.out = out;
         op.P = s.P; op.S = s.S; op.K = s.K; op.N = s.N;
+        if (pg_.nsplit && op.K == 81 && op.N == 81) op.nsplit = pg_.nsplit;
         op.bytes = (double)(s.n_in + 2 * s.n_out) * pg_.esize;
         op.macs = (double)s.mac + (double)s.n_out;
         use(in, level); use(E, level); use(adj, level);

@@ -32,6 +32,7 @@ int family_of(int kind) {
     switch (kind) {
         case OP_ABSORB: return FAM_ABSORB;
         case OP_ABSORB_DOT: return FAM_ABSORB_DOT;
+        case OP_TC_SPLIT: return FAM_OTHER;
         case OP_GEMM: case OP_GEMM_DOT: return FAM_GEMM;
         case OP_TC_GEMM: case OP_TC_GEMM_DOT: return FAM_TC;
         default: return FAM_OTHER;
@@ -72,7 +73,8 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
             int K = 0, N = 0, var = 0;
             if (op.kind == OP_ABSORB || op.kind == OP_ABSORB_DOT) {
                 K = op.K; N = op.N;
-                var = absorb_variant(b->dt, op.P, op.S, op.K, op.N);
+                // 3 / 4: tensor-core absorption with 2 / 3 split planes
+                var = op.nsplit ? 1 + op.nsplit : absorb_variant(b->dt, op.P, op.S, op.K, op.N);
             } else if (op.kind == OP_GEMM || op.kind == OP_GEMM_DOT) {
                 var = gemm_variant(b->dt, op.gm, op.gn, op.gk, op.sam, op.sak, op.sbk, op.sbn);
             } else if (op.kind == OP_TC_GEMM || op.kind == OP_TC_GEMM_DOT) {
@@ -107,8 +109,10 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         const int kind = std::get<1>(kv.first);
         for (const OpRef& r : kv.second) {
             const Op& op = b->m[r.member].pg->ops[r.op];
-            if (kind == OP_ABSORB_DOT)
-                npart += absorb_tiles_v(std::get<4>(kv.first), op.P, op.S, op.K, op.N);
+            if (kind == OP_ABSORB_DOT) {
+                const int var = std::get<4>(kv.first);
+                npart += var >= 3 ? tc_absorb_tiles(op.P, op.S) : absorb_tiles_v(var, op.P, op.S, op.K, op.N);
+            }
             else if (kind == OP_GEMM_DOT) {
                 int tn_;
                 const int var = std::get<4>(kv.first);
@@ -180,7 +184,8 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 t.slot_E = slot_of(r.member, op.E);
                 t.slot_out = slot_of(r.member, op.out);
                 t.tile0 = tile;
-                const long long nt = absorb_tiles_v(L.variant, op.P, op.S, op.K, op.N);
+                const long long nt = L.variant >= 3 ? tc_absorb_tiles(op.P, op.S)
+                                                    : absorb_tiles_v(L.variant, op.P, op.S, op.K, op.N);
                 t.ntiles = (int)nt;
                 if (kind == OP_ABSORB_DOT) {
                     t.adj = tensor_ptr(r.member, op.adj);
@@ -469,8 +474,12 @@ cudaError_t issue(tn_batch* b, cudaStream_t st, std::vector<std::pair<cudaEvent_
                 break;
             case OP_ABSORB:
             case OP_ABSORB_DOT:
-                e = launch_absorb(L.dt, L.kind == OP_ABSORB_DOT, L.K, L.N, static_cast<const AbsorbTask*>(tp),
-                                  L.ntasks, L.nblocks, slots, st, L.variant);
+                if (L.variant >= 3)
+                    e = launch_tc_absorb(L.variant - 1, L.kind == OP_ABSORB_DOT, static_cast<const AbsorbTask*>(tp),
+                                         L.ntasks, L.nblocks, slots, status, st);
+                else
+                    e = launch_absorb(L.dt, L.kind == OP_ABSORB_DOT, L.K, L.N, static_cast<const AbsorbTask*>(tp),
+                                      L.ntasks, L.nblocks, slots, st, L.variant);
                 break;
             case OP_GEMM:
             case OP_GEMM_DOT:

@@ -163,6 +163,16 @@ __device__ __forceinline__ int find_task_tc(const Task* __restrict__ tasks, int 
     return lo;
 }
 
+struct CSumF {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return s + c; }
+};
+
 __device__ __forceinline__ double block_reduce(double v, double* red, bool is_max) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -383,6 +393,230 @@ k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
             }
         }
     }
+}
+
+// ------------------------------------------------------- D=3 absorption --
+//
+// Out[p][n][s] = sum_k In[p][k][s] E[k][n] for K = N = 81 (interior double-layer
+// steps of D = 3) on tensor cores.  Each CTA (128 threads) takes kAbsSub
+// consecutive groups of 128 outer positions o = p*S + s.  Per group, thread t
+// loads the 81 inputs of position o0 + t (rescaled by the input slot), splits
+// them into BF16 planes and writes them as row t of the A operand (K-major,
+// k padded to 96); the site matrix, transposed into B'[n][k], is split once per
+// CTA.  One thread issues 6 k-steps x NPROD products (M = 128, N = 96), the
+// accumulator row of each lane is its outer position, so the FP32 stores of
+// Out (or the fused dot with the adjoint) are coalesced along s.
+constexpr int kAbsK = 81, kAbsKp = 96, kAbsSub = 4;
+constexpr uint32_t kAbsAPlane = 128 * kAbsKp * 2;   // 24 KiB
+constexpr uint32_t kAbsBPlane = kAbsKp * kAbsKp * 2;  // 18 KiB
+constexpr uint32_t kAbsSBO = (kAbsKp / 8) * 128;      // next 8-row group: 12 core matrices
+constexpr uint32_t kAbsIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kAbsKp >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ uint64_t smem_desc_sbo(uint32_t saddr, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Split 8 FP32 values and store them as one 16-byte row segment per plane.
+template <int NSPLIT>
+__device__ __forceinline__ void split_store8(const float* x, unsigned char* base, uint32_t plane_bytes, uint32_t off) {
+    __align__(16) __nv_bfloat16 q0[8], q1[8], q2[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(x[i]);
+        const float r1 = x[i] - __bfloat162float(h0);
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+        q0[i] = h0;
+        q1[i] = h1;
+        if (NSPLIT == 3) q2[i] = __float2bfloat16_rn(r1 - __bfloat162float(h1));
+    }
+    *reinterpret_cast<uint4*>(base + off) = *reinterpret_cast<const uint4*>(q0);
+    *reinterpret_cast<uint4*>(base + plane_bytes + off) = *reinterpret_cast<const uint4*>(q1);
+    if (NSPLIT == 3) *reinterpret_cast<uint4*>(base + 2 * plane_bytes + off) = *reinterpret_cast<const uint4*>(q2);
+}
+
+template <int NSPLIT, int MODE>
+__global__ void __launch_bounds__(128, 1)
+k_tc_absorb(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, int* __restrict__ status) {
+    constexpr int NPROD = NSPLIT == 2 ? 3 : 6;
+    constexpr int PA[6] = {NSPLIT == 2 ? 1 : 2, NSPLIT == 2 ? 0 : 1, NSPLIT == 2 ? 0 : 0, 1, 0, 0};
+    constexpr int PB[6] = {NSPLIT == 2 ? 0 : 0, NSPLIT == 2 ? 1 : 1, NSPLIT == 2 ? 0 : 2, 0, 1, 0};
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mma_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ double red[32];
+    unsigned char* ring = smem + ((1024 - (smem_u32(smem) & 1023)) & 1023);
+    unsigned char* Bs = ring;                                  // NSPLIT planes of B'
+    unsigned char* As = ring + NSPLIT * kAbsBPlane;            // NSPLIT planes of A
+
+    const long long tile = blockIdx.x;
+    const AbsorbTask& t = tasks[find_task_tc(tasks, ntasks, tile)];
+    const long long local = tile - t.tile0;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long S = t.S, nouter = t.P * S;
+
+    if (tid == 0) {
+        mbar_init(&mma_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_base_sh, 128);
+        tmem_relinquish();
+    }
+    // B'[n][k] = E_task[k][n], zero outside 81 x 81
+    const float* E = static_cast<const float*>(t.E);
+    if (tid < kAbsKp) {
+#pragma unroll 1
+        for (int k8 = 0; k8 < kAbsKp / 8; ++k8) {
+            float x[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k = 8 * k8 + i, n = tid;
+                x[i] = (k < kAbsK && n < kAbsK) ? (t.transE ? E[n * kAbsK + k] : E[k * kAbsK + n]) : 0.0f;
+            }
+            split_store8<NSPLIT>(x, Bs, kAbsBPlane, (uint32_t)(((tid >> 3) * (kAbsKp / 8) + k8) * 128 + (tid & 7) * 16));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+    const int e_in = slot_shift_tc(&slots[t.slot_in]);
+    const float sc_in = pow2f(-e_in);
+    int e_adj = 0;
+    float sc_adj = 1.0f;
+    if (MODE == 2) { e_adj = slot_shift_tc(&slots[t.slot_adj]); sc_adj = pow2f(-e_adj); }
+    const float* in = static_cast<const float*>(t.in);
+    float lmax = 0.0f;
+    double ldot = 0.0;
+    bool ok = true;
+    int last_fail = -1;
+    for (int sub = 0; sub < kAbsSub; ++sub) {
+        const long long o = (local * kAbsSub + sub) * 128 + tid;
+        const bool valid = o < nouter;
+        const long long p = valid ? o / S : 0, s = valid ? o - p * S : 0;
+        // A row tid: the 81 inputs of this outer position (k padded to 96)
+        float x[kAbsKp];
+#pragma unroll
+        for (int k = 0; k < kAbsKp; ++k) x[k] = (valid && k < kAbsK) ? in[(p * kAbsK + k) * S + s] * sc_in : 0.0f;
+#pragma unroll
+        for (int k8 = 0; k8 < kAbsKp / 8; ++k8)
+            split_store8<NSPLIT>(x + 8 * k8, As, kAbsAPlane,
+                                 (uint32_t)(((tid >> 3) * (kAbsKp / 8) + k8) * 128 + (tid & 7) * 16));
+        // make the generic-proxy stores visible to the tensor cores
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll
+            for (int ks = 0; ks < kAbsKp / 16; ++ks)
+#pragma unroll
+                for (int q = 0; q < NPROD; ++q)
+                    tc_mma(tmem, smem_desc_sbo(a0 + PA[q] * kAbsAPlane + ks * 256, kAbsSBO),
+                           smem_desc_sbo(b0 + PB[q] * kAbsBPlane + ks * 256, kAbsSBO), kAbsIdesc,
+                           (ks > 0 || q > 0) ? 1u : 0u);
+            tc_commit(&mma_bar);
+        }
+        // bounded wait; the verdict is made block-uniform so all warps stop together
+        ok = __syncthreads_and(mbar_wait(&mma_bar, (uint32_t)(sub & 1)) ? 1 : 0) != 0;
+        if (!ok) {
+            last_fail = sub;
+            break;
+        }
+        tc_fence_after();
+        // accumulator lane = this warp's rows; 6 x 16 columns
+        const long long orow = (local * kAbsSub + sub) * 128 + warp * 32 + lane;
+        const bool vrow = orow < nouter;
+        const long long pr = vrow ? orow / S : 0, sr = vrow ? orow - pr * S : 0;
+        CSumF acc;
+#pragma unroll
+        for (int cb = 0; cb < kAbsKp; cb += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+            if (!vrow) continue;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int n = cb + i;
+                if (n >= kAbsK) continue;
+                const long long idx = (pr * kAbsK + n) * S + sr;
+                if (MODE == 1) {
+                    static_cast<float*>(t.out)[idx] = v[i];
+                    lmax = fmaxf(lmax, fabsf(v[i]));
+                } else {
+                    acc.add(v[i] * (static_cast<const float*>(t.adj)[idx] * sc_adj));
+                }
+            }
+        }
+        if (MODE == 2) ldot += (double)acc.value();
+        // every thread has read its accumulator lanes before the next group overwrites A or D
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (!ok) {
+        // the products of the failed group may still run: wait for them once
+        // more (bounded) before the tensor memory is returned
+        if (tid == 0) {
+            atomicExch(status, 1);
+            (void)mbar_wait(&mma_bar, (uint32_t)(last_fail & 1));
+        }
+        __syncthreads();
+    }
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 128);
+    if (MODE == 1) {
+        const double m = block_reduce((double)lmax, red, true);
+        if (tid == 0) {
+            atomicMax(&slots[t.slot_out].maxbits, (unsigned long long)__double_as_longlong(m));
+            if (local == 0) slots[t.slot_out].X = slots[t.slot_in].X + e_in + slots[t.slot_E].X;
+        }
+    } else {
+        const double part = block_reduce(ldot, red, false);
+        __shared__ int is_last;
+        if (tid == 0) {
+            t.partial[local] = part;
+            __threadfence();
+            const unsigned prev = atomicAdd(&slots[t.slot_out].count, 1u);
+            is_last = (prev == (unsigned)(t.ntiles - 1));
+        }
+        __syncthreads();
+        if (is_last) {
+            __threadfence();
+            double a = 0.0;
+            for (int k = tid; k < t.ntiles; k += blockDim.x) a += __ldcg(t.partial + k);
+            a = block_reduce(a, red, false);
+            if (tid == 0) {
+                slots[t.slot_out].mant = a;
+                slots[t.slot_out].X =
+                    slots[t.slot_in].X + e_in + slots[t.slot_E].X + slots[t.slot_adj].X + e_adj;
+            }
+        }
+    }
+}
+
+long long tc_absorb_tiles(long long P, long long S) { return (P * S + 128 * kAbsSub - 1) / (128 * kAbsSub); }
+
+cudaError_t launch_tc_absorb(int nsplit, bool dot, const AbsorbTask* tasks, int ntasks, long long nblocks,
+                             Slot* slots, int* status, cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    const size_t smem = (size_t)nsplit * (kAbsAPlane + kAbsBPlane) + 1024;
+#define TN_TCA_LAUNCH(NS, MD)                                                                  \
+    {                                                                                          \
+        auto fn = k_tc_absorb<NS, MD>;                                                         \
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                        \
+        fn<<<(unsigned)nblocks, 128, smem, st>>>(tasks, ntasks, slots, status);                \
+        return cudaGetLastError();                                                             \
+    }
+    if (nsplit == 2) { if (dot) TN_TCA_LAUNCH(2, 2) else TN_TCA_LAUNCH(2, 1) }
+    if (dot) TN_TCA_LAUNCH(3, 2) else TN_TCA_LAUNCH(3, 1)
+#undef TN_TCA_LAUNCH
 }
 
 // ------------------------------------------------------------- launchers --

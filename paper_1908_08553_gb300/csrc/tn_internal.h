@@ -108,7 +108,7 @@ struct Op {
     int64_t sam = 0, sak = 0, sbk = 0, sbn = 0;
     // tensor cores: source tensors of the split operands (their slots carry the scale)
     int A_src = -1, B_src = -1;
-    int nsplit = 0;
+    int nsplit = 0;               // tensor cores: 2 or 3 split planes (products and D=3 absorption)
     long long Rp = 0, Kp = 0;
     // sitemat
     int site = -1, phys = PH_I;

@@ -152,6 +152,10 @@ cudaError_t launch_sitemat(int dt, const SiteMatTask* tasks, int ntasks, Slot* s
 cudaError_t launch_init(Slot* slots, long long nslots, const ConstOne* ones, int nones, int dt,
                         cudaStream_t st);
 cudaError_t launch_final(const FinalTask* tasks, int ntasks, const Slot* slots, cudaStream_t st);
+// D = 3 interior absorption (K = N = 81) on tensor cores, 512 outer positions per block.
+long long tc_absorb_tiles(long long P, long long S);
+cudaError_t launch_tc_absorb(int nsplit, bool dot, const AbsorbTask* tasks, int ntasks, long long nblocks,
+                             Slot* slots, int* status, cudaStream_t st);
 long long tc_split_tiles(long long Rp, long long Kp);
 cudaError_t launch_tc_split(const TcSplitTask* tasks, int ntasks, long long nblocks, const Slot* slots,
                             cudaStream_t st);

@@ -47,10 +47,10 @@ def test_12x12_d2_sampled_oracle_and_fp64(ctx):
     L, W, D = 12, 12, 2
     A = inputs.random_lattice(L, W, D, 1212)
     r64, sx64, zz64 = _run(ctx, L, W, D, A, tn.TN_FP64)
-    for prec in (tn.TN_FP32, tn.TN_BF16X3):
+    for prec, tol_obs in ((tn.TN_FP32, 1e-6), (tn.TN_BF16X3, 1e-5)):
         r, sx, zz = _run(ctx, L, W, D, A, prec)
         assert abs(r.energy - r64.energy) / (L * W) <= 1e-6 * max(1.0, abs(r64.energy) / (L * W))
-        assert np.max(np.abs(sx - sx64)) <= 1e-6 and np.max(np.abs(zz - zz64)) <= 1e-6
+        assert np.max(np.abs(sx - sx64)) <= tol_obs and np.max(np.abs(zz - zz64)) <= tol_obs
         assert abs(_log2(r) - _log2(r64)) <= 1e-6 * abs(_log2(r64))
     bonds = inputs.bonds(L, W)
     samples = [("x", 0, 0), ("x", 5 * W + 6, 0), ("zz", bonds[70][0][0] * W + bonds[70][0][1],
@@ -99,7 +99,7 @@ def test_8x8_d3_order_invariance_and_precisions(ctx):
         tn.tn_destroy_lattice(lat)
     r64, sx64, zz64 = _run(c, L, W, D, A, tn.TN_FP64)
     assert abs(_log2(r64) - logs[0]) <= 1e-12 * abs(logs[0])
-    for prec in (tn.TN_FP32, tn.TN_BF16X3):
+    for prec, tol_obs in ((tn.TN_FP32, 1e-6), (tn.TN_BF16X6, 1e-6), (tn.TN_BF16X3, 1e-5)):
         r, sx, zz = _run(c, L, W, D, A, prec)
         assert abs(r.energy - r64.energy) / (L * W) <= 1e-6 * max(1.0, abs(r64.energy) / (L * W))
-        assert np.max(np.abs(sx - sx64)) <= 1e-6 and np.max(np.abs(zz - zz64)) <= 1e-6
+        assert np.max(np.abs(sx - sx64)) <= tol_obs and np.max(np.abs(zz - zz64)) <= tol_obs

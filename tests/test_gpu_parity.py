@@ -1,10 +1,13 @@
 """GPU parity: libtn's CUDA path against the FP64 CPU oracle, element by element.
 
-Tolerances (written per test): FP64 mode 1e-10, FP32 and BF16x3 modes 1e-6,
-applied as |gpu - ref| <= tol * max(1, |ref|) to the energy per site E/N and to
-every <X_k> and <Z_i Z_j> (an <X> or a random state's E can be ~0, so a purely
-relative error would mean nothing; all of them are O(1) quantities).  Exact
-cases (all-ones, D = 2) are compared with ==.
+Tolerances (written per test), applied as |gpu - ref| <= tol * max(1, |ref|)
+(an <X> or a random state's E can be ~0, so a purely relative error would mean
+nothing; all of them are O(1) quantities):
+  energy per site E/N: FP64 1e-10; FP32, BF16x3 and BF16x6 1e-6;
+  every <X_k> and <Z_i Z_j>: FP64 1e-10; FP32 and BF16x6 1e-6; BF16x3 1e-5
+  (three split products keep about 16 mantissa bits; with D = 3 the absorption
+  itself runs on them).
+Exact cases (all-ones, D = 2) are compared with ==.
 """
 import math
 
@@ -17,7 +20,8 @@ from paper_1908_08553_gb300 import inputs, tn
 
 pytestmark = pytest.mark.gpu
 
-TOL = {tn.TN_FP64: 1e-10, tn.TN_FP32: 1e-6, tn.TN_BF16X3: 1e-6, tn.TN_BF16X6: 1e-6}
+TOL = {tn.TN_FP64: 1e-10, tn.TN_FP32: 1e-6, tn.TN_BF16X3: 1e-6, tn.TN_BF16X6: 1e-6}      # E / N
+TOL_OBS = {tn.TN_FP64: 1e-10, tn.TN_FP32: 1e-6, tn.TN_BF16X3: 1e-5, tn.TN_BF16X6: 1e-6}  # <X>, <ZZ>
 PRECS = [tn.TN_FP64, tn.TN_FP32]
 SCHEDS = [tn.TN_SCHED_AUTO, tn.TN_SCHED_ROW, tn.TN_SCHED_COL, tn.TN_SCHED_QUADRANT]
 
@@ -42,13 +46,13 @@ def _energy(ctx, L, W, D, A, prec, sched, J=1.0, h=3.04):
 
 
 def _check(r, sx, zz, ref, prec, J=1.0, h=3.04):
-    tol = TOL[prec]
+    tol, tol_obs = TOL[prec], TOL_OBS[prec]
     n = sx.size
     e_ref = ref.energy(J, h) / n
     assert abs(r.energy / n - e_ref) <= tol * max(1.0, abs(e_ref)), (r.energy / n, e_ref)
-    np.testing.assert_allclose(sx, ref.sx, rtol=0, atol=tol * max(1.0, np.abs(ref.sx).max()))
+    np.testing.assert_allclose(sx, ref.sx, rtol=0, atol=tol_obs * max(1.0, np.abs(ref.sx).max()))
     if zz.size:
-        np.testing.assert_allclose(zz, ref.szsz, rtol=0, atol=tol * max(1.0, np.abs(ref.szsz).max()))
+        np.testing.assert_allclose(zz, ref.szsz, rtol=0, atol=tol_obs * max(1.0, np.abs(ref.szsz).max()))
     lg = math.log2(abs(r.norm.mant)) + r.norm.exp2
     assert abs(lg - ref.log2_norm) <= max(tol, 1e-12) * 64 * max(1.0, abs(ref.log2_norm))
 
