@@ -137,7 +137,7 @@ public:
         auto key = std::make_tuple(src, R, Kd, sr, sk);
         auto it = split_.find(key);
         if (it != split_.end()) return it->second;
-        const int64_t Rp = (R + 127) / 128 * 128, Kp = (Kd + 63) / 64 * 64;
+        const int64_t Rp = (R + kTcRowPad - 1) / kTcRowPad * kTcRowPad, Kp = (Kd + 63) / 64 * 64;
         const int level = level_of(src) + 1;
         // BF16 planes counted in 4-byte units of the FP32 arena
         const int out = tensor((int64_t)pg_.nsplit * Rp * Kp / 2, level);
@@ -172,8 +172,8 @@ public:
             op.gm = M; op.gn = N; op.gk = K;
             op.Kp = (K + 63) / 64 * 64;
             op.nsplit = pg_.nsplit;
-            op.bytes = (double)pg_.nsplit * ((M + 127) / 128 * 128 + (N + 127) / 128 * 128) * op.Kp * 2 +
-                       (double)M * N * 4;
+            op.bytes = (double)pg_.nsplit * ((M + kTcRowPad - 1) / kTcRowPad + (N + kTcRowPad - 1) / kTcRowPad) *
+                           kTcRowPad * op.Kp * 2 + (double)M * N * 4;
             op.macs = (double)M * N * K;
             use(Ap, lv); use(Bp, lv); use(A, lv); use(B, lv);
             if (Cd >= 0) use(Cd, lv);

@@ -78,7 +78,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
             } else if (op.kind == OP_GEMM || op.kind == OP_GEMM_DOT) {
                 var = gemm_variant(b->dt, op.gm, op.gn, op.gk, op.sam, op.sak, op.sbk, op.sbn);
             } else if (op.kind == OP_TC_GEMM || op.kind == OP_TC_GEMM_DOT) {
-                var = op.nsplit;
+                var = op.nsplit * 1000 + tc_gemm_bn(op.nsplit, op.gn);   // planes and tile width
             }
             groups[std::make_tuple(op.level, (int)op.kind, K, N, var)].push_back({mi, oi});
         }
@@ -119,8 +119,10 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 npart += gemm_tiles_v(var, op.gm, op.gn, &tn_) * gemm_ksplit(var, true, op.gk);
             }
             else if (kind == OP_DOT) npart += (op.gm + kDotPerBlock - 1) / kDotPerBlock;
-            else if (kind == OP_TC_GEMM_DOT)
-                npart += ((op.gm + 127) / 128) * ((op.gn + 127) / 128) * ((op.Kp + kGemmKSlice - 1) / kGemmKSlice);
+            else if (kind == OP_TC_GEMM_DOT) {
+                const int bn = std::get<4>(kv.first) % 1000;
+                npart += ((op.gm + 127) / 128) * ((op.gn + bn - 1) / bn) * ((op.Kp + kGemmKSlice - 1) / kGemmKSlice);
+            }
         }
     }
     lay.npart = npart;
@@ -240,18 +242,21 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 TcGemmTask t{};
                 t.A = tensor_ptr(r.member, op.A);
                 t.B = tensor_ptr(r.member, op.B);
-                const long long Mp = (op.gm + 127) / 128 * 128, Np = (op.gn + 127) / 128 * 128;
-                t.a_plane_bytes = Mp * op.Kp * 2;
-                t.b_plane_bytes = Np * op.Kp * 2;
+                const int bn = L.variant % 1000;
+                const long long Ma = (op.gm + kTcRowPad - 1) / kTcRowPad * kTcRowPad;
+                const long long Nb = (op.gn + kTcRowPad - 1) / kTcRowPad * kTcRowPad;
+                t.a_plane_bytes = Ma * op.Kp * 2;
+                t.b_plane_bytes = Nb * op.Kp * 2;
                 t.M = op.gm; t.N = op.gn; t.Kp = op.Kp;
                 t.slot_A = slot_of(r.member, op.A_src);
                 t.slot_B = slot_of(r.member, op.B_src);
                 t.slot_C = slot_of(r.member, op.out);
-                t.tiles_n = (int)(Np / 128);
+                t.tiles_m = (op.gm + 127) / 128;
+                t.tiles_n = (int)((op.gn + bn - 1) / bn);
                 const long long ksp = kind == OP_TC_GEMM_DOT ? (op.Kp + kGemmKSlice - 1) / kGemmKSlice : 1;
                 t.ksplit = (int)ksp;
-                t.kchunks = ksp > 1 ? kGemmKSlice / 64 : op.Kp / 64;
-                const long long nt = (Mp / 128) * (Np / 128) * ksp;
+                t.kchunks = ksp > 1 ? kGemmKSlice / kTcChunk : op.Kp / kTcChunk;
+                const long long nt = t.tiles_m * t.tiles_n * ksp;
                 t.ntiles = (int)nt;
                 t.tile0 = tile;
                 if (kind == OP_TC_GEMM_DOT) {
@@ -494,8 +499,8 @@ cudaError_t issue(tn_batch* b, cudaStream_t st, std::vector<std::pair<cudaEvent_
                 break;
             case OP_TC_GEMM:
             case OP_TC_GEMM_DOT:
-                e = launch_tc_gemm(L.variant, L.kind == OP_TC_GEMM_DOT, static_cast<const TcGemmTask*>(tp),
-                                   L.ntasks, L.nblocks, slots, status, st);
+                e = launch_tc_gemm(L.variant / 1000, L.kind == OP_TC_GEMM_DOT, L.variant % 1000,
+                                   static_cast<const TcGemmTask*>(tp), L.ntasks, L.nblocks, slots, status, st);
                 break;
         }
         if (ev) cudaEventRecord((*ev)[li].second, st);

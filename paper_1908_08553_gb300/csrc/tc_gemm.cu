@@ -35,8 +35,9 @@ namespace tn {
 
 namespace {
 
-constexpr int kTcM = 128, kTcN = 128, kTcK = 64;      // tile rows, tile cols, k per chunk
-constexpr uint32_t kBlockBytes = kTcM * kTcK * 2;     // one 128 x 64 BF16 block
+constexpr int kTcM = 128, kTcN = 128, kTcK = kTcChunk;   // tile rows, tile cols, k per chunk
+constexpr uint32_t kBlockBytes = kTcM * kTcK * 2;     // one 128 x 32 BF16 block (8 KiB)
+constexpr uint32_t kTcSBO = (kTcK / 8) * 128;         // next 8-row group inside a block
 constexpr long long kWaitCycles = 4000000000LL;       // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -131,7 +132,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFF);             // start address
     d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;        // LBO: next core matrix along k
-    d |= (uint64_t)((1024u >> 4) & 0x3FFF) << 32;       // SBO: next 8-row group
+    d |= (uint64_t)((kTcSBO >> 4) & 0x3FFF) << 32;      // SBO: next 8-row group
     d |= (uint64_t)1 << 46;                             // descriptor version (tcgen05)
     return d;                                           // base offset 0, no swizzle
 }
@@ -209,9 +210,10 @@ k_tc_split(const TcSplitTask* __restrict__ tasks, int ntasks, const Slot* __rest
         const long long k = ko * 8 + kk;
         x[kk] = (r < t.R && k < t.Kd) ? src[r * t.sr + k * t.sk] * sc : 0.0f;
     }
+    constexpr int kOct = kTcK / 8;                    // 8-wide k groups per chunk
     const long long nchunks = t.Kp / kTcK;
-    const long long rb = r / kTcM, rr = r % kTcM, c = ko / 8, ki = ko % 8;
-    const long long off = (rb * nchunks + c) * (long long)kBlockBytes + (((rr / 8) * 8 + ki) * 8 + (rr % 8)) * 16;
+    const long long rb = r / kTcM, rr = r % kTcM, c = ko / kOct, ki = ko % kOct;
+    const long long off = (rb * nchunks + c) * (long long)kBlockBytes + (((rr / 8) * kOct + ki) * 8 + (rr % 8)) * 16;
     __align__(16) __nv_bfloat16 p0[8], p1[8], p2[8];
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) {
@@ -231,15 +233,19 @@ k_tc_split(const TcSplitTask* __restrict__ tasks, int ntasks, const Slot* __rest
 
 // ------------------------------------------------------------------ mma ---
 
-template <int NSPLIT, bool DOT>
+template <int NSPLIT, bool DOT, int BN>
 __global__ void __launch_bounds__(128, 1)
 k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, int* __restrict__ status) {
-    constexpr int STAGES = NSPLIT == 2 ? 3 : 2;
-    constexpr uint32_t kStageBytes = 2u * NSPLIT * kBlockBytes;    // A planes then B planes
+    constexpr int NB = BN / kTcM;                                   // 128-row B blocks per tile
+    constexpr uint32_t kStageBytes = NSPLIT * (1 + NB) * kBlockBytes;   // A planes then B planes
+    constexpr int STAGES = (196608u / kStageBytes) >= 6 ? 6 : (int)(196608u / kStageBytes);
     constexpr int NPROD = NSPLIT == 2 ? 3 : 6;
     // products (plane of A, plane of B), smallest terms first
     constexpr int PA[6] = {NSPLIT == 2 ? 1 : 2, NSPLIT == 2 ? 0 : 1, NSPLIT == 2 ? 0 : 0, 1, 0, 0};
     constexpr int PB[6] = {NSPLIT == 2 ? 0 : 0, NSPLIT == 2 ? 1 : 1, NSPLIT == 2 ? 0 : 2, 0, 1, 0};
+    constexpr uint32_t kIdescN = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                 ((uint32_t)(kTcM >> 4) << 24);
+    constexpr int kGroup = 8;                                       // tile rows sharing A in L2
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
     __shared__ uint32_t tmem_base_sh;
@@ -250,7 +256,11 @@ k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
     const TcGemmTask& t = tasks[find_task_tc(tasks, ntasks, tile)];
     const long long local = tile - t.tile0;
     const long long mn = local / t.ksplit, ks = local % t.ksplit;
-    const long long tm = mn / t.tiles_n, tn_ = mn % t.tiles_n;
+    // grouped rasterisation: kGroup tile rows, columns outer, rows inner
+    const long long per_group = (long long)kGroup * t.tiles_n;
+    const long long g = mn / per_group, gi = mn % per_group;
+    const long long grows = min((long long)kGroup, t.tiles_m - g * kGroup);
+    const long long tm = g * kGroup + gi % grows, tn_ = gi / grows;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long nchunks_all = t.Kp / kTcK;       // chunks of the whole k range (layout)
     const long long cbeg = ks * t.kchunks;
@@ -266,7 +276,7 @@ k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 0) {
-        tmem_alloc(&tmem_base_sh, kTcN);
+        tmem_alloc(&tmem_base_sh, BN);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -275,7 +285,7 @@ k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
     const uint32_t tmem = tmem_base_sh;
 
     const char* Ab = static_cast<const char*>(t.A) + (tm * nchunks_all + cbeg) * (long long)kBlockBytes;
-    const char* Bb = static_cast<const char*>(t.B) + (tn_ * nchunks_all + cbeg) * (long long)kBlockBytes;
+    const char* Bb = static_cast<const char*>(t.B) + (tn_ * NB * nchunks_all + cbeg) * (long long)kBlockBytes;
     int my_fail = 0;
     int armed[STAGES];
 #pragma unroll
@@ -290,8 +300,11 @@ k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
             mbar_expect_tx(&full_bar[s], kStageBytes);
             for (int p = 0; p < NSPLIT; ++p) {
                 bulk_g2s(st + p * kBlockBytes, Ab + p * t.a_plane_bytes + c * kBlockBytes, kBlockBytes, &full_bar[s]);
-                bulk_g2s(st + (NSPLIT + p) * kBlockBytes, Bb + p * t.b_plane_bytes + c * kBlockBytes, kBlockBytes,
-                         &full_bar[s]);
+                // the NB row blocks of B sit back to back, so one descriptor spans them
+                for (int h = 0; h < NB; ++h)
+                    bulk_g2s(st + (NSPLIT + p * NB + h) * kBlockBytes,
+                             Bb + p * t.b_plane_bytes + (h * nchunks_all + c) * kBlockBytes, kBlockBytes,
+                             &full_bar[s]);
             }
         }
     } else if (warp == 1 && lane == 0) {
@@ -302,12 +315,12 @@ k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
             tc_fence_after();
             const uint32_t st = smem_u32(ring + s * kStageBytes);
 #pragma unroll
-            for (int ks = 0; ks < kTcK / 16; ++ks) {
+            for (int kk = 0; kk < kTcK / 16; ++kk) {
 #pragma unroll
                 for (int q = 0; q < NPROD; ++q) {
-                    const uint64_t da = smem_desc(st + PA[q] * kBlockBytes + ks * 256);
-                    const uint64_t db = smem_desc(st + (NSPLIT + PB[q]) * kBlockBytes + ks * 256);
-                    tc_mma(tmem, da, db, kIdesc, (c > 0 || ks > 0 || q > 0) ? 1u : 0u);
+                    const uint64_t da = smem_desc(st + PA[q] * kBlockBytes + kk * 256);
+                    const uint64_t db = smem_desc(st + (NSPLIT + PB[q] * NB) * kBlockBytes + kk * 256);
+                    tc_mma(tmem, da, db, kIdescN, (c > 0 || kk > 0 || q > 0) ? 1u : 0u);
                 }
             }
             tc_commit(&empty_bar[s]);
@@ -329,7 +342,7 @@ k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
     __syncthreads();
     tc_fence_after();
     const long long row = tm * kTcM + warp * 32 + lane;
-    const long long n0 = tn_ * kTcN;
+    const long long n0 = tn_ * BN;
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
     const int eA = slot_shift_tc(&slots[t.slot_A]), eB = slot_shift_tc(&slots[t.slot_B]);
     double mx = 0.0, dsum = 0.0;
@@ -337,7 +350,7 @@ k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
     float sD = 1.0f;
     int eD = 0;
     if (DOT) { eD = slot_shift_tc(&slots[t.slot_D]); sD = pow2f(-eD); }
-    for (int cb = 0; cb < kTcN; cb += 16) {
+    for (int cb = 0; cb < BN; cb += 16) {
         float v[16];
         tmem_ld16(lane_addr + (uint32_t)cb, v);
         if (!good || row >= t.M) continue;
@@ -365,7 +378,7 @@ k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kTcN);
+    if (warp == 0) tmem_dealloc(tmem, BN);
     if (!DOT) {
         const double m = block_reduce(mx, red, true);
         if (threadIdx.x == 0) {
@@ -630,21 +643,26 @@ cudaError_t launch_tc_split(const TcSplitTask* tasks, int ntasks, long long nblo
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_gemm(int nsplit, bool dot, const TcGemmTask* tasks, int ntasks, long long nblocks,
+int tc_gemm_bn(int nsplit, long long N) { return (nsplit == 2 && N > 128) ? 256 : 128; }
+
+cudaError_t launch_tc_gemm(int nsplit, bool dot, int bn, const TcGemmTask* tasks, int ntasks, long long nblocks,
                            Slot* slots, int* status, cudaStream_t st) {
     if (nblocks <= 0) return cudaSuccess;
-    const int stages = nsplit == 2 ? 3 : 2;
-    const size_t smem = (size_t)stages * 2 * nsplit * kBlockBytes + 1024;
-#define TN_TC_LAUNCH(NS, DT)                                                                   \
+    const int nb = bn / kTcM;
+    const uint32_t stage = (uint32_t)nsplit * (1 + nb) * kBlockBytes;
+    const int stages = (196608u / stage) >= 6 ? 6 : (int)(196608u / stage);
+    const size_t smem = (size_t)stages * stage + 1024;
+#define TN_TC_LAUNCH(NS, DT, B)                                                                \
     {                                                                                          \
-        auto fn = k_tc_gemm<NS, DT>;                                                           \
+        auto fn = k_tc_gemm<NS, DT, B>;                                                        \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                        \
         fn<<<(unsigned)nblocks, 128, smem, st>>>(tasks, ntasks, slots, status);                \
         return cudaGetLastError();                                                             \
     }
-    if (nsplit == 2) { if (dot) TN_TC_LAUNCH(2, true) else TN_TC_LAUNCH(2, false) }
-    if (dot) TN_TC_LAUNCH(3, true) else TN_TC_LAUNCH(3, false)
+    if (nsplit == 2 && bn == 256) { if (dot) TN_TC_LAUNCH(2, true, 256) else TN_TC_LAUNCH(2, false, 256) }
+    if (nsplit == 2) { if (dot) TN_TC_LAUNCH(2, true, 128) else TN_TC_LAUNCH(2, false, 128) }
+    if (dot) TN_TC_LAUNCH(3, true, 128) else TN_TC_LAUNCH(3, false, 128)
 #undef TN_TC_LAUNCH
 }
 

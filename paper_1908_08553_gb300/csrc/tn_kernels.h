@@ -123,6 +123,7 @@ struct TcGemmTask {
     long long M, N, Kp;
     long long tile0;
     long long kchunks;            // 64-wide k chunks per tile (split along k in dot mode)
+    long long tiles_m;
     int tiles_n, ntiles;
     int ksplit;
     int slot_A, slot_B, slot_C, slot_D;   // slots of the FP32 sources / result
@@ -160,8 +161,14 @@ long long tc_split_tiles(long long Rp, long long Kp);
 cudaError_t launch_tc_split(const TcSplitTask* tasks, int ntasks, long long nblocks, const Slot* slots,
                             cudaStream_t st);
 // status: set to 1 if a bounded wait inside the kernel timed out.
-cudaError_t launch_tc_gemm(int nsplit, bool dot, const TcGemmTask* tasks, int ntasks, long long nblocks,
+// Output tile 128 x bn, bn = tc_gemm_bn(nsplit, N) (256 for 2 planes and N > 128).
+int tc_gemm_bn(int nsplit, long long N);
+cudaError_t launch_tc_gemm(int nsplit, bool dot, int bn, const TcGemmTask* tasks, int ntasks, long long nblocks,
                            Slot* slots, int* status, cudaStream_t st);
+// Rows of every split operand are padded to a multiple of this.
+constexpr long long kTcRowPad = 256;
+// Reduction (k) width of one staged block of a split operand.
+constexpr int kTcChunk = 32;
 cudaError_t launch_absorb_plain(int dt, const void* in, const void* E, void* out, long long P,
                                 int K, int N, long long S, cudaStream_t st);
 // <absorb(in, E), adj> into *result (device).  scratch: 16 B counter header
