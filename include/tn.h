@@ -148,6 +148,12 @@ tn_status tn_footprint(const tn_lattice *lat, tn_schedule sched, tn_precision pr
  * cut (i, j) is taken on the transposed lattice.  Writes at most cap words
  * and the full length to *n. */
 tn_status tn_plan(const tn_lattice *lat, tn_schedule sched, int64_t *out, size_t cap, size_t *n);
+/* As tn_plan for a given work.  TN_WORK_NORM is tn_plan.  TN_WORK_ENERGY keeps
+ * every chain state for its environment sweeps, so among the cuts with the
+ * smallest bottleneck it prefers the smallest summed chain output, then the
+ * fewest multiply-adds (word [6] is still the norm's multiply-adds). */
+tn_status tn_plan_work(const tn_lattice *lat, tn_schedule sched, tn_work work, int64_t *out, size_t cap,
+                       size_t *n);
 
 /* ---------------------------------------------------------- contraction -- */
 

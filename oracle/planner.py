@@ -26,6 +26,9 @@ Reading used here (the paper gives no formula for the candidates):
     d = D^2 per bond) of any of these pairwise contractions;
   * ties: fewest multiply-adds, then the cut nearest the middle
     (|2i - L'| + |2j - W'|), then o, then i, then j (all smallest first);
+    for an energy evaluation, whose environment method keeps every chain
+    state, the summed size of all chain-step outputs is compared right after
+    the bottleneck;
   * integer products and sums saturate at 2^62 (such plans never fit memory).
 
 Forced schedules: ROW = (o=0, i=L, j=W); COL = (o=1, i=W, j=L);
@@ -113,17 +116,19 @@ def evaluate(L: int, W: int, D: int, o: int, i: int, j: int) -> dict:
     m_size = _pow(hcut, Wp)
     peak = m_size
     mac = 0
+    cached = 0
     for s in steps:
         peak = max(peak, s["n_in"], s["n_out"])
         mac = _add(mac, s["mac"])
+        cached = _add(cached, s["n_out"])
     mac = _add(mac, _mul(m_size, _pow(vcut, i)))        # M_top = TL TR^T
     mac = _add(mac, _mul(m_size, _pow(vcut, Lp - i)))   # M_bot = BL BR^T
     mac = _add(mac, m_size)                             # <M_top, M_bot>
-    return dict(o=o, i=i, j=j, peak=peak, mac=mac, steps=steps,
+    return dict(o=o, i=i, j=j, peak=peak, mac=mac, steps=steps, cached=cached,
                 centre=abs(2 * i - Lp) + abs(2 * j - Wp))
 
 
-def plan(L: int, W: int, D: int, schedule: int = AUTO) -> dict:
+def plan(L: int, W: int, D: int, schedule: int = AUTO, energy: bool = False) -> dict:
     if schedule == ROW:
         return evaluate(L, W, D, 0, L, W)
     if schedule == COL:
@@ -136,7 +141,7 @@ def plan(L: int, W: int, D: int, schedule: int = AUTO) -> dict:
         for i in range(Lp + 1):
             for j in range(Wp + 1):
                 ev = evaluate(L, W, D, o, i, j)
-                key = (ev["peak"], ev["mac"], ev["centre"], o, i, j)
+                key = (ev["peak"], ev["cached"] if energy else 0, ev["mac"], ev["centre"], o, i, j)
                 if best_key is None or key < best_key:
                     best, best_key = ev, key
     return best

@@ -249,9 +249,16 @@ tn_status tn_footprint(const tn_lattice* lat, tn_schedule sched, tn_precision pr
 }
 
 tn_status tn_plan(const tn_lattice* lat, tn_schedule sched, int64_t* out, size_t cap, size_t* n) {
+    return tn_plan_work(lat, sched, TN_WORK_NORM, out, cap, n);
+}
+
+tn_status tn_plan_work(const tn_lattice* lat, tn_schedule sched, tn_work work, int64_t* out, size_t cap,
+                       size_t* n) {
     TN_GUARD_BEGIN
-    if (!lat || !n || sched < TN_SCHED_AUTO || sched > TN_SCHED_QUADRANT) return TN_ERR_INVALID;
-    const Plan p = plan_choose(lat->L, lat->W, lat->D, sched);
+    if (!lat || !n || sched < TN_SCHED_AUTO || sched > TN_SCHED_QUADRANT || work < TN_WORK_NORM ||
+        work > TN_WORK_ENERGY)
+        return TN_ERR_INVALID;
+    const Plan p = plan_choose(lat->L, lat->W, lat->D, sched, work);
     std::vector<int64_t> w = {1, p.o, p.i, p.j, 0, p.peak, p.mac};
     int64_t nsteps = 0;
     for (int q = 0; q < 4; ++q)

@@ -13,7 +13,9 @@
 // M_top = TL TR^T, M_bot = BL BR^T, <M_top, M_bot>.
 // Bottleneck = largest input or output (entries) of those contractions; ties
 // go to fewer multiply-adds, then the cut nearest the middle, then smaller o,
-// i, j.  Integer arithmetic saturates at 2^62.
+// i, j.  For energies (which keep every chain state for the environment
+// method) the second key is the summed size of the chain outputs.  Integer
+// arithmetic saturates at 2^62.
 #include <algorithm>
 #include <climits>
 
@@ -96,6 +98,7 @@ Plan plan_evaluate(int L, int W, int D, int o, int i, int j) {
                 s.mac = sat_mul(sat_mul(sat_mul(s.P, s.S), s.K), s.N);
                 peak = std::max(peak, std::max(s.n_in, s.n_out));
                 mac = sat_add(mac, s.mac);
+                p.chain_elems = sat_add(p.chain_elems, s.n_out);
                 cp.steps.push_back(s);
             }
             rt_done = sat_mul(rt_done, drt(b - 1));
@@ -112,7 +115,7 @@ Plan plan_evaluate(int L, int W, int D, int o, int i, int j) {
     return p;
 }
 
-Plan plan_choose(int L, int W, int D, tn_schedule sched) {
+Plan plan_choose(int L, int W, int D, tn_schedule sched, tn_work work) {
     switch (sched) {
         case TN_SCHED_ROW: return plan_evaluate(L, W, D, 0, L, W);
         case TN_SCHED_COL: return plan_evaluate(L, W, D, 1, W, L);
@@ -126,8 +129,12 @@ Plan plan_choose(int L, int W, int D, tn_schedule sched) {
         for (int i = 0; i <= Lp; ++i)
             for (int j = 0; j <= Wp; ++j) {
                 Plan c = plan_evaluate(L, W, D, o, i, j);
-                auto key = std::make_tuple(c.peak, c.mac, c.centre, c.o, c.i, c.j);
-                auto bkey = std::make_tuple(best.peak, best.mac, best.centre, best.o, best.i, best.j);
+                // energies cache every chain state: among cuts with the same
+                // bottleneck they prefer the smallest cached total
+                const int64_t kc = work == TN_WORK_ENERGY ? c.chain_elems : 0;
+                const int64_t kb = work == TN_WORK_ENERGY ? best.chain_elems : 0;
+                auto key = std::make_tuple(c.peak, kc, c.mac, c.centre, c.o, c.i, c.j);
+                auto bkey = std::make_tuple(best.peak, kb, best.mac, best.centre, best.o, best.i, best.j);
                 if (!have || key < bkey) { best = std::move(c); have = true; }
             }
     }

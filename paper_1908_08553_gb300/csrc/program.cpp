@@ -94,8 +94,12 @@ public:
     }
 
     // out = absorb(in, E) with the shape of step s (transposed: backward sweep).
+    // Ops created while a floor is set start no earlier than that wave (used to
+    // run observable chains in memory-bounded stages).
+    void set_floor(int f) { floor_ = f; }
+
     int absorb(int in, int E, const Step& s, bool trans) {
-        const int level = std::max(level_of(in), level_of(E)) + 1;
+        const int level = std::max({level_of(in), level_of(E), floor_}) + 1;
         const int64_t nout = trans ? s.n_in : s.n_out;
         const int out = tensor(nout, level);
         Op op;
@@ -215,6 +219,7 @@ public:
 private:
     Program& pg_;
     int one_ = -1;
+    int floor_ = 0;
     std::map<std::pair<int, int>, int> E_;
     std::map<std::tuple<int, int64_t, int64_t, int64_t, int64_t>, int> split_;
 };
@@ -285,7 +290,7 @@ std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sc
                                              tn_precision prec, tn_work work) {
     auto pgp = std::make_shared<Program>();
     Program& pg = *pgp;
-    pg.plan = plan_choose(L, W, D, sched);
+    pg.plan = plan_choose(L, W, D, sched, work);
     pg.work = work;
     pg.dt = prec == TN_FP64 ? DT_F64 : DT_F32;
     pg.nsplit = prec == TN_BF16X3 ? 2 : (prec == TN_BF16X6 ? 3 : 0);
@@ -392,20 +397,48 @@ std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sc
         };
         pg.zz_slot.assign(bonds.size(), -1);
         pg.zz_den.assign(bonds.size(), pg.norm_slot);
+        // Bond chains run in stages: a chain whose temporaries would push the
+        // stage above kStageElems starts after every earlier chain has
+        // finished, so the arena reuses their memory (only the amount of
+        // concurrent work changes, not any value).
+        constexpr int64_t kStageElems = int64_t(1) << 27;
+        int64_t stage_used = 0;
+        int stage_floor = 0, stage_end = 0;
+        auto max_out = [&](int q, int t0, int t1) {
+            int64_t m = 0;
+            for (int u = t0; u <= t1; ++u) m = std::max(m, step_of(q, u).n_out);
+            return m;
+        };
+        auto begin_chain = [&](int64_t temp) {
+            if (stage_used > 0 && stage_used + temp > kStageElems) {
+                stage_floor = stage_end;
+                stage_used = 0;
+            }
+            stage_used += temp;
+            bd.set_floor(stage_floor);
+        };
+        auto end_chain = [&](int last_tensor) {
+            stage_end = std::max(stage_end, pg.tensors[last_tensor].level);
+            bd.set_floor(0);
+        };
         for (size_t bi = 0; bi < bonds.size(); ++bi) {
             SiteRef a = where[bonds[bi].first], b = where[bonds[bi].second];
             int v = -1;
             if (a.q == b.q) {
                 if (a.t > b.t) std::swap(a, b);
                 const int q = a.q;
+                begin_chain(2 * max_out(q, a.t, b.t));
                 int x = bd.absorb(F[q][a.t - 1], E_at(q, a.t, PH_Z), step_of(q, a.t), false);
                 for (int u = a.t + 1; u < b.t; ++u) x = bd.absorb(x, E_at(q, u, PH_I), step_of(q, u), false);
                 v = bd.absorb_dot(x, E_at(q, b.t, PH_Z), G[q][b.t], step_of(q, b.t));
+                end_chain(v);
                 pg.zz_den[bi] = norm_at(q, b.t);
             } else {
                 int qa = a.q, qb = b.q;
                 int ta = a.t, tb = b.t;
                 if (qa > qb) { std::swap(qa, qb); std::swap(ta, tb); }
+                const int Ta = (int)pl.corner[qa].steps.size(), Tb = (int)pl.corner[qb].steps.size();
+                begin_chain(2 * max_out(qa, ta, Ta) + 2 * max_out(qb, tb, Tb));
                 const int Za = regrow(qa, ta), Zb = regrow(qb, tb);
                 // each class of cut-crossing bond is normalised by the same fused
                 // product on the unmodified corners (the norm through the same path)
@@ -434,6 +467,7 @@ std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sc
                 } else {
                     throw std::logic_error("bond between non-adjacent corners");
                 }
+                end_chain(v);
             }
             pg.zz_slot[bi] = pg.tensors[v].slot;
         }

@@ -291,7 +291,7 @@ static tn_status take_result(Server* s, uint64_t ticket, tn_result* out, std::un
     if (j->state < 2) return TN_NOT_READY;
     tn_status st = j->status;
     if (st == TN_OK && out) {
-        const Plan p = plan_choose(j->L, j->W, j->D, TN_SCHED_AUTO);
+        const Plan p = plan_choose(j->L, j->W, j->D, TN_SCHED_AUTO, TN_WORK_ENERGY);
         st = result_from_array(j->result.data(), j->L, j->W, j->prec, p, out);
     }
     s->jobs.erase(it);

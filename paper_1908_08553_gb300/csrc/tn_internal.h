@@ -54,13 +54,14 @@ struct Plan {
     int o = 0, i = 0, j = 0;     // orientation and cut
     int Lp = 0, Wp = 0;          // oriented lattice dims
     int64_t peak = 0, mac = 0;
+    int64_t chain_elems = 0;     // summed outputs of all chain steps (what an energy caches)
     int centre = 0;
     CornerPlan corner[4];
     int64_t hb_L = 1, hb_R = 1, vr_T = 1, vr_B = 1;   // ring leg-group sizes
 };
 
 Plan plan_evaluate(int L, int W, int D, int o, int i, int j);
-Plan plan_choose(int L, int W, int D, tn_schedule sched);
+Plan plan_choose(int L, int W, int D, tn_schedule sched, tn_work work = TN_WORK_NORM);
 // oriented coordinates (r', c') of lattice site (r, c)
 void orient(const Plan& p, int r, int c, int* rr, int* cc);
 

@@ -53,6 +53,7 @@ SIGNATURES = {
     "tn_get_site_tensors": (c_int, [c_void_p, c_void_p, c_size_t]),
     "tn_footprint": (c_int, [c_void_p, c_int, c_int, c_int, POINTER(c_size_t)]),
     "tn_plan": (c_int, [c_void_p, c_int, c_void_p, c_size_t, POINTER(c_size_t)]),
+    "tn_plan_work": (c_int, [c_void_p, c_int, c_int, c_void_p, c_size_t, POINTER(c_size_t)]),
     "tn_contract_norm": (c_int, [c_void_p, c_int, c_int, POINTER(tn_scalar)]),
     "tn_expectation": (c_int, [c_void_p, c_int, c_int, c_int, c_int, POINTER(c_double)]),
     "tn_energy": (c_int, [c_void_p, c_double, c_double, c_int, POINTER(tn_result)]),
@@ -188,6 +189,14 @@ def tn_plan(lat, sched: int = TN_SCHED_AUTO) -> np.ndarray:
     check(lib().tn_plan(lat, sched, None, 0, byref(n)), "tn_plan")
     out = np.zeros(n.value, dtype=np.int64)
     check(lib().tn_plan(lat, sched, _ptr(out), out.size, byref(n)), "tn_plan")
+    return out
+
+
+def tn_plan_work(lat, sched: int = TN_SCHED_AUTO, work: int = TN_WORK_ENERGY) -> np.ndarray:
+    n = c_size_t()
+    check(lib().tn_plan_work(lat, sched, work, None, 0, byref(n)), "tn_plan_work")
+    out = np.zeros(n.value, dtype=np.int64)
+    check(lib().tn_plan_work(lat, sched, work, _ptr(out), out.size, byref(n)), "tn_plan_work")
     return out
 
 

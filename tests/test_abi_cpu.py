@@ -66,6 +66,22 @@ def test_planner_bit_exact_vs_oracle(cpu_ctx, L, W, D):
         tn.tn_destroy_lattice(lat)
 
 
+@pytest.mark.parametrize("L,W,D", SHAPES + [(8, 9, 3), (8, 10, 3), (9, 8, 3), (7, 12, 3)])
+def test_energy_planner_bit_exact_vs_oracle(cpu_ctx, L, W, D):
+    lat = tn.tn_create_lattice(cpu_ctx, L, W, D)
+    try:
+        hdr, steps = tn.plan_steps(tn.tn_plan_work(lat, tn.TN_SCHED_AUTO, tn.TN_WORK_ENERGY))
+        p = planner.plan(L, W, D, planner.AUTO, energy=True)
+        assert (hdr["o"], hdr["i"], hdr["j"], hdr["peak"], hdr["mac"]) == (p["o"], p["i"], p["j"], p["peak"], p["mac"])
+        ref = np.array([[s["corner"], s["k"], s["c"], s["r"], s["col"], s["P"], s["K"], s["N"], s["S"]]
+                        for s in p["steps"]], dtype=np.int64).reshape(-1, 9)
+        assert np.array_equal(steps, ref)
+        # the same bottleneck as the norm's plan
+        assert hdr["peak"] == planner.plan(L, W, D)["peak"]
+    finally:
+        tn.tn_destroy_lattice(lat)
+
+
 @pytest.mark.parametrize("L,W,D", [(4, 4, 2), (8, 8, 2), (3, 5, 3)])
 @pytest.mark.parametrize("seed", [0, 1, 12345, 2 ** 63 + 7])
 def test_fill_random_matches_generator(cpu_ctx, L, W, D, seed):
