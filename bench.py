@@ -218,6 +218,197 @@ def run_large(args):
     return 0
 
 
+def run_serve(args):
+    """Serving: a Poisson stream of requests (L, W ~ U{4..12}, D ~ U{2,3},
+    h ~ U[0.5, 5], seeded tensors) at 80% of the measured capacity, admitted by
+    exact footprint against a 160 GB budget; p50/p99 latency and throughput,
+    beside sequential FP64 solves of a sample of the same requests."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_1908_08553_gb300 import tn
+
+    torch.cuda.set_device(0)
+    prec = tn.PRECISIONS[args.precision]
+    budget = int(160e9)
+    rng = np.random.default_rng(3)
+    n = args.requests
+    reqs = [(int(rng.integers(4, 13)), int(rng.integers(4, 13)), int(rng.choice([2, 3])),
+             float(rng.uniform(0.5, 5.0)), 10_000 + k) for k in range(n + args.calibrate)]
+    ctx = tn.tn_ctx_create(0, budget)
+    probe = tn.tn_ctx_create(-1)
+    fits = []
+    for (L, W, D, h, seed) in reqs:
+        lat = tn.tn_create_lattice(probe, L, W, D)
+        fits.append(tn.tn_footprint(lat, tn.TN_SCHED_AUTO, prec, tn.TN_WORK_ENERGY) <= budget)
+        tn.tn_destroy_lattice(lat)
+    tn.tn_ctx_destroy(probe)
+    calib = [r for r, f in zip(reqs[n:], fits[n:]) if f]
+    stream_reqs = list(zip(reqs[:n], fits[:n]))
+
+    # capacity: a burst of admissible requests
+    t0 = time.perf_counter()
+    ts = [tn.tn_submit(ctx, L, W, D, prec, 1.0, h, seed=sd) for (L, W, D, h, sd) in calib]
+    for t, (L, W, D, h, sd) in zip(ts, calib):
+        tn.tn_wait(ctx, t, 600.0, L, W)
+    cap = len(calib) / (time.perf_counter() - t0)
+    rate = 0.8 * cap
+
+    # Poisson stream with a polling collector
+    pending, done, lock = {}, {}, threading.Lock()
+    stop = threading.Event()
+
+    deadline = time.perf_counter() + 900.0
+
+    def collector():
+        while (not stop.is_set() or pending) and time.perf_counter() < deadline:
+            with lock:
+                items = list(pending.items())
+            for t, (L, W, ts_) in items:
+                r = tn.tn_poll(ctx, t, L, W)
+                if r is not None:
+                    with lock:
+                        done[t] = (ts_, time.perf_counter(), r[0].energy)
+                        del pending[t]
+            time.sleep(0.0005)
+
+    th = threading.Thread(target=collector)
+    th.start()
+    rejected = 0
+    gaps = rng.exponential(1.0 / rate, size=n)
+    t_start = time.perf_counter()
+    t_next = t_start
+    for ((L, W, D, h, sd), fit), g in zip(stream_reqs, gaps):
+        t_next += g
+        while time.perf_counter() < t_next:
+            time.sleep(0.0002)
+        try:
+            t = tn.tn_submit(ctx, L, W, D, prec, 1.0, h, seed=sd)
+        except tn.TNError as e:
+            if e.status == tn.TN_ERR_OVER_BUDGET:
+                rejected += 1
+                continue
+            raise
+        with lock:
+            pending[t] = (L, W, time.perf_counter())
+    stop.set()
+    th.join()
+    t_end = max(v[1] for v in done.values())
+    lat = np.array([v[1] - v[0] for v in done.values()])
+    served = len(done)
+
+    # sequential plain FP64 solves of a sample of the admitted requests (those
+    # whose FP64 footprint also fits the budget)
+    probe = tn.tn_ctx_create(-1)
+
+    def fits64(L, W, D):
+        lat_ = tn.tn_create_lattice(probe, L, W, D)
+        ok = tn.tn_footprint(lat_, tn.TN_SCHED_AUTO, tn.TN_FP64, tn.TN_WORK_ENERGY) <= budget
+        tn.tn_destroy_lattice(lat_)
+        return ok
+
+    sample = [r for r, f in stream_reqs if f and fits64(*r[:3])][: args.seq_sample]
+    tn.tn_ctx_destroy(probe)
+    t0 = time.perf_counter()
+    n_seq = 0
+    for (L, W, D, h, sd) in sample:
+        l = tn.tn_create_lattice(ctx, L, W, D)
+        tn.tn_fill_random(l, sd)
+        tn.tn_energy(l, 1.0, h, tn.TN_FP64, tn.TN_SCHED_AUTO, L, W)
+        tn.tn_destroy_lattice(l)
+        n_seq += 1
+        if time.perf_counter() - t0 > args.seq_seconds:
+            break
+    seq_rate = n_seq / (time.perf_counter() - t0)
+    tn.tn_ctx_destroy(ctx)
+    line = {"metric": "served p50/p99 latency", "workload": "Poisson stream of TFIM-PEPS energy requests",
+            "unit": "s", "precision": args.precision, "requests": n, "served": served, "rejected_over_budget": rejected,
+            "budget_gb": budget / 1e9, "capacity_jobs_per_s": cap, "offered_rate_jobs_per_s": rate,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_latency_s": float(lat.mean()), "throughput_energies_per_s": served / (t_end - t_start),
+            "sequential_fp64": {"energies_per_s": seq_rate, "sample": n_seq},
+            "distribution": "L, W ~ U{4..12}, D ~ U{2,3}, h ~ U[0.5,5], seeded uniform[-1,1) tensors"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch(args):
+    """512 independent lattices, L, W ~ U{4..10}, D ~ U{2,3}, h ~ U[0.5,5]: as few
+    graph-captured batches as the HBM budget allows (members run together,
+    every wave of all members one grouped launch); members whose footprint
+    alone exceeds the budget are reported, not run."""
+    import numpy as np
+    import torch
+
+    from paper_1908_08553_gb300 import tn
+
+    torch.cuda.set_device(0)
+    prec = tn.PRECISIONS[args.precision]
+    budget = int(200e9)
+    rng = np.random.default_rng(2)
+    n = args.members
+    Ls = rng.integers(4, 11, size=n)
+    Ws = rng.integers(4, 11, size=n)
+    Ds = rng.choice([2, 3], size=n)
+    hs = rng.uniform(0.5, 5.0, size=n)
+    probe = tn.tn_ctx_create(-1)
+    fp = []
+    for L, W, D in zip(Ls, Ws, Ds):
+        lat = tn.tn_create_lattice(probe, int(L), int(W), int(D))
+        fp.append(tn.tn_footprint(lat, tn.TN_SCHED_AUTO, prec, tn.TN_WORK_ENERGY))
+        tn.tn_destroy_lattice(lat)
+    tn.tn_ctx_destroy(probe)
+    ok = [k for k in range(n) if fp[k] <= budget]
+    excluded = [k for k in range(n) if fp[k] > budget]
+    # pack members in order into sub-batches of at most the budget
+    groups, cur, used = [], [], 0
+    for k in ok:
+        if cur and used + fp[k] > budget:
+            groups.append(cur)
+            cur, used = [], 0
+        cur.append(k)
+        used += fp[k]
+    if cur:
+        groups.append(cur)
+    stream = torch.cuda.Stream()
+    ctx = tn.tn_ctx_create(0, int(250e9), stream)
+    total_ms, results, launches = 0.0, {}, 0
+    for g in groups:
+        b = tn.tn_batch_create(ctx, Ls[g], Ws[g], Ds[g], prec)
+        tn.tn_batch_fill_random(b, args.batch_seed)      # member seeds from the batch seed
+        hh = hs[g].copy()
+        tn.tn_batch_run(b, 1.0, hh)                      # capture + first run
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tn.tn_batch_run(b, 1.0, hh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        launches += tn.tn_batch_launch_count(b)
+        r = tn.tn_batch_results_host(b)
+        off = 0
+        for k in g:
+            L, W = int(Ls[k]), int(Ws[k])
+            nres = 6 + L * W + L * (W - 1) + W * (L - 1)
+            results[k] = r[off:off + nres]
+            off += nres
+        tn.tn_batch_destroy(b)
+    tn.tn_ctx_destroy(ctx)
+    m = len(ok)
+    line = {"metric": "batched exact TFIM-PEPS energy evals/s", "workload": "512 mixed lattices (configs[2])",
+            "precision": args.precision, "members": n, "evaluated": m, "excluded_over_budget": len(excluded),
+            "excluded_shapes": sorted({(int(Ls[k]), int(Ws[k]), int(Ds[k])) for k in excluded}),
+            "graphs": len(groups), "kernel_launches": launches, "ms": total_ms,
+            "evals_per_s": m / (total_ms / 1e3), "energies_per_s": m / (total_ms / 1e3),
+            "budget_gb": budget / 1e9,
+            "distribution": "L, W ~ U{4..10}, D ~ U{2,3}, h ~ U[0.5,5], seeded uniform[-1,1) tensors"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -229,13 +420,24 @@ def main():
     ap.add_argument("--ref-lattices", type=int, default=2)
     ap.add_argument("--cpu-lattices", type=int, default=3)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 line and the CPU baseline")
-    ap.add_argument("--workload", default="8x8", choices=["8x8", "large"],
-                    help="8x8: the bench line; large: 12x12 D=2 / 8x8 D=3 measurements")
+    ap.add_argument("--workload", default="8x8", choices=["8x8", "large", "serve", "batch"],
+                    help="8x8: the bench line; large: 12x12 D=2 / 8x8 D=3; serve: Poisson request "
+                         "stream; batch: 512 mixed lattices")
+    ap.add_argument("--members", type=int, default=512, help="batch: lattices")
+    ap.add_argument("--batch-seed", type=int, default=2, help="batch: tensor seed")
+    ap.add_argument("--requests", type=int, default=300, help="serve: requests in the stream")
+    ap.add_argument("--calibrate", type=int, default=60, help="serve: burst size for the capacity")
+    ap.add_argument("--seq-sample", type=int, default=30, help="serve: sequential FP64 sample")
+    ap.add_argument("--seq-seconds", type=float, default=60.0, help="serve: time cap of the FP64 sample")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "large":
         return run_large(args)
+    if args.workload == "serve":
+        return run_serve(args)
+    if args.workload == "batch":
+        return run_batch(args)
 
     import numpy as np
     import torch
