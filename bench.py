@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 L_, W_, D_ = 8, 8, 2
 H_FIELDS = (2.0, 3.04, 4.0)
 METRIC = "exact LxL Ising-PEPS energy evals/s"
-WORKLOAD = "8x8 open-boundary TFIM PEPS, D=2, E at h in {2.0, 3.04, 4.0} (configs[1] shape)"
+WORKLOAD = "8x8 open-boundary TFIM PEPS, D=2, E at h in {2.0, 3.04, 4.0}"
 
 
 def _peak_key(key, default):
@@ -59,10 +59,11 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, path: str | None = None):
+        import tempfile
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), f"tn_clocks_{os.getpid()}_{device}.csv")
 
     def __enter__(self):
         try:
@@ -398,13 +399,56 @@ def run_batch(args):
         tn.tn_batch_destroy(b)
     tn.tn_ctx_destroy(ctx)
     m = len(ok)
-    line = {"metric": "batched exact TFIM-PEPS energy evals/s", "workload": "512 mixed lattices (configs[2])",
+    line = {"metric": "batched exact TFIM-PEPS energy evals/s", "workload": "512 mixed lattices, L, W in 4..10, D in {2,3}",
             "precision": args.precision, "members": n, "evaluated": m, "excluded_over_budget": len(excluded),
             "excluded_shapes": sorted({(int(Ls[k]), int(Ws[k]), int(Ds[k])) for k in excluded}),
             "graphs": len(groups), "kernel_launches": launches, "ms": total_ms,
             "evals_per_s": m / (total_ms / 1e3), "energies_per_s": m / (total_ms / 1e3),
             "budget_gb": budget / 1e9,
             "distribution": "L, W ~ U{4..10}, D ~ U{2,3}, h ~ U[0.5,5], seeded uniform[-1,1) tensors"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_case(args):
+    """One lattice (--L, --W, --D, --seed) contracted --steps times after
+    --warmup runs, in one precision, schedule and work kind: the small,
+    self-contained command that kernel captures run on."""
+    import numpy as np
+    import torch
+
+    from paper_1908_08553_gb300 import inputs, tn
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    ctx = tn.tn_ctx_create(0, 0, stream)
+    sched = {"auto": tn.TN_SCHED_AUTO, "row": tn.TN_SCHED_ROW, "col": tn.TN_SCHED_COL,
+             "quadrant": tn.TN_SCHED_QUADRANT}[args.schedule]
+    work = tn.TN_WORK_ENERGY if args.work == "energy" else tn.TN_WORK_NORM
+    prec = tn.PRECISIONS[args.precision]
+    L, W, D = args.L, args.W, args.D
+    b = tn.tn_batch_create(ctx, [L] * args.batch, [W] * args.batch, [D] * args.batch, prec, sched, work)
+    A = np.concatenate([inputs.random_lattice(L, W, D, inputs.lattice_seed(args.seed, k))
+                        for k in range(args.batch)])
+    tn.tn_batch_set_tensors(b, A)
+    hs = np.full(args.batch, 3.04)
+    for _ in range(args.warmup):
+        tn.tn_batch_run(b, 1.0, hs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        tn.tn_batch_run(b, 1.0, hs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    r = tn.tn_batch_results_host(b)
+    line = {"workload": f"{args.batch} x {L}x{W} D={D}", "precision": args.precision,
+            "schedule": args.schedule, "work": args.work, "ms_per_run": ms,
+            "launches_per_run": tn.tn_batch_launch_count(b),
+            "log2_norm": float(r[1]), "energy_per_site": float(r[0]) / (L * W)}
+    tn.tn_batch_destroy(b)
+    tn.tn_ctx_destroy(ctx)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -420,9 +464,16 @@ def main():
     ap.add_argument("--ref-lattices", type=int, default=2)
     ap.add_argument("--cpu-lattices", type=int, default=3)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 line and the CPU baseline")
-    ap.add_argument("--workload", default="8x8", choices=["8x8", "large", "serve", "batch"],
+    ap.add_argument("--workload", default="8x8", choices=["8x8", "large", "serve", "batch", "case"],
                     help="8x8: the bench line; large: 12x12 D=2 / 8x8 D=3; serve: Poisson request "
-                         "stream; batch: 512 mixed lattices")
+                         "stream; batch: 512 mixed lattices; case: --batch copies of one L x W lattice")
+    ap.add_argument("--L", type=int, default=8, help="case: rows")
+    ap.add_argument("--W", type=int, default=8, help="case: columns")
+    ap.add_argument("--D", type=int, default=2, help="case: bond dimension")
+    ap.add_argument("--seed", type=int, default=7, help="case: tensor seed")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "row", "col", "quadrant"])
+    ap.add_argument("--work", default="energy", choices=["energy", "norm"], help="case: work kind")
+    ap.add_argument("--clock-log", default=None, help="CSV file for the nvidia-smi clock samples")
     ap.add_argument("--members", type=int, default=512, help="batch: lattices")
     ap.add_argument("--batch-seed", type=int, default=2, help="batch: tensor seed")
     ap.add_argument("--requests", type=int, default=300, help="serve: requests in the stream")
@@ -438,6 +489,8 @@ def main():
         return run_serve(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "case":
+        return run_case(args)
 
     import numpy as np
     import torch
@@ -479,7 +532,7 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clock_log) as clk:
         for s in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.fill_(float(s))
@@ -550,7 +603,7 @@ def main():
                     "peak_source": f"MEASURED_PEAKS.json bf16_tflops_sustained (of {src})"}
         achieved = 2 * fd["macs"] / (fd["ms"] / 1e3) / 1e12
         if esize == 8:
-            peak = 152 * 64 * 2 * sm_max * 1e6 / 1e12 / 32    # FP64 ALU estimate, see the design doc
+            peak = 152 * 64 * 2 * sm_max * 1e6 / 1e12 / 32    # FP64: 1/64 of the FP32 lane rate
         else:
             peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # FP32 FMA lanes x 2 flop x max clock
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,

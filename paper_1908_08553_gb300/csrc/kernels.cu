@@ -208,11 +208,11 @@ __device__ __forceinline__ void absorb_tile(const AbsorbTask& t, long long local
 
 template <typename T, int K, int N, int MODE>
 __global__ void __launch_bounds__(kAbsorbThreads)
-k_absorb(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+k_absorb(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     const long long tile = blockIdx.x;
-    const AbsorbTask& t = tasks[find_task(tasks, ntasks, tile)];
+    const AbsorbTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
     absorb_tile<T, K, N, MODE>(t, tile - t.tile0, slots, reinterpret_cast<T*>(smem_raw), red);
 }
 
@@ -237,11 +237,11 @@ constexpr int kV2Threads = 128;
 
 template <int K, int N, int MODE, bool ALONG_P>
 __global__ void __launch_bounds__(kV2Threads, 3)
-k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
     __shared__ __align__(16) float Es[K * N];
     __shared__ double red[32];
     const long long tile = blockIdx.x;
-    const AbsorbTask& t = tasks[find_task(tasks, ntasks, tile)];
+    const AbsorbTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
     const long long local = tile - t.tile0;
     const float* E = static_cast<const float*>(t.E);
     for (int idx = threadIdx.x; idx < K * N; idx += blockDim.x) {
@@ -382,10 +382,11 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
 // global memory, one output leg at a time.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kAbsorbThreads)
-k_absorb_generic(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+k_absorb_generic(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots,
+                 const int* __restrict__ tmap) {
     __shared__ double red[32];
     const long long tile = blockIdx.x;
-    const AbsorbTask& t = tasks[find_task(tasks, ntasks, tile)];
+    const AbsorbTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
     const int K = t.K, N = t.N;
     const T* E = static_cast<const T*>(t.E);
     int e_in = 0, e_adj = 0;
@@ -458,14 +459,14 @@ bool kn_fast(int K, int N) {
 
 template <typename T, int MODE>
 cudaError_t absorb_dispatch(int K, int N, const AbsorbTask* tasks, int ntasks, long long nblocks,
-                            Slot* slots, cudaStream_t st) {
+                            Slot* slots, cudaStream_t st, const int* tmap) {
     const size_t smem = (size_t)K * N * sizeof(T);
 #define TN_ABSORB_CASE(KK, NN)                                                              \
     if (K == KK && N == NN) {                                                               \
         auto fn = k_absorb<T, KK, NN, MODE>;                                                \
         if (smem > 48 * 1024)                                                               \
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        fn<<<(unsigned)nblocks, kAbsorbThreads, smem, st>>>(tasks, ntasks, slots);          \
+        fn<<<(unsigned)nblocks, kAbsorbThreads, smem, st>>>(tasks, ntasks, slots, tmap);    \
         return cudaGetLastError();                                                          \
     }
     TN_ABSORB_CASE(1, 1)
@@ -476,7 +477,7 @@ cudaError_t absorb_dispatch(int K, int N, const AbsorbTask* tasks, int ntasks, l
     TN_ABSORB_CASE(1, 81) TN_ABSORB_CASE(81, 1) TN_ABSORB_CASE(9, 81) TN_ABSORB_CASE(81, 9)
     TN_ABSORB_CASE(81, 81)
 #undef TN_ABSORB_CASE
-    k_absorb_generic<T, MODE><<<(unsigned)nblocks, kAbsorbThreads, 0, st>>>(tasks, ntasks, slots);
+    k_absorb_generic<T, MODE><<<(unsigned)nblocks, kAbsorbThreads, 0, st>>>(tasks, ntasks, slots, tmap);
     return cudaGetLastError();
 }
 
@@ -487,10 +488,10 @@ bool absorb_has_fast_path(int K, int N) { return kn_fast(K, N); }
 namespace {
 template <int MODE, bool ALONG_P>
 cudaError_t absorb4_dispatch(int K, int N, const AbsorbTask* tasks, int ntasks, long long nblocks, Slot* slots,
-                             cudaStream_t st) {
+                             cudaStream_t st, const int* tmap) {
 #define TN_A4_CASE(KK, NN)                                                                        \
     if (K == KK && N == NN) {                                                                     \
-        k_absorb4<KK, NN, MODE, ALONG_P><<<(unsigned)nblocks, kV2Threads, 0, st>>>(tasks, ntasks, slots); \
+        k_absorb4<KK, NN, MODE, ALONG_P><<<(unsigned)nblocks, kV2Threads, 0, st>>>(tasks, ntasks, slots, tmap); \
         return cudaGetLastError();                                                                \
     }
     TN_A4_CASE(1, 1) TN_A4_CASE(1, 4) TN_A4_CASE(4, 1) TN_A4_CASE(4, 4)
@@ -501,19 +502,19 @@ cudaError_t absorb4_dispatch(int K, int N, const AbsorbTask* tasks, int ntasks, 
 }  // namespace
 
 cudaError_t launch_absorb(int dt, bool dot, int K, int N, const AbsorbTask* tasks, int ntasks,
-                          long long nblocks, Slot* slots, cudaStream_t st, int variant) {
+                          long long nblocks, Slot* slots, cudaStream_t st, int variant, const int* tmap) {
     if (nblocks <= 0) return cudaSuccess;
     if (variant == 1)
-        return dot ? absorb4_dispatch<2, false>(K, N, tasks, ntasks, nblocks, slots, st)
-                   : absorb4_dispatch<1, false>(K, N, tasks, ntasks, nblocks, slots, st);
+        return dot ? absorb4_dispatch<2, false>(K, N, tasks, ntasks, nblocks, slots, st, tmap)
+                   : absorb4_dispatch<1, false>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
     if (variant == 2)
-        return dot ? absorb4_dispatch<2, true>(K, N, tasks, ntasks, nblocks, slots, st)
-                   : absorb4_dispatch<1, true>(K, N, tasks, ntasks, nblocks, slots, st);
+        return dot ? absorb4_dispatch<2, true>(K, N, tasks, ntasks, nblocks, slots, st, tmap)
+                   : absorb4_dispatch<1, true>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
     if (dt == 0)
-        return dot ? absorb_dispatch<double, 2>(K, N, tasks, ntasks, nblocks, slots, st)
-                   : absorb_dispatch<double, 1>(K, N, tasks, ntasks, nblocks, slots, st);
-    return dot ? absorb_dispatch<float, 2>(K, N, tasks, ntasks, nblocks, slots, st)
-               : absorb_dispatch<float, 1>(K, N, tasks, ntasks, nblocks, slots, st);
+        return dot ? absorb_dispatch<double, 2>(K, N, tasks, ntasks, nblocks, slots, st, tmap)
+                   : absorb_dispatch<double, 1>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
+    return dot ? absorb_dispatch<float, 2>(K, N, tasks, ntasks, nblocks, slots, st, tmap)
+               : absorb_dispatch<float, 1>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
 }
 
 // ------------------------------------------------------ dense products ---
@@ -627,7 +628,7 @@ k_gemm(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots)
 constexpr int kG2M = 128, kG2N = 128, kG2K = 8;
 
 template <bool DOT, bool VEC4>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_gemm2(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
     __shared__ __align__(16) float As[2][kG2K][kG2M + 4];
     __shared__ __align__(16) float Bs[2][kG2K][kG2N + 4];
@@ -838,10 +839,10 @@ cudaError_t launch_gemm(int dt, bool dot, const GemmTask* tasks, int ntasks, lon
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_dot(const DotTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+k_dot(const DotTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
     __shared__ double red[32];
     const long long tile = blockIdx.x;
-    const DotTask& t = tasks[find_task(tasks, ntasks, tile)];
+    const DotTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
     const long long local = tile - t.tile0;
     const int eA = slot_shift(&slots[t.slot_A]), eB = slot_shift(&slots[t.slot_B]);
     const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
@@ -859,10 +860,10 @@ k_dot(const DotTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
 }
 
 cudaError_t launch_dot(int dt, const DotTask* tasks, int ntasks, long long nblocks, Slot* slots,
-                       cudaStream_t st) {
+                       cudaStream_t st, const int* tmap) {
     if (nblocks <= 0) return cudaSuccess;
-    if (dt == 0) k_dot<double><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
-    else k_dot<float><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+    if (dt == 0) k_dot<double><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots, tmap);
+    else k_dot<float><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots, tmap);
     return cudaGetLastError();
 }
 

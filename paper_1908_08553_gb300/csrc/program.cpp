@@ -288,9 +288,14 @@ int64_t pack_arena(Program& pg) {
 
 std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sched,
                                              tn_precision prec, tn_work work) {
+    return program_build_plan(plan_choose(L, W, D, sched, work), prec, work);
+}
+
+std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision prec, tn_work work) {
     auto pgp = std::make_shared<Program>();
     Program& pg = *pgp;
-    pg.plan = plan_choose(L, W, D, sched, work);
+    pg.plan = plan;
+    const int L = plan.L, W = plan.W, D = plan.D;
     pg.work = work;
     pg.dt = prec == TN_FP64 ? DT_F64 : DT_F32;
     pg.nsplit = prec == TN_BF16X3 ? 2 : (prec == TN_BF16X6 ? 3 : 0);

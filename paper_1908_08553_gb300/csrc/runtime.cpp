@@ -41,6 +41,11 @@ int family_of(int kind) {
 
 // Build every launch and its task table.  With base == nullptr only sizes are
 // computed (footprint); otherwise task structs hold absolute device pointers.
+long long absorb_tiles_any(int var, long long P, long long S, int K, int N) {
+    if (var >= 3) return tc_absorb_tiles(P, S);
+    return absorb_tiles_v(var, P, S, K, N);
+}
+
 void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vector<int>* ints_out,
                  std::vector<ConstOne>* ones_out) {
     Layout& lay = b->lay;
@@ -74,6 +79,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
             if (op.kind == OP_ABSORB || op.kind == OP_ABSORB_DOT) {
                 K = op.K; N = op.N;
                 // 3 / 4: tensor-core absorption with 2 / 3 split planes
+                // 3 / 4: tensor-core absorption with 2 / 3 split planes; else 0..2
                 var = op.nsplit ? 1 + op.nsplit : absorb_variant(b->dt, op.P, op.S, op.K, op.N);
             } else if (op.kind == OP_GEMM || op.kind == OP_GEMM_DOT) {
                 var = gemm_variant(b->dt, op.gm, op.gn, op.gk, op.sam, op.sak, op.sbk, op.sbn);
@@ -111,7 +117,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
             const Op& op = b->m[r.member].pg->ops[r.op];
             if (kind == OP_ABSORB_DOT) {
                 const int var = std::get<4>(kv.first);
-                npart += var >= 3 ? tc_absorb_tiles(op.P, op.S) : absorb_tiles_v(var, op.P, op.S, op.K, op.N);
+                npart += absorb_tiles_any(var, op.P, op.S, op.K, op.N);
             }
             else if (kind == OP_GEMM_DOT) {
                 int tn_;
@@ -158,7 +164,9 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         long long tile = 0;
         align_group();
         size_t first = SIZE_MAX;
+        std::vector<long long> starts;
         for (const OpRef& r : refs) {
+            starts.push_back(tile);
             const Member& mb = b->m[r.member];
             const Program& pg = *mb.pg;
             const Op& op = pg.ops[r.op];
@@ -186,8 +194,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 t.slot_E = slot_of(r.member, op.E);
                 t.slot_out = slot_of(r.member, op.out);
                 t.tile0 = tile;
-                const long long nt = L.variant >= 3 ? tc_absorb_tiles(op.P, op.S)
-                                                    : absorb_tiles_v(L.variant, op.P, op.S, op.K, op.N);
+                const long long nt = absorb_tiles_any(L.variant, op.P, op.S, op.K, op.N);
                 t.ntiles = (int)nt;
                 if (kind == OP_ABSORB_DOT) {
                     t.adj = tensor_ptr(r.member, op.adj);
@@ -287,6 +294,19 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         }
         L.task_off = first;
         L.nblocks = tile;
+        // block -> task table for launches of many short blocks (saves each
+        // block a dependent binary search over the task list)
+        const bool mapped = ((kind == OP_ABSORB || kind == OP_ABSORB_DOT) && L.variant <= 2) || kind == OP_DOT;
+        if (mapped && L.ntasks > 8) {
+            tasks.resize((tasks.size() + 15) / 16 * 16);
+            L.map_off = tasks.size();
+            tasks.resize(tasks.size() + (size_t)tile * sizeof(int));
+            int* mp = reinterpret_cast<int*>(tasks.data() + L.map_off);
+            for (size_t ti = 0; ti < starts.size(); ++ti) {
+                const long long end = ti + 1 < starts.size() ? starts[ti + 1] : tile;
+                for (long long k = starts[ti]; k < end; ++k) mp[k] = (int)ti;
+            }
+        }
         b->launches.push_back(L);
     }
     // const-one tensors
@@ -473,6 +493,7 @@ cudaError_t issue(tn_batch* b, cudaStream_t st, std::vector<std::pair<cudaEvent_
         const Launch& L = b->launches[li];
         if (ev) cudaEventRecord((*ev)[li].first, st);
         const void* tp = tb + L.task_off;
+        const int* tmap = L.map_off ? reinterpret_cast<const int*>(tb + L.map_off) : nullptr;
         switch (L.kind) {
             case OP_SITEMAT:
                 e = launch_sitemat(L.dt, static_cast<const SiteMatTask*>(tp), L.ntasks, slots, st);
@@ -484,7 +505,7 @@ cudaError_t issue(tn_batch* b, cudaStream_t st, std::vector<std::pair<cudaEvent_
                                          L.ntasks, L.nblocks, slots, status, st);
                 else
                     e = launch_absorb(L.dt, L.kind == OP_ABSORB_DOT, L.K, L.N, static_cast<const AbsorbTask*>(tp),
-                                      L.ntasks, L.nblocks, slots, st, L.variant);
+                                      L.ntasks, L.nblocks, slots, st, L.variant, tmap);
                 break;
             case OP_GEMM:
             case OP_GEMM_DOT:
@@ -492,7 +513,7 @@ cudaError_t issue(tn_batch* b, cudaStream_t st, std::vector<std::pair<cudaEvent_
                                 L.nblocks, slots, st, L.variant);
                 break;
             case OP_DOT:
-                e = launch_dot(L.dt, static_cast<const DotTask*>(tp), L.ntasks, L.nblocks, slots, st);
+                e = launch_dot(L.dt, static_cast<const DotTask*>(tp), L.ntasks, L.nblocks, slots, st, tmap);
                 break;
             case OP_TC_SPLIT:
                 e = launch_tc_split(static_cast<const TcSplitTask*>(tp), L.ntasks, L.nblocks, slots, st);

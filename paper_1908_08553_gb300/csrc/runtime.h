@@ -33,6 +33,7 @@ struct Launch {
     int K = 0, N = 0;
     int variant = 0;      // absorption kernel variant (see launch_absorb)
     size_t task_off = 0;  // bytes into the task region
+    size_t map_off = 0;   // bytes into the task region of the block -> task table (0: none)
     int ntasks = 0;
     long long nblocks = 0;
     double bytes = 0, macs = 0;

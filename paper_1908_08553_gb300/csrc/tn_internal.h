@@ -145,6 +145,8 @@ struct Program {
 
 std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sched,
                                              tn_precision prec, tn_work work);
+// the same for a given plan (any orientation and cut)
+std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision prec, tn_work work);
 int64_t program_footprint(const Program& p);   // arena + inputs + slots + results + scratch
 
 }  // namespace tn

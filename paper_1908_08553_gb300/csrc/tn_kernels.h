@@ -135,7 +135,8 @@ struct TcGemmTask {
 // K, N in {1, 4, 16}, four outer positions per thread along s (S % 4 == 0) or
 // along p (S == 1, P % 4 == 0).  All tasks of one launch share (K, N, variant).
 cudaError_t launch_absorb(int dt, bool dot, int K, int N, const AbsorbTask* tasks, int ntasks,
-                          long long nblocks, Slot* slots, cudaStream_t st, int variant = 0);
+                          long long nblocks, Slot* slots, cudaStream_t st, int variant = 0,
+                          const int* tmap = nullptr);
 int absorb_variant(int dt, long long P, long long S, int K, int N);
 long long absorb_tiles_v(int variant, long long P, long long S, int K, int N);
 // variant 0: 64x64 tiles, any dtype; 1: FP32 128x128 double-buffered with
@@ -147,7 +148,7 @@ int gemm_variant(int dt, long long M, long long N, long long K, long long sam, l
 long long gemm_tiles_v(int variant, long long M, long long N, int* tiles_n);
 long long gemm_ksplit(int variant, bool dot, long long K);
 cudaError_t launch_dot(int dt, const DotTask* tasks, int ntasks, long long nblocks, Slot* slots,
-                       cudaStream_t st);
+                       cudaStream_t st, const int* tmap = nullptr);
 cudaError_t launch_sitemat(int dt, const SiteMatTask* tasks, int ntasks, Slot* slots,
                            cudaStream_t st);
 cudaError_t launch_init(Slot* slots, long long nslots, const ConstOne* ones, int nones, int dt,
