@@ -239,6 +239,7 @@ template <int K, int N, int MODE, bool ALONG_P>
 __global__ void __launch_bounds__(kV2Threads, 3)
 k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
     __shared__ __align__(16) float Es[K * N];
+    __shared__ __align__(16) float Es2[MODE == 4 ? K * N : 4];
     __shared__ double red[32];
     const long long tile = blockIdx.x;
     const AbsorbTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
@@ -247,12 +248,13 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
     for (int idx = threadIdx.x; idx < K * N; idx += blockDim.x) {
         const int k = idx / N, n = idx - k * N;
         Es[idx] = t.transE ? E[n * K + k] : E[idx];
+        if (MODE == 4) Es2[idx] = static_cast<const float*>(t.E2)[idx];
     }
     const int e_in = slot_shift(&slots[t.slot_in]);
     const float sc_in = pow2<float>(-e_in);
     int e_adj = 0;
     float sc_adj = 1.0f;
-    if (MODE == 2) {
+    if (MODE >= 2) {
         e_adj = slot_shift(&slots[t.slot_adj]);
         sc_adj = pow2<float>(-e_adj);
     }
@@ -261,7 +263,7 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
     const long long ngroups = ALONG_P ? t.P / 4 : t.P * (S / 4);
     const long long g = local * kV2Threads + threadIdx.x;
     float lmax = 0.0f;
-    double ldot = 0.0;
+    double ldot = 0.0, ldot2 = 0.0;
     if (g < ngroups) {
         long long p, s;
         if (ALONG_P) { p = 4 * g; s = 0; }
@@ -286,6 +288,61 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
                     x[v][4 * kq] = w.x; x[v][4 * kq + 1] = w.y; x[v][4 * kq + 2] = w.z; x[v][4 * kq + 3] = w.w;
                 }
         }
+        if (MODE == 4) {
+            // dual dot: per group of 4 outputs n, both site matrices, then the
+            // adjoint (keeps two accumulator sets of 16 instead of 2 N x 4)
+            const float* adj = static_cast<const float*>(t.adj);
+            CSum<float> acc1, acc2;
+#pragma unroll
+            for (int nq = 0; nq < (N + 3) / 4; ++nq) {
+                constexpr int NW = N >= 4 ? 4 : 1;
+                float z1[4][NW], z2[4][NW];
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+#pragma unroll
+                    for (int j = 0; j < NW; ++j) { z1[v][j] = 0.0f; z2[v][j] = 0.0f; }
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    float e1[NW], e2[NW];
+                    if (NW == 4) {
+                        const float4 a1 = *reinterpret_cast<const float4*>(&Es[k * N + 4 * nq]);
+                        const float4 a2 = *reinterpret_cast<const float4*>(&Es2[k * N + 4 * nq]);
+                        e1[0] = a1.x; e1[1] = a1.y; e1[2] = a1.z; e1[3] = a1.w;
+                        e2[0] = a2.x; e2[1] = a2.y; e2[2] = a2.z; e2[3] = a2.w;
+                    } else {
+                        e1[0] = Es[k]; e2[0] = Es2[k];
+                    }
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const float xv = x[v][k] * sc_in;
+#pragma unroll
+                        for (int j = 0; j < NW; ++j) {
+                            z1[v][j] = fmaf(xv, e1[j], z1[v][j]);
+                            z2[v][j] = fmaf(xv, e2[j], z2[v][j]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < NW; ++j) {
+                    const int n = NW * nq + j;
+                    float a[4];
+                    if (!ALONG_P) {
+                        const float4 w = __ldg(reinterpret_cast<const float4*>(adj + (p * N + n) * S + s));
+                        a[0] = w.x; a[1] = w.y; a[2] = w.z; a[3] = w.w;
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) a[v] = __ldg(adj + (p + v) * N + n);
+                    }
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        acc1.add(z1[v][j] * (a[v] * sc_adj));
+                        acc2.add(z2[v][j] * (a[v] * sc_adj));
+                    }
+                }
+            }
+            ldot = (double)acc1.value();
+            ldot2 = (double)acc2.value();
+        } else {
         float y[4][N];
 #pragma unroll
         for (int v = 0; v < 4; ++v)
@@ -364,6 +421,7 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
             }
             ldot = (double)acc.value();
         }
+        }
     }
     if (MODE == 1) {
         const double m = block_max((double)lmax, red);
@@ -375,6 +433,11 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
         const double part = block_sum(ldot, red);
         const long long X = slots[t.slot_in].X + e_in + slots[t.slot_E].X + slots[t.slot_adj].X + e_adj;
         finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_out], X, red);
+        if (MODE == 4) {
+            const double part2 = block_sum(ldot2, red);
+            const long long X2 = slots[t.slot_in].X + e_in + slots[t.slot_E2].X + slots[t.slot_adj].X + e_adj;
+            finish_sum(part2, t.partial + t.ntiles, t.ntiles, local, &slots[t.slot_out2], X2, red);
+        }
     }
 }
 
@@ -510,6 +573,9 @@ cudaError_t launch_absorb(int dt, bool dot, int K, int N, const AbsorbTask* task
     if (variant == 2)
         return dot ? absorb4_dispatch<2, true>(K, N, tasks, ntasks, nblocks, slots, st, tmap)
                    : absorb4_dispatch<1, true>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
+    // 11 / 12: the dual dot of variants 1 / 2
+    if (variant == 11) return absorb4_dispatch<4, false>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
+    if (variant == 12) return absorb4_dispatch<4, true>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
     if (dt == 0)
         return dot ? absorb_dispatch<double, 2>(K, N, tasks, ntasks, nblocks, slots, st, tmap)
                    : absorb_dispatch<double, 1>(K, N, tasks, ntasks, nblocks, slots, st, tmap);

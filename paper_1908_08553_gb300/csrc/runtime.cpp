@@ -42,6 +42,7 @@ int family_of(int kind) {
 // Build every launch and its task table.  With base == nullptr only sizes are
 // computed (footprint); otherwise task structs hold absolute device pointers.
 long long absorb_tiles_any(int var, long long P, long long S, int K, int N) {
+    if (var >= 10) return absorb_tiles_v(var - 10, P, S, K, N);   // dual dot of variants 1 / 2
     if (var >= 3) return tc_absorb_tiles(P, S);
     return absorb_tiles_v(var, P, S, K, N);
 }
@@ -79,8 +80,9 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
             if (op.kind == OP_ABSORB || op.kind == OP_ABSORB_DOT) {
                 K = op.K; N = op.N;
                 // 3 / 4: tensor-core absorption with 2 / 3 split planes
-                // 3 / 4: tensor-core absorption with 2 / 3 split planes; else 0..2
+                // 3 / 4: tensor-core absorption with 2 / 3 split planes; 11 / 12: dual dot; else 0..2
                 var = op.nsplit ? 1 + op.nsplit : absorb_variant(b->dt, op.P, op.S, op.K, op.N);
+                if (op.E2 >= 0) var += 10;
             } else if (op.kind == OP_GEMM || op.kind == OP_GEMM_DOT) {
                 var = gemm_variant(b->dt, op.gm, op.gn, op.gk, op.sam, op.sak, op.sbk, op.sbn);
             } else if (op.kind == OP_TC_GEMM || op.kind == OP_TC_GEMM_DOT) {
@@ -117,7 +119,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
             const Op& op = b->m[r.member].pg->ops[r.op];
             if (kind == OP_ABSORB_DOT) {
                 const int var = std::get<4>(kv.first);
-                npart += absorb_tiles_any(var, op.P, op.S, op.K, op.N);
+                npart += (op.E2 >= 0 ? 2 : 1) * absorb_tiles_any(var, op.P, op.S, op.K, op.N);
             }
             else if (kind == OP_GEMM_DOT) {
                 int tn_;
@@ -199,7 +201,12 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 if (kind == OP_ABSORB_DOT) {
                     t.adj = tensor_ptr(r.member, op.adj);
                     t.slot_adj = slot_of(r.member, op.adj);
-                    t.partial = take_partial(nt);
+                    t.partial = take_partial(op.E2 >= 0 ? 2 * nt : nt);
+                    if (op.E2 >= 0) {
+                        t.E2 = tensor_ptr(r.member, op.E2);
+                        t.slot_E2 = slot_of(r.member, op.E2);
+                        t.slot_out2 = slot_of(r.member, op.out2);
+                    }
                 } else {
                     t.out = tensor_ptr(r.member, op.out);
                 }
@@ -296,7 +303,8 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         L.nblocks = tile;
         // block -> task table for launches of many short blocks (saves each
         // block a dependent binary search over the task list)
-        const bool mapped = ((kind == OP_ABSORB || kind == OP_ABSORB_DOT) && L.variant <= 2) || kind == OP_DOT;
+        const bool mapped =
+            ((kind == OP_ABSORB || kind == OP_ABSORB_DOT) && (L.variant <= 2 || L.variant >= 10)) || kind == OP_DOT;
         if (mapped && L.ntasks > 8) {
             tasks.resize((tasks.size() + 15) / 16 * 16);
             L.map_off = tasks.size();
@@ -500,7 +508,7 @@ cudaError_t issue(tn_batch* b, cudaStream_t st, std::vector<std::pair<cudaEvent_
                 break;
             case OP_ABSORB:
             case OP_ABSORB_DOT:
-                if (L.variant >= 3)
+                if (L.variant >= 3 && L.variant < 10)
                     e = launch_tc_absorb(L.variant - 1, L.kind == OP_ABSORB_DOT, static_cast<const AbsorbTask*>(tp),
                                          L.ntasks, L.nblocks, slots, status, st);
                 else

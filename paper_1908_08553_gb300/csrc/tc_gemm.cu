@@ -575,6 +575,7 @@ long long tc_absorb_tiles(long long P, long long S) { return (P * S + 128 * kAbs
 cudaError_t launch_tc_absorb(int nsplit, bool dot, const AbsorbTask* tasks, int ntasks, long long nblocks,
                              Slot* slots, int* status, cudaStream_t st) {
     if (nblocks <= 0) return cudaSuccess;
+    if (nsplit != 2 && nsplit != 3) return cudaErrorInvalidValue;
     const size_t smem = (size_t)nsplit * (kAbsAPlane + kAbsBPlane) + 1024;
 #define TN_TCA_LAUNCH(NS, MD)                                                                  \
     {                                                                                          \

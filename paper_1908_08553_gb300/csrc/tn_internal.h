@@ -100,6 +100,7 @@ struct Op {
     int level = 0;
     // absorb
     int in = -1, E = -1, out = -1, adj = -1;
+    int E2 = -1, out2 = -1;       // dual absorb-dot: second site matrix and its scalar
     int64_t P = 0, S = 0;
     int K = 0, N = 0;
     bool transE = false;

@@ -39,6 +39,10 @@ struct AbsorbTask {
     int transE;           // 1: use E[n][k] as E[k][n] (backward / environment sweep)
     int slot_in, slot_E, slot_out, slot_adj;
     int ntiles;
+    // dual dot mode: a second site matrix on the same input and adjoint, its
+    // result in slot_out2 (partials ntiles..2 ntiles-1)
+    const void* E2;
+    int slot_E2, slot_out2;
 };
 
 struct GemmTask {
