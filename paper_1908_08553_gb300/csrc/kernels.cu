@@ -854,6 +854,122 @@ k_gemm2(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots
     }
 }
 
+// Full tiles (M and N multiples of 128, the k range a multiple of 8, operands
+// with a unit-stride axis and 16-byte aligned rows): the same 128 x 128 scheme
+// with the operand layouts as template parameters, one pointer increment per
+// k slice instead of per-load index arithmetic, and no bounds tests.
+// AK: A contiguous along k (else along m); BNC: B contiguous along n (else k).
+template <bool DOT, bool AK, bool BNC>
+__global__ void __launch_bounds__(256, 2)
+k_gemm3(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+    __shared__ __align__(16) float As[2][kG2K][kG2M + 4];
+    __shared__ __align__(16) float Bs[2][kG2K][kG2N + 4];
+    __shared__ double red[32];
+    const long long tile = blockIdx.x;
+    const GemmTask& t = tasks[find_task(tasks, ntasks, tile)];
+    const long long local = tile - t.tile0;
+    const long long mn = local / t.ksplit, ks = local % t.ksplit;
+    const long long m0 = (mn / t.tiles_n) * kG2M, n0 = (mn % t.tiles_n) * kG2N;
+    const long long kbeg = ks * t.kslice, kend = min(t.K, kbeg + t.kslice);
+    const int eA = slot_shift(&slots[t.slot_A]), eB = slot_shift(&slots[t.slot_B]);
+    const float sA = pow2<float>(-eA), sB = pow2<float>(-eB);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    int a_mm, a_kk, b_nn, b_kk;
+    if (AK) { a_mm = tid >> 1; a_kk = (tid & 1) * 4; } else { a_kk = tid >> 5; a_mm = (tid & 31) * 4; }
+    if (BNC) { b_kk = tid >> 5; b_nn = (tid & 31) * 4; } else { b_nn = tid >> 1; b_kk = (tid & 1) * 4; }
+    const float* pa = static_cast<const float*>(t.A) +
+                      (AK ? (m0 + a_mm) * t.sam + kbeg + a_kk : (kbeg + a_kk) * t.sak + m0 + a_mm);
+    const float* pb = static_cast<const float*>(t.B) +
+                      (BNC ? (kbeg + b_kk) * t.sbk + n0 + b_nn : (n0 + b_nn) * t.sbn + kbeg + b_kk);
+    const long long da = AK ? kG2K : kG2K * t.sak;
+    const long long db = BNC ? kG2K * t.sbk : kG2K;
+    float4 ra = __ldg(reinterpret_cast<const float4*>(pa));
+    float4 rb = __ldg(reinterpret_cast<const float4*>(pb));
+    auto store = [&](int buf) {
+        if (AK) {
+            As[buf][a_kk][a_mm] = ra.x * sA; As[buf][a_kk + 1][a_mm] = ra.y * sA;
+            As[buf][a_kk + 2][a_mm] = ra.z * sA; As[buf][a_kk + 3][a_mm] = ra.w * sA;
+        } else {
+            *reinterpret_cast<float4*>(&As[buf][a_kk][a_mm]) = make_float4(ra.x * sA, ra.y * sA, ra.z * sA, ra.w * sA);
+        }
+        if (BNC) {
+            *reinterpret_cast<float4*>(&Bs[buf][b_kk][b_nn]) = make_float4(rb.x * sB, rb.y * sB, rb.z * sB, rb.w * sB);
+        } else {
+            Bs[buf][b_kk][b_nn] = rb.x * sB; Bs[buf][b_kk + 1][b_nn] = rb.y * sB;
+            Bs[buf][b_kk + 2][b_nn] = rb.z * sB; Bs[buf][b_kk + 3][b_nn] = rb.w * sB;
+        }
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    const int nk = (int)((kend - kbeg) / kG2K);
+    store(0);
+    __syncthreads();
+    for (int kt = 0; kt < nk; ++kt) {
+        const int cur = kt & 1;
+        const bool more = kt + 1 < nk;
+        if (more) {
+            pa += da;
+            pb += db;
+            ra = __ldg(reinterpret_cast<const float4*>(pa));
+            rb = __ldg(reinterpret_cast<const float4*>(pb));
+        }
+#pragma unroll
+        for (int kk = 0; kk < kG2K; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][4 * ty]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + 4 * ty]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][4 * tx]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + 4 * tx]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (more) store(cur ^ 1);
+        __syncthreads();
+    }
+    auto row = [&](int i) { return m0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + (i - 4)); };
+    const long long c0 = n0 + 4 * tx, c1 = n0 + 64 + 4 * tx;
+    if (!DOT) {
+        float* C = static_cast<float*>(t.C);
+        float m = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float* cr = C + row(i) * t.N;
+            *reinterpret_cast<float4*>(cr + c0) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            *reinterpret_cast<float4*>(cr + c1) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) m = fmaxf(m, fabsf(acc[i][j]));
+        }
+        const double mm = block_max((double)m, red);
+        if (threadIdx.x == 0) {
+            record_max(&slots[t.slot_C], mm);
+            if (local == 0) slots[t.slot_C].X = slots[t.slot_A].X + eA + slots[t.slot_B].X + eB;
+        }
+    } else {
+        const int eD = slot_shift(&slots[t.slot_D]);
+        const float sD = pow2<float>(-eD);
+        const float* Dm = static_cast<const float*>(t.Dm);
+        CSum<float> sum;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float* dr = Dm + row(i) * t.N;
+            const float4 d0 = __ldg(reinterpret_cast<const float4*>(dr + c0));
+            const float4 d1 = __ldg(reinterpret_cast<const float4*>(dr + c1));
+            const float d[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) sum.add(acc[i][j] * (d[j] * sD));
+        }
+        const double part = block_sum((double)sum.value(), red);
+        const long long X = slots[t.slot_A].X + eA + slots[t.slot_B].X + eB + slots[t.slot_D].X + eD;
+        finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_C], X, red);
+    }
+}
+
 long long gemm_tiles_v(int variant, long long M, long long N, int* tiles_n) {
     const int bm = variant == 0 ? kGemmTile : kG2M, bn = variant == 0 ? kGemmTile : kG2N;
     const long long tm = (M + bm - 1) / bm, tn_ = (N + bn - 1) / bn;
@@ -866,7 +982,8 @@ long long gemm_ksplit(int variant, bool dot, long long K) {
     return (K + kGemmKSlice - 1) / kGemmKSlice;
 }
 
-// 0: v1 (64x64, any dtype); 1: v2 FP32 with 16-byte loads; 2: v2 FP32 scalar loads.
+// 0: v1 (64x64, any dtype); 1: v2 FP32 with 16-byte loads; 2: v2 FP32 scalar loads;
+// 3..6: full-tile FP32 (3 + 2 [A k-contiguous] + [B n-contiguous]).
 int gemm_variant(int dt, long long M, long long N, long long K, long long sam, long long sak, long long sbk,
                  long long sbn) {
     if (dt != 1) return 0;
@@ -875,7 +992,10 @@ int gemm_variant(int dt, long long M, long long N, long long K, long long sam, l
     // per-thread offsets are multiples of 4), and C rows are 16-byte aligned.
     const bool a_ok = sak == 1 ? (sam % 4 == 0 && K % 4 == 0) : (sam == 1 && sak % 4 == 0 && M % 4 == 0);
     const bool b_ok = sbn == 1 ? (sbk % 4 == 0 && N % 4 == 0) : (sbk == 1 && sbn % 4 == 0 && K % 4 == 0);
-    return (a_ok && b_ok && N % 4 == 0) ? 1 : 2;
+    if (!(a_ok && b_ok && N % 4 == 0)) return 2;
+    // 3..6: full tiles (k slices of 512 keep the k range a multiple of 8)
+    if (M % kG2M == 0 && N % kG2N == 0 && K % kG2K == 0) return 3 + 2 * (sak == 1) + (sbn == 1);
+    return 1;
 }
 
 cudaError_t launch_gemm(int dt, bool dot, const GemmTask* tasks, int ntasks, long long nblocks,
@@ -889,6 +1009,15 @@ cudaError_t launch_gemm(int dt, bool dot, const GemmTask* tasks, int ntasks, lon
     if (variant == 2) {
         if (dot) k_gemm2<true, false><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
         else k_gemm2<false, false><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+        return cudaGetLastError();
+    }
+    if (variant >= 3 && variant <= 6) {
+        const bool ak = variant >= 5, bn = (variant - 3) % 2 == 1;
+#define TN_G3(D_, A_, B_) \
+        if (dot == D_ && ak == A_ && bn == B_) k_gemm3<D_, A_, B_><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+        TN_G3(true, true, true) TN_G3(true, true, false) TN_G3(true, false, true) TN_G3(true, false, false)
+        TN_G3(false, true, true) TN_G3(false, true, false) TN_G3(false, false, true) TN_G3(false, false, false)
+#undef TN_G3
         return cudaGetLastError();
     }
     if (dt == 0) {

@@ -86,7 +86,8 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
             } else if (op.kind == OP_GEMM || op.kind == OP_GEMM_DOT) {
                 var = gemm_variant(b->dt, op.gm, op.gn, op.gk, op.sam, op.sak, op.sbk, op.sbn);
             } else if (op.kind == OP_TC_GEMM || op.kind == OP_TC_GEMM_DOT) {
-                var = op.nsplit * 1000 + tc_gemm_bn(op.nsplit, op.gn);   // planes and tile width
+                // short k range (+10000), planes, tile width
+                var = (op.Kp <= kTcShortK ? 10000 : 0) + op.nsplit * 1000 + tc_gemm_bn(op.nsplit, op.gn, op.Kp);
             }
             groups[std::make_tuple(op.level, (int)op.kind, K, N, var)].push_back({mi, oi});
         }
@@ -528,8 +529,9 @@ cudaError_t issue(tn_batch* b, cudaStream_t st, std::vector<std::pair<cudaEvent_
                 break;
             case OP_TC_GEMM:
             case OP_TC_GEMM_DOT:
-                e = launch_tc_gemm(L.variant / 1000, L.kind == OP_TC_GEMM_DOT, L.variant % 1000,
-                                   static_cast<const TcGemmTask*>(tp), L.ntasks, L.nblocks, slots, status, st);
+                e = launch_tc_gemm((L.variant % 10000) / 1000, L.kind == OP_TC_GEMM_DOT, L.variant % 1000,
+                                   static_cast<const TcGemmTask*>(tp), L.ntasks, L.nblocks, slots, status, st,
+                                   L.variant >= 10000);
                 break;
         }
         if (ev) cudaEventRecord((*ev)[li].second, st);

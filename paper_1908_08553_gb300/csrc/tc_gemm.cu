@@ -190,12 +190,15 @@ k_tc_split(const TcSplitTask* __restrict__ tasks, int ntasks, const Slot* __rest
 
 // ------------------------------------------------------------------ mma ---
 
-template <int NSPLIT, bool DOT, int BN>
+// STAGES: ring depth (0: as many 192 KB allow, up to 6; short k ranges use a
+// shallow ring so two CTAs share an SM and overlap each other's epilogues).
+template <int NSPLIT, bool DOT, int BN, int STAGES_>
 __global__ void __launch_bounds__(128, 1)
 k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, int* __restrict__ status) {
     constexpr int NB = BN / kTcM;                                   // 128-row B blocks per tile
     constexpr uint32_t kStageBytes = NSPLIT * (1 + NB) * kBlockBytes;   // A planes then B planes
-    constexpr int STAGES = (196608u / kStageBytes) >= 6 ? 6 : (int)(196608u / kStageBytes);
+    constexpr int STAGES =
+        STAGES_ > 0 ? STAGES_ : ((196608u / kStageBytes) >= 6 ? 6 : (int)(196608u / kStageBytes));
     constexpr int NPROD = NSPLIT == 2 ? 3 : 6;
     // products (plane of A, plane of B), smallest terms first
     constexpr int PA[6] = {NSPLIT == 2 ? 1 : 2, NSPLIT == 2 ? 0 : 1, NSPLIT == 2 ? 0 : 0, 1, 0, 0};
@@ -601,18 +604,36 @@ cudaError_t launch_tc_split(const TcSplitTask* tasks, int ntasks, long long nblo
     return cudaGetLastError();
 }
 
-int tc_gemm_bn(int nsplit, long long N) { return (nsplit == 2 && N > 128) ? 256 : 128; }
+int tc_gemm_bn(int nsplit, long long N, long long Kp) {
+    if (Kp <= kTcShortK) return 128;
+    return (nsplit == 2 && N > 128) ? 256 : 128;
+}
 
 cudaError_t launch_tc_gemm(int nsplit, bool dot, int bn, const TcGemmTask* tasks, int ntasks, long long nblocks,
-                           Slot* slots, int* status, cudaStream_t st) {
+                           Slot* slots, int* status, cudaStream_t st, bool short_k) {
     if (nblocks <= 0) return cudaSuccess;
     const int nb = bn / kTcM;
     const uint32_t stage = (uint32_t)nsplit * (1 + nb) * kBlockBytes;
-    const int stages = (196608u / stage) >= 6 ? 6 : (int)(196608u / stage);
+    const int stages = short_k ? (nsplit == 2 ? 3 : 2) : ((196608u / stage) >= 6 ? 6 : (int)(196608u / stage));
     const size_t smem = (size_t)stages * stage + 1024;
+    if (short_k) {
+        // 128-wide tiles, 2 (3 planes) or 3 (2 planes) stages: ~97 KB, two CTAs per SM
+#define TN_TCS_LAUNCH(NS, DT, SG)                                                              \
+        {                                                                                      \
+            auto fn = k_tc_gemm<NS, DT, 128, SG>;                                              \
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            if (e != cudaSuccess) return e;                                                    \
+            fn<<<(unsigned)nblocks, 128, smem, st>>>(tasks, ntasks, slots, status);            \
+            return cudaGetLastError();                                                         \
+        }
+        if (bn != 128) return cudaErrorInvalidValue;
+        if (nsplit == 2) { if (dot) TN_TCS_LAUNCH(2, true, 3) else TN_TCS_LAUNCH(2, false, 3) }
+        if (dot) TN_TCS_LAUNCH(3, true, 2) else TN_TCS_LAUNCH(3, false, 2)
+#undef TN_TCS_LAUNCH
+    }
 #define TN_TC_LAUNCH(NS, DT, B)                                                                \
     {                                                                                          \
-        auto fn = k_tc_gemm<NS, DT, B>;                                                        \
+        auto fn = k_tc_gemm<NS, DT, B, 0>;                                                     \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                        \
         fn<<<(unsigned)nblocks, 128, smem, st>>>(tasks, ntasks, slots, status);                \

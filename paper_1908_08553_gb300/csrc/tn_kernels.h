@@ -166,10 +166,13 @@ long long tc_split_tiles(long long Rp, long long Kp);
 cudaError_t launch_tc_split(const TcSplitTask* tasks, int ntasks, long long nblocks, const Slot* slots,
                             cudaStream_t st);
 // status: set to 1 if a bounded wait inside the kernel timed out.
-// Output tile 128 x bn, bn = tc_gemm_bn(nsplit, N) (256 for 2 planes and N > 128).
-int tc_gemm_bn(int nsplit, long long N);
+// Output tile 128 x bn, bn = tc_gemm_bn(nsplit, N, Kp): 256 for 2 planes and
+// N > 128, except short k ranges (Kp <= kTcShortK), which take 128-wide tiles
+// and a shallow stage ring (launch with short_k) so two CTAs share an SM.
+constexpr long long kTcShortK = 1024;
+int tc_gemm_bn(int nsplit, long long N, long long Kp);
 cudaError_t launch_tc_gemm(int nsplit, bool dot, int bn, const TcGemmTask* tasks, int ntasks, long long nblocks,
-                           Slot* slots, int* status, cudaStream_t st);
+                           Slot* slots, int* status, cudaStream_t st, bool short_k = false);
 // Rows of every split operand are padded to a multiple of this.
 constexpr long long kTcRowPad = 256;
 // Reduction (k) width of one staged block of a split operand.
