@@ -236,7 +236,7 @@ k_absorb_one(const __grid_constant__ AbsorbTask t) {
 constexpr int kV2Threads = 128;
 
 template <int K, int N, int MODE, bool ALONG_P>
-__global__ void __launch_bounds__(kV2Threads, 3)
+__global__ void __launch_bounds__(kV2Threads, MODE == 4 ? 3 : 4)
 k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
     __shared__ __align__(16) float Es[K * N];
     __shared__ __align__(16) float Es2[MODE == 4 ? K * N : 4];
@@ -288,6 +288,10 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
                     x[v][4 * kq] = w.x; x[v][4 * kq + 1] = w.y; x[v][4 * kq + 2] = w.z; x[v][4 * kq + 3] = w.w;
                 }
         }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) x[v][k] *= sc_in;      // inputs scaled once
         if (MODE == 4) {
             // dual dot: per group of 4 outputs n, both site matrices, then the
             // adjoint (keeps two accumulator sets of 16 instead of 2 N x 4)
@@ -314,7 +318,7 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
                     }
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
-                        const float xv = x[v][k] * sc_in;
+                        const float xv = x[v][k];
 #pragma unroll
                         for (int j = 0; j < NW; ++j) {
                             z1[v][j] = fmaf(xv, e1[j], z1[v][j]);
@@ -343,84 +347,90 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
             ldot = (double)acc1.value();
             ldot2 = (double)acc2.value();
         } else {
-        float y[4][N];
+        // outputs formed NC columns at a time (8 of 16 when along s) so a
+        // thread holds 4 x NC accumulators, not 4 x N
+        constexpr int NC = (N >= 8 && !ALONG_P) ? 8 : N;
+        CSum<float> acc;
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
-#pragma unroll
-            for (int n = 0; n < N; ++n) y[v][n] = 0.0f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            if (N >= 4) {
-#pragma unroll
-                for (int nq = 0; nq < N / 4; ++nq) {
-                    const float4 e = *reinterpret_cast<const float4*>(&Es[k * N + 4 * nq]);
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const float xv = x[v][k] * sc_in;
-                        y[v][4 * nq] = fmaf(xv, e.x, y[v][4 * nq]);
-                        y[v][4 * nq + 1] = fmaf(xv, e.y, y[v][4 * nq + 1]);
-                        y[v][4 * nq + 2] = fmaf(xv, e.z, y[v][4 * nq + 2]);
-                        y[v][4 * nq + 3] = fmaf(xv, e.w, y[v][4 * nq + 3]);
-                    }
-                }
-            } else {
-                const float e = Es[k];
-#pragma unroll
-                for (int v = 0; v < 4; ++v) y[v][0] = fmaf(x[v][k] * sc_in, e, y[v][0]);
-            }
-        }
-        if (MODE == 1) {
-            float* out = static_cast<float*>(t.out);
-            if (!ALONG_P) {
-#pragma unroll
-                for (int n = 0; n < N; ++n)
-                    *reinterpret_cast<float4*>(out + (p * N + n) * S + s) = make_float4(y[0][n], y[1][n], y[2][n], y[3][n]);
-            } else if (N == 1) {
-                *reinterpret_cast<float4*>(out + p) = make_float4(y[0][0], y[1][0], y[2][0], y[3][0]);
-            } else {
-#pragma unroll
-                for (int v = 0; v < 4; ++v)
-#pragma unroll
-                    for (int nq = 0; nq < N / 4; ++nq)
-                        *reinterpret_cast<float4*>(out + (p + v) * N + 4 * nq) =
-                            make_float4(y[v][4 * nq], y[v][4 * nq + 1], y[v][4 * nq + 2], y[v][4 * nq + 3]);
-            }
+        for (int h = 0; h < N / NC; ++h) {
+            float y[4][NC];
 #pragma unroll
             for (int v = 0; v < 4; ++v)
 #pragma unroll
-                for (int n = 0; n < N; ++n) lmax = fmaxf(lmax, fabsf(y[v][n]));
-        } else {
-            const float* adj = static_cast<const float*>(t.adj);
-            CSum<float> acc;
-            if (!ALONG_P) {
+                for (int j = 0; j < NC; ++j) y[v][j] = 0.0f;
 #pragma unroll
-                for (int n = 0; n < N; ++n) {
-                    const float4 a = __ldg(reinterpret_cast<const float4*>(adj + (p * N + n) * S + s));
-                    acc.add(y[0][n] * (a.x * sc_adj));
-                    acc.add(y[1][n] * (a.y * sc_adj));
-                    acc.add(y[2][n] * (a.z * sc_adj));
-                    acc.add(y[3][n] * (a.w * sc_adj));
+            for (int k = 0; k < K; ++k) {
+                if (NC >= 4) {
+#pragma unroll
+                    for (int nq = 0; nq < NC / 4; ++nq) {
+                        const float4 e = *reinterpret_cast<const float4*>(&Es[k * N + h * NC + 4 * nq]);
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            y[v][4 * nq] = fmaf(x[v][k], e.x, y[v][4 * nq]);
+                            y[v][4 * nq + 1] = fmaf(x[v][k], e.y, y[v][4 * nq + 1]);
+                            y[v][4 * nq + 2] = fmaf(x[v][k], e.z, y[v][4 * nq + 2]);
+                            y[v][4 * nq + 3] = fmaf(x[v][k], e.w, y[v][4 * nq + 3]);
+                        }
+                    }
+                } else {
+                    const float e = Es[k];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) y[v][0] = fmaf(x[v][k], e, y[v][0]);
                 }
-            } else if (N == 1) {
-                const float4 a = __ldg(reinterpret_cast<const float4*>(adj + p));
-                acc.add(y[0][0] * (a.x * sc_adj));
-                acc.add(y[1][0] * (a.y * sc_adj));
-                acc.add(y[2][0] * (a.z * sc_adj));
-                acc.add(y[3][0] * (a.w * sc_adj));
-            } else {
+            }
+            if (MODE == 1) {
+                float* out = static_cast<float*>(t.out);
+                if (!ALONG_P) {
+#pragma unroll
+                    for (int j = 0; j < NC; ++j)
+                        *reinterpret_cast<float4*>(out + (p * N + h * NC + j) * S + s) =
+                            make_float4(y[0][j], y[1][j], y[2][j], y[3][j]);
+                } else if (N == 1) {
+                    *reinterpret_cast<float4*>(out + p) = make_float4(y[0][0], y[1][0], y[2][0], y[3][0]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+#pragma unroll
+                        for (int nq = 0; nq < N / 4; ++nq)
+                            *reinterpret_cast<float4*>(out + (p + v) * N + 4 * nq) =
+                                make_float4(y[v][4 * nq], y[v][4 * nq + 1], y[v][4 * nq + 2], y[v][4 * nq + 3]);
+                }
 #pragma unroll
                 for (int v = 0; v < 4; ++v)
 #pragma unroll
-                    for (int nq = 0; nq < N / 4; ++nq) {
-                        const float4 a = __ldg(reinterpret_cast<const float4*>(adj + (p + v) * N + 4 * nq));
-                        acc.add(y[v][4 * nq] * (a.x * sc_adj));
-                        acc.add(y[v][4 * nq + 1] * (a.y * sc_adj));
-                        acc.add(y[v][4 * nq + 2] * (a.z * sc_adj));
-                        acc.add(y[v][4 * nq + 3] * (a.w * sc_adj));
+                    for (int j = 0; j < NC; ++j) lmax = fmaxf(lmax, fabsf(y[v][j]));
+            } else {
+                const float* adj = static_cast<const float*>(t.adj);
+                if (!ALONG_P) {
+#pragma unroll
+                    for (int j = 0; j < NC; ++j) {
+                        const float4 a = __ldg(reinterpret_cast<const float4*>(adj + (p * N + h * NC + j) * S + s));
+                        acc.add(y[0][j] * (a.x * sc_adj));
+                        acc.add(y[1][j] * (a.y * sc_adj));
+                        acc.add(y[2][j] * (a.z * sc_adj));
+                        acc.add(y[3][j] * (a.w * sc_adj));
                     }
+                } else if (N == 1) {
+                    const float4 a = __ldg(reinterpret_cast<const float4*>(adj + p));
+                    acc.add(y[0][0] * (a.x * sc_adj));
+                    acc.add(y[1][0] * (a.y * sc_adj));
+                    acc.add(y[2][0] * (a.z * sc_adj));
+                    acc.add(y[3][0] * (a.w * sc_adj));
+                } else {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+#pragma unroll
+                        for (int nq = 0; nq < N / 4; ++nq) {
+                            const float4 a = __ldg(reinterpret_cast<const float4*>(adj + (p + v) * N + 4 * nq));
+                            acc.add(y[v][4 * nq] * (a.x * sc_adj));
+                            acc.add(y[v][4 * nq + 1] * (a.y * sc_adj));
+                            acc.add(y[v][4 * nq + 2] * (a.z * sc_adj));
+                            acc.add(y[v][4 * nq + 3] * (a.w * sc_adj));
+                        }
+                }
             }
-            ldot = (double)acc.value();
         }
+        if (MODE == 2) ldot = (double)acc.value();
         }
     }
     if (MODE == 1) {
