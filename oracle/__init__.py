@@ -51,9 +51,10 @@ def lib():
         _lib.or_peps_energy.argtypes = [i32, i32, i32, P, d, d, P, P, P, P, P]
         _lib.or_peps_expect_one.argtypes = [i32, i32, i32, P, i32, i32, i32, P, P, P]
         _lib.or_ising_enumerate.argtypes = [i32, i32, d, P, P, P]
+        _lib.or_peps_sz.argtypes = [i32, i32, i32, P, P]
         for f in (_lib.or_grid_contract, _lib.or_peps_norm, _lib.or_peps_norm_all_cuts,
                   _lib.or_peps_observables, _lib.or_peps_energy, _lib.or_peps_expect_one,
-                  _lib.or_ising_enumerate, _lib.or_num_threads):
+                  _lib.or_ising_enumerate, _lib.or_num_threads, _lib.or_peps_sz):
             f.restype = i32
     return _lib
 
@@ -105,6 +106,14 @@ class Observables:
     norm_e: int
     sx: np.ndarray
     szsz: np.ndarray
+    sz: np.ndarray | None = None     # <Z_k>, filled by observables(..., with_z=True)
+
+    def connected(self, L: int, W: int) -> np.ndarray:
+        """c_ij = <Z_i Z_j> - <Z_i><Z_j> per bond (Eq. cij), bond order of szsz."""
+        from paper_1908_08553_gb300.inputs import bonds
+        i = np.array([a[0] * W + a[1] for a, _ in bonds(L, W)], dtype=np.int64)
+        j = np.array([b[0] * W + b[1] for _, b in bonds(L, W)], dtype=np.int64)
+        return self.szsz - self.sz[i] * self.sz[j]
 
     def energy(self, J: float, h: float) -> float:
         """E = -J sum <zz> - h sum <x> (Eqs. Hamiltonian and Etot)."""
@@ -115,21 +124,25 @@ class Observables:
         return float(np.log2(abs(self.norm_m)) + self.norm_e)
 
 
-def observables(L: int, W: int, D: int, A: np.ndarray) -> Observables:
+def observables(L: int, W: int, D: int, A: np.ndarray, with_z: bool = False) -> Observables:
     A = _check_sites(L, W, D, A)
     nb = L * (W - 1) + W * (L - 1)
     m, e = np.zeros(1), np.zeros(1, np.int64)
     sx, szsz = np.zeros(L * W), np.zeros(max(nb, 1))
     lib().or_peps_observables(L, W, D, _ptr(A), _ptr(m), _ptr(e), _ptr(sx), _ptr(szsz))
-    return Observables(float(m[0]), int(e[0]), sx, szsz[:nb])
+    sz = None
+    if with_z:
+        sz = np.zeros(L * W)
+        lib().or_peps_sz(L, W, D, _ptr(A), _ptr(sz))
+    return Observables(float(m[0]), int(e[0]), sx, szsz[:nb], sz)
 
 
 def expect_one(L: int, W: int, D: int, A: np.ndarray, op: str, i: int = 0, j: int = 0):
-    """One observable with only two cached boundaries: op in {'norm', 'x', 'zz'}.
+    """One observable with only two cached boundaries: op in {'norm', 'x', 'zz', 'z'}.
 
     Returns (ratio, norm_mantissa, norm_exponent)."""
     A = _check_sites(L, W, D, A)
-    code = {"norm": 0, "x": 1, "zz": 2}[op]
+    code = {"norm": 0, "x": 1, "zz": 2, "z": 3}[op]
     v, m, e = np.zeros(1), np.zeros(1), np.zeros(1, np.int64)
     rc = lib().or_peps_expect_one(L, W, D, _ptr(A), code, i, j, _ptr(v), _ptr(m), _ptr(e))
     if rc != 0:

@@ -76,6 +76,14 @@ def observables(L: int, W: int, D: int, flat: np.ndarray):
     return norm, sx, np.array(zz)
 
 
+def sz(L: int, W: int, D: int, flat: np.ndarray) -> np.ndarray:
+    """<Z_k>[N] straight from the state vector (p = 1 <-> sigma = +1)."""
+    psi = state_vector(L, W, D, flat)
+    idx = np.arange(psi.size)
+    w = psi * psi
+    return np.array([float(np.sum(w * np.where((idx >> k) & 1, 1.0, -1.0))) for k in range(L * W)]) / float(w.sum())
+
+
 def hamiltonian(L: int, W: int, J: float, h: float):
     """Sparse TFIM Hamiltonian -J sum Z_i Z_j - h sum X_k on the 2^N basis."""
     import scipy.sparse as sp

@@ -399,6 +399,42 @@ int or_peps_observables(int L, int W, int D, const double *A,
     return 0;
 }
 
+/*
+ * <Z_k> for every site (Eq. mz with Pauli Z), with cached boundaries:
+ * sz[L*W] in row-major site order (caller-owned).  Sec. 3 defines the
+ * connected correlator c_ij = <Z_i Z_j> - <Z_i><Z_j> from these and szsz.
+ */
+int or_peps_sz(int L, int W, int D, const double *A, double *sz) {
+    grid_t g = norm_grid(L, W, D, A);
+    size_t *off = site_offsets(L, W, D);
+    bnd_t *tops = (bnd_t *)malloc(sizeof(bnd_t) * (L + 1));
+    bnd_t *bots = (bnd_t *)malloc(sizeof(bnd_t) * (L + 1));
+    top_boundaries(&g, tops);
+    bottom_boundaries(&g, bots);
+    double nm; int64_t ne;
+    bnd_dot(&tops[L], &bots[L], &nm, &ne);
+    double **over = (double **)calloc((size_t)W, sizeof(double *));
+    for (int r = 0; r < L; ++r)
+        for (int c = 0; c < W; ++c) {
+            int d[4];
+            site_dims(L, W, D, r, c, d);
+            double *ez = double_layer(A + off[r * W + c], d, OP_Z);
+            bnd_t b = bnd_copy(&tops[r]);
+            over[c] = ez;
+            absorb_row(&g, r, over, &b);
+            over[c] = NULL;
+            double m; int64_t e;
+            bnd_dot(&b, &bots[r + 1], &m, &e);
+            sz[r * W + c] = ratio(m, e, nm, ne);
+            free(b.v); free(ez);
+        }
+    free(over);
+    for (int r = 0; r <= L; ++r) { free(tops[r].v); free(bots[r].v); }
+    free(tops); free(bots); free(off);
+    grid_free(&g);
+    return 0;
+}
+
 /* E = -J sum <zz> - h sum <x>; also returns everything or_peps_observables does. */
 int or_peps_energy(int L, int W, int D, const double *A, double J, double h,
                    double *norm_m, int64_t *norm_e, double *sx, double *szsz,
@@ -415,7 +451,8 @@ int or_peps_energy(int L, int W, int D, const double *A, double J, double h,
 /*
  * One observable alone, keeping only two boundaries (for sampled checks of
  * lattices too large for the cached version).  op: 0 = norm (i, j ignored),
- * 1 = X at site i, 2 = Z_i Z_j on the bond (i, j) (site indices, row-major).
+ * 1 = X at site i, 2 = Z_i Z_j on the bond (i, j) (site indices, row-major),
+ * 3 = Z at site i.
  * Returns the ratio to the norm in *val and the norm in (*nm, *ne).
  */
 int or_peps_expect_one(int L, int W, int D, const double *A, int op, int i, int j,
@@ -424,7 +461,7 @@ int or_peps_expect_one(int L, int W, int D, const double *A, int op, int i, int 
     size_t *off = site_offsets(L, W, D);
     int ri = i / W, ci = i % W, rj = j / W, cj = j % W;
     int rlo = 0, rhi = 0;  /* rows [rlo, rhi] carry the insertions */
-    if (op == 1) { rlo = rhi = ri; }
+    if (op == 1 || op == 3) { rlo = rhi = ri; }
     if (op == 2) {
         if (!((ri == rj && cj == ci + 1) || (ci == cj && rj == ri + 1))) {
             free(off); grid_free(&g); return -1;
@@ -450,9 +487,9 @@ int or_peps_expect_one(int L, int W, int D, const double *A, int op, int i, int 
         double **over = (double **)calloc((size_t)W, sizeof(double *));
         bnd_t b = bnd_copy(&top);
         int d[4];
-        if (op == 1) {
+        if (op == 1 || op == 3) {
             site_dims(L, W, D, ri, ci, d);
-            over[ci] = double_layer(A + off[i], d, OP_X);
+            over[ci] = double_layer(A + off[i], d, op == 1 ? OP_X : OP_Z);
             absorb_row(&g, ri, over, &b);
             free(over[ci]); over[ci] = NULL;
         } else {
