@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 L_, W_, D_ = 8, 8, 2
 H_FIELDS = (2.0, 3.04, 4.0)
 METRIC = "exact LxL Ising-PEPS energy evals/s"
+ABSORB_DRAM_PER_BYTE = 1023.75 / 1207.96   # k_absorb4<16,16,1,0> capture, profiles/k_absorb4_8x8_d2_batch64.md
 WORKLOAD = "8x8 open-boundary TFIM PEPS, D=2, E at h in {2.0, 3.04, 4.0}"
 
 
@@ -393,7 +394,7 @@ def run_batch(args):
         off = 0
         for k in g:
             L, W = int(Ls[k]), int(Ws[k])
-            nres = 6 + L * W + L * (W - 1) + W * (L - 1)
+            nres = 6 + 2 * L * W + L * (W - 1) + W * (L - 1)
             results[k] = r[off:off + nres]
             off += nres
         tn.tn_batch_destroy(b)
@@ -462,7 +463,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16x3", "bf16x6"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-lattices", type=int, default=2)
-    ap.add_argument("--cpu-lattices", type=int, default=3)
+    ap.add_argument("--cpu-lattices", type=int, default=10)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 line and the CPU baseline")
     ap.add_argument("--workload", default="8x8", choices=["8x8", "large", "serve", "batch", "case"],
                     help="8x8: the bench line; large: 12x12 D=2 / 8x8 D=3; serve: Poisson request "
@@ -591,9 +592,19 @@ def main():
             return None
         if name in ("absorb", "absorb_dot", "other"):
             achieved = fd["bytes"] / (fd["ms"] / 1e3) / 1e9
-            return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                    "traffic": None, "kernel": name,
-                    "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs (of {src})"}
+            traffic, note = None, None
+            if name == "absorb" and prec == tn.TN_FP32:
+                # DRAM bytes per algorithmic byte of the interior FP32 absorption,
+                # from one ncu capture (8x8 D=2, 64 lattices: 1024 MB of DRAM
+                # traffic for 1208 MB in + out), applied to this run's average launch
+                traffic = ABSORB_DRAM_PER_BYTE * fd["bytes"] / fd["launches"]
+                note = "ncu dram bytes/algorithmic bytes of one interior launch x mean bytes per launch"
+            r = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                 "traffic": traffic, "kernel": name,
+                 "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs (of {src})"}
+            if note:
+                r["traffic_source"] = note
+            return r
         if name == "gemm_tc":
             algo = 2 * fd["macs"] / (fd["ms"] / 1e3) / 1e12
             achieved = products * algo
@@ -647,7 +658,7 @@ def main():
             torch.cuda.synchronize()
             r64 = tn.tn_batch_results_host(b64)
             t64 = e0.elapsed_time(e1) / 3 / 1e3
-            stride = 6 + 64 + 112
+            stride = n_res // B     # per member: header, <X_k>, <Z_i Z_j>, <Z_k>
             rel = float(np.max(np.abs(res[0::stride][:B] - r64[0::stride][:B]) /
                                np.maximum(1.0, np.abs(r64[0::stride][:B]))))
             line["fp64_gpu"] = {"value": B / t64, "unit": "lattice evals/s",

@@ -6,7 +6,9 @@
  *   <Z_i Z_j> (first term of Eq. cij) and the transverse-field Ising energy
  *   E = -J sum_<ij> <Z_i Z_j> - h sum_k <X_k> (Eqs. Hamiltonian, Etot), with
  *   Pauli operators (spins +-1) and Z = diag(-1, +1) on the physical index p,
- *   because p = 1 is sigma = +1 (Eq. Psi, x = (sigma + 1)/2).
+ *   because p = 1 is sigma = +1 (Eq. Psi, x = (sigma + 1)/2); also every
+ *   <Z_k> (Eq. mz with Pauli Z) and the connected correlators
+ *   c_ij = <Z_i Z_j> - <Z_i><Z_j> (Eq. cij) of the nearest-neighbour bonds.
  *
  * How (Sec. 4): the double-layer network <Psi|O|Psi> (bond dimension D^2) is
  * contracted exactly as chains of pairwise contractions that absorb one site
@@ -74,13 +76,14 @@ typedef enum {
 
 typedef enum {
     TN_WORK_NORM = 0,      /* <Psi|Psi> only */
-    TN_WORK_ENERGY = 1     /* norm, every <X_k>, every <Z_i Z_j> */
+    TN_WORK_ENERGY = 1     /* norm, every <X_k>, every <Z_i Z_j>, every <Z_k> */
 } tn_work;
 
 typedef enum {
     TN_OP_NORM = 0,        /* <Psi|Psi> (returned as a ratio 1) */
     TN_OP_X = 1,           /* <X_i>, Eq. mx */
-    TN_OP_ZZ = 2           /* <Z_i Z_j> for nearest neighbours i, j, Eq. cij first term */
+    TN_OP_ZZ = 2,          /* <Z_i Z_j> for nearest neighbours i, j, Eq. cij first term */
+    TN_OP_Z = 3            /* <Z_i>, Eq. mz with Pauli Z */
 } tn_op;
 
 /* value = mant * 2^exp2 (the norm of a large lattice leaves the FP64 range). */
@@ -98,6 +101,8 @@ typedef struct {
     double err_bound_est;     /* a-priori relative rounding bound of the precision used */
     int precision;            /* tn_precision used */
     int schedule_o, schedule_i, schedule_j;   /* partition actually used (see tn_plan) */
+    double *sz;               /* caller-owned, L*W entries <Z_k>, or NULL */
+    double *czz;              /* caller-owned, nb entries c_ij = <Z_i Z_j> - <Z_i><Z_j>, or NULL */
 } tn_result;
 
 typedef struct tn_ctx tn_ctx;
@@ -159,10 +164,12 @@ tn_status tn_plan_work(const tn_lattice *lat, tn_schedule sched, tn_work work, i
 
 /* <Psi|Psi> (blocking). */
 tn_status tn_contract_norm(tn_lattice *lat, tn_precision prec, tn_schedule sched, tn_scalar *out);
-/* One expectation value (blocking): op = TN_OP_X with site i = r*W + c, or
- * TN_OP_ZZ with nearest-neighbour sites i < j.  Returns the ratio to the norm. */
+/* One expectation value (blocking): op = TN_OP_X or TN_OP_Z with site
+ * i = r*W + c, or TN_OP_ZZ with nearest-neighbour sites i < j.  Returns the
+ * ratio to the norm. */
 tn_status tn_expectation(tn_lattice *lat, tn_precision prec, int op, int i, int j, double *out);
-/* Norm, every <X_k>, every <Z_i Z_j> and E for (J, h) (blocking, AUTO schedule). */
+/* Norm, every <X_k>, every <Z_i Z_j>, every <Z_k>, the connected c_ij and E
+ * for (J, h) (blocking, AUTO schedule); each array of *out is filled if non-NULL. */
 tn_status tn_energy(tn_lattice *lat, double J, double h, tn_precision prec, tn_result *out);
 /* As tn_energy with an explicit schedule. */
 tn_status tn_energy_sched(tn_lattice *lat, double J, double h, tn_precision prec,
@@ -189,8 +196,8 @@ tn_status tn_batch_fill_random(tn_batch *b, uint64_t batch_seed);
 /* Run the whole batch (asynchronous on the ctx stream).  h holds one field per
  * member; J is shared. */
 tn_status tn_batch_run(tn_batch *b, double J, const double *h);
-/* Per member: 6 + L*W + nb doubles [energy, log2 norm, norm mantissa, norm
- * exponent, sum_k <X_k>, sum_<ij> <Z_i Z_j>, <X_k>..., <Z_i Z_j>...]
+/* Per member: 6 + 2 L*W + nb doubles [energy, log2 norm, norm mantissa, norm
+ * exponent, sum_k <X_k>, sum_<ij> <Z_i Z_j>, <X_k>..., <Z_i Z_j>..., <Z_k>...]
  * (work = ENERGY) or 6 doubles (NORM), members concatenated.  E at any other
  * field is -J * [5] - h * [4].  _size gives the total; _host synchronises and copies;
  * _device returns the device pointer of the same array (valid until the next

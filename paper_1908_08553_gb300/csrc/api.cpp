@@ -59,7 +59,7 @@ void fill_uniform(uint64_t seed, double* out, size_t n) {
     }
 }
 
-// tn_result from one member's result array [header | <X_k> | <Z_i Z_j>].
+// tn_result from one member's result array [header | <X_k> | <Z_i Z_j> | <Z_k>].
 tn_status result_from_array(const double* r, int L, int W, tn_precision prec, const Plan& p, tn_result* out) {
     const int N = L * W, nb = L * (W - 1) + W * (L - 1);
     out->energy = r[0];
@@ -68,6 +68,16 @@ tn_status result_from_array(const double* r, int L, int W, tn_precision prec, co
     out->norm.exp2 = (int64_t)r[3];
     if (out->sx) std::memcpy(out->sx, r + kResultHeader, sizeof(double) * N);
     if (out->szsz) std::memcpy(out->szsz, r + kResultHeader + N, sizeof(double) * nb);
+    const double* z = r + kResultHeader + N + nb;
+    if (out->sz) std::memcpy(out->sz, z, sizeof(double) * N);
+    if (out->czz) {
+        // c_ij = <Z_i Z_j> - <Z_i><Z_j> (Eq. cij), bonds in output order
+        int b = 0;
+        for (int rr = 0; rr < L; ++rr)
+            for (int c = 0; c + 1 < W; ++c, ++b) out->czz[b] = r[kResultHeader + N + b] - z[rr * W + c] * z[rr * W + c + 1];
+        for (int rr = 0; rr + 1 < L; ++rr)
+            for (int c = 0; c < W; ++c, ++b) out->czz[b] = r[kResultHeader + N + b] - z[rr * W + c] * z[(rr + 1) * W + c];
+    }
     out->err_bound_est = unit_roundoff(prec) * (double)(2 * N + 4);
     out->precision = (int)prec;
     out->schedule_o = p.o;
@@ -307,7 +317,7 @@ tn_status tn_expectation(tn_lattice* lat, tn_precision prec, int op, int i, int 
     if (!lat || !out) return TN_ERR_INVALID;
     const int L = lat->L, W = lat->W, N = L * W;
     if (op == TN_OP_NORM) { *out = 1.0; return TN_OK; }
-    if (op == TN_OP_X) {
+    if (op == TN_OP_X || op == TN_OP_Z) {
         if (i < 0 || i >= N) return TN_ERR_INVALID;
     } else if (op == TN_OP_ZZ) {
         if (i < 0 || j < 0 || i >= N || j >= N) return TN_ERR_INVALID;
@@ -321,6 +331,7 @@ tn_status tn_expectation(tn_lattice* lat, tn_precision prec, int op, int i, int 
     tn_status s = run_single(lat, prec, TN_SCHED_AUTO, TN_WORK_ENERGY, 1.0, 0.0, &r, nullptr);
     if (s != TN_OK) return s;
     if (op == TN_OP_X) { *out = r[kResultHeader + i]; return TN_OK; }
+    if (op == TN_OP_Z) { *out = r[kResultHeader + N + L * (W - 1) + W * (L - 1) + i]; return TN_OK; }
     const int ri = i / W, ci = i % W;
     int bi;
     if (j == i + 1 && ri == j / W) bi = ri * (W - 1) + ci;

@@ -80,7 +80,8 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 }
 
 // Compensated sum (Neumaier's variant of Kahan summation) for the per-thread
-// FP32 parts of every dot product; FP64 sums are plain.
+// FP32 parts of every dot product (the FP32 absorption kernel feeds it the sum
+// of a thread's 4 outer positions per output column); FP64 sums are plain.
 template <typename T>
 struct CSum {
     T s = T(0), c = T(0);
@@ -236,10 +237,11 @@ k_absorb_one(const __grid_constant__ AbsorbTask t) {
 constexpr int kV2Threads = 128;
 
 template <int K, int N, int MODE, bool ALONG_P>
-__global__ void __launch_bounds__(kV2Threads, MODE == 4 ? 3 : 4)
+__global__ void __launch_bounds__(kV2Threads, MODE >= 4 ? 3 : 4)
 k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
     __shared__ __align__(16) float Es[K * N];
-    __shared__ __align__(16) float Es2[MODE == 4 ? K * N : 4];
+    __shared__ __align__(16) float Es2[MODE >= 4 ? K * N : 4];
+    __shared__ __align__(16) float Es3[MODE == 5 ? K * N : 4];
     __shared__ double red[32];
     const long long tile = blockIdx.x;
     const AbsorbTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
@@ -248,7 +250,8 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
     for (int idx = threadIdx.x; idx < K * N; idx += blockDim.x) {
         const int k = idx / N, n = idx - k * N;
         Es[idx] = t.transE ? E[n * K + k] : E[idx];
-        if (MODE == 4) Es2[idx] = static_cast<const float*>(t.E2)[idx];
+        if (MODE >= 4) Es2[idx] = static_cast<const float*>(t.E2)[idx];
+        if (MODE == 5) Es3[idx] = static_cast<const float*>(t.E3)[idx];
     }
     const int e_in = slot_shift(&slots[t.slot_in]);
     const float sc_in = pow2<float>(-e_in);
@@ -263,7 +266,7 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
     const long long ngroups = ALONG_P ? t.P / 4 : t.P * (S / 4);
     const long long g = local * kV2Threads + threadIdx.x;
     float lmax = 0.0f;
-    double ldot = 0.0, ldot2 = 0.0;
+    double ldot = 0.0, ldot2 = 0.0, ldot3 = 0.0;
     if (g < ngroups) {
         long long p, s;
         if (ALONG_P) { p = 4 * g; s = 0; }
@@ -292,38 +295,42 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
         for (int k = 0; k < K; ++k)
 #pragma unroll
             for (int v = 0; v < 4; ++v) x[v][k] *= sc_in;      // inputs scaled once
-        if (MODE == 4) {
-            // dual dot: per group of 4 outputs n, both site matrices, then the
-            // adjoint (keeps two accumulator sets of 16 instead of 2 N x 4)
+        if (MODE >= 4) {
+            // dual (triple) dot: per group of 4 outputs n, every site matrix,
+            // then the adjoint (keeps NE accumulator sets of 16, not NE x 4 x N)
+            constexpr int NE = MODE == 5 ? 3 : 2;
             const float* adj = static_cast<const float*>(t.adj);
-            CSum<float> acc1, acc2;
+            CSum<float> acc[NE];
 #pragma unroll
             for (int nq = 0; nq < (N + 3) / 4; ++nq) {
                 constexpr int NW = N >= 4 ? 4 : 1;
-                float z1[4][NW], z2[4][NW];
+                float z[NE][4][NW];
 #pragma unroll
-                for (int v = 0; v < 4; ++v)
+                for (int q = 0; q < NE; ++q)
 #pragma unroll
-                    for (int j = 0; j < NW; ++j) { z1[v][j] = 0.0f; z2[v][j] = 0.0f; }
+                    for (int v = 0; v < 4; ++v)
+#pragma unroll
+                        for (int j = 0; j < NW; ++j) z[q][v][j] = 0.0f;
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
-                    float e1[NW], e2[NW];
-                    if (NW == 4) {
-                        const float4 a1 = *reinterpret_cast<const float4*>(&Es[k * N + 4 * nq]);
-                        const float4 a2 = *reinterpret_cast<const float4*>(&Es2[k * N + 4 * nq]);
-                        e1[0] = a1.x; e1[1] = a1.y; e1[2] = a1.z; e1[3] = a1.w;
-                        e2[0] = a2.x; e2[1] = a2.y; e2[2] = a2.z; e2[3] = a2.w;
-                    } else {
-                        e1[0] = Es[k]; e2[0] = Es2[k];
+                    float e[NE][NW];
+#pragma unroll
+                    for (int q = 0; q < NE; ++q) {
+                        const float* Eq = q == 0 ? Es : (q == 1 ? Es2 : Es3);
+                        if (NW == 4) {
+                            const float4 a4 = *reinterpret_cast<const float4*>(&Eq[k * N + 4 * nq]);
+                            e[q][0] = a4.x; e[q][1] = a4.y; e[q][2] = a4.z; e[q][3] = a4.w;
+                        } else {
+                            e[q][0] = Eq[k];
+                        }
                     }
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const float xv = x[v][k];
 #pragma unroll
-                        for (int j = 0; j < NW; ++j) {
-                            z1[v][j] = fmaf(xv, e1[j], z1[v][j]);
-                            z2[v][j] = fmaf(xv, e2[j], z2[v][j]);
-                        }
+                        for (int q = 0; q < NE; ++q)
+#pragma unroll
+                            for (int j = 0; j < NW; ++j) z[q][v][j] = fmaf(xv, e[q][j], z[q][v][j]);
                     }
                 }
 #pragma unroll
@@ -337,15 +344,19 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
 #pragma unroll
                         for (int v = 0; v < 4; ++v) a[v] = __ldg(adj + (p + v) * N + n);
                     }
+                    // the 4 outer positions of this column summed first, then compensated
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        acc1.add(z1[v][j] * (a[v] * sc_adj));
-                        acc2.add(z2[v][j] * (a[v] * sc_adj));
+                    for (int q = 0; q < NE; ++q) {
+                        float g = z[q][0][j] * (a[0] * sc_adj);
+#pragma unroll
+                        for (int v = 1; v < 4; ++v) g = fmaf(z[q][v][j], a[v] * sc_adj, g);
+                        acc[q].add(g);
                     }
                 }
             }
-            ldot = (double)acc1.value();
-            ldot2 = (double)acc2.value();
+            ldot = (double)acc[0].value();
+            ldot2 = (double)acc[1].value();
+            if (NE == 3) ldot3 = (double)acc[NE - 1].value();
         } else {
         // outputs formed NC columns at a time (8 of 16 when along s) so a
         // thread holds 4 x NC accumulators, not 4 x N
@@ -405,10 +416,12 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
 #pragma unroll
                     for (int j = 0; j < NC; ++j) {
                         const float4 a = __ldg(reinterpret_cast<const float4*>(adj + (p * N + h * NC + j) * S + s));
-                        acc.add(y[0][j] * (a.x * sc_adj));
-                        acc.add(y[1][j] * (a.y * sc_adj));
-                        acc.add(y[2][j] * (a.z * sc_adj));
-                        acc.add(y[3][j] * (a.w * sc_adj));
+                        // the 4 outer positions of this column summed first, then compensated
+                        float g = y[0][j] * (a.x * sc_adj);
+                        g = fmaf(y[1][j], a.y * sc_adj, g);
+                        g = fmaf(y[2][j], a.z * sc_adj, g);
+                        g = fmaf(y[3][j], a.w * sc_adj, g);
+                        acc.add(g);
                     }
                 } else if (N == 1) {
                     const float4 a = __ldg(reinterpret_cast<const float4*>(adj + p));
@@ -443,10 +456,15 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
         const double part = block_sum(ldot, red);
         const long long X = slots[t.slot_in].X + e_in + slots[t.slot_E].X + slots[t.slot_adj].X + e_adj;
         finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_out], X, red);
-        if (MODE == 4) {
+        if (MODE >= 4) {
             const double part2 = block_sum(ldot2, red);
             const long long X2 = slots[t.slot_in].X + e_in + slots[t.slot_E2].X + slots[t.slot_adj].X + e_adj;
             finish_sum(part2, t.partial + t.ntiles, t.ntiles, local, &slots[t.slot_out2], X2, red);
+        }
+        if (MODE == 5) {
+            const double part3 = block_sum(ldot3, red);
+            const long long X3 = slots[t.slot_in].X + e_in + slots[t.slot_E3].X + slots[t.slot_adj].X + e_adj;
+            finish_sum(part3, t.partial + 2 * (long long)t.ntiles, t.ntiles, local, &slots[t.slot_out3], X3, red);
         }
     }
 }
@@ -583,9 +601,11 @@ cudaError_t launch_absorb(int dt, bool dot, int K, int N, const AbsorbTask* task
     if (variant == 2)
         return dot ? absorb4_dispatch<2, true>(K, N, tasks, ntasks, nblocks, slots, st, tmap)
                    : absorb4_dispatch<1, true>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
-    // 11 / 12: the dual dot of variants 1 / 2
+    // 11 / 12: the dual dot of variants 1 / 2; 21 / 22: the triple dot
     if (variant == 11) return absorb4_dispatch<4, false>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
     if (variant == 12) return absorb4_dispatch<4, true>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
+    if (variant == 21) return absorb4_dispatch<5, false>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
+    if (variant == 22) return absorb4_dispatch<5, true>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
     if (dt == 0)
         return dot ? absorb_dispatch<double, 2>(K, N, tasks, ntasks, nblocks, slots, st, tmap)
                    : absorb_dispatch<double, 1>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
@@ -1184,6 +1204,11 @@ __global__ void k_final(const FinalTask* __restrict__ tasks, const Slot* __restr
         const Slot& s = slots[t.zz_slots[k]];
         const Slot& d = slots[t.zz_den[k]];
         v[t.n_sites + k] = ldexp(s.mant / d.mant, (int)(s.X - d.X));
+    }
+    for (int k = threadIdx.x; k < t.n_sites; k += blockDim.x) {
+        const Slot& s = slots[t.sz_slots[k]];
+        const Slot& d = slots[t.sx_den[k]];
+        v[t.n_sites + t.n_bonds + k] = ldexp(s.mant / d.mant, (int)(s.X - d.X));
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -136,26 +136,28 @@ public:
         return out;
     }
 
-    // Whether the FP32 streaming absorption serves this step (it has the dual dot).
+    // Whether the FP32 streaming absorption serves this step (it has the triple dot).
     bool dual_ok(const Step& s) const {
         const int v = absorb_variant(pg_.dt == DT_F64 ? 0 : 1, s.P, s.S, s.K, s.N);
         return pg_.dt == DT_F32 && !(pg_.nsplit && s.K == 81 && s.N == 81) && (v == 1 || v == 2);
     }
 
-    // (<absorb(in, E), adj>, <absorb(in, E2), adj>) in one pass over in and adj.
-    std::pair<int, int> absorb_dot2(int in, int E, int E2, int adj, const Step& s) {
-        const int level = std::max({level_of(in), level_of(E), level_of(E2), level_of(adj)}) + 1;
-        const int out = scalar(level), out2 = scalar(level);
+    // (<absorb(in, E), adj>, <absorb(in, E2), adj>, <absorb(in, E3), adj>) in
+    // one pass over in and adj.
+    std::tuple<int, int, int> absorb_dot3(int in, int E, int E2, int E3, int adj, const Step& s) {
+        const int level = std::max({level_of(in), level_of(E), level_of(E2), level_of(E3), level_of(adj)}) + 1;
+        const int out = scalar(level), out2 = scalar(level), out3 = scalar(level);
         Op op;
         op.kind = OP_ABSORB_DOT;
         op.level = level;
-        op.in = in; op.E = E; op.E2 = E2; op.adj = adj; op.out = out; op.out2 = out2;
+        op.in = in; op.E = E; op.E2 = E2; op.E3 = E3; op.adj = adj;
+        op.out = out; op.out2 = out2; op.out3 = out3;
         op.P = s.P; op.S = s.S; op.K = s.K; op.N = s.N;
         op.bytes = (double)(s.n_in + s.n_out) * pg_.esize;
-        op.macs = 2.0 * ((double)s.mac + (double)s.n_out);
-        use(in, level); use(E, level); use(E2, level); use(adj, level);
+        op.macs = 3.0 * ((double)s.mac + (double)s.n_out);
+        use(in, level); use(E, level); use(E2, level); use(E3, level); use(adj, level);
         add(op);
-        return {out, out2};
+        return {out, out2, out3};
     }
 
     // Tiled BF16 planes of the operand X[r][k] = src[r*sr + k*sk] (one per view).
@@ -388,7 +390,7 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
             G[q][T] = Env[q];
             for (int t = T; t >= 2; --t) G[q][t - 1] = bd.absorb(G[q][t], E_at(q, t, PH_I), step_of(q, t), true);
         }
-        // norm along each step's path: <F[q][t], G[q][t]> (from the site's dual
+        // norm along each step's path: <F[q][t], G[q][t]> (from the site's triple
         // absorb-dot where the streaming kernel serves the step, else a dot)
         std::map<std::pair<int, int>, int> local_norm;
         auto norm_at = [&](int q, int t) {
@@ -402,19 +404,23 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
         };
         // sites
         pg.sx_slot.assign(nsite, -1);
+        pg.sz_slot.assign(nsite, -1);
         pg.sx_den.assign(nsite, -1);
         for (int s = 0; s < nsite; ++s) {
             const SiteRef& w = where[s];
             const Step& st = step_of(w.q, w.t);
             if (bd.dual_ok(st)) {
-                // the site's <X> and the local norm <absorb(F[t-1], E_I), G[t]> in one pass
-                const auto v2 = bd.absorb_dot2(F[w.q][w.t - 1], E_at(w.q, w.t, PH_X), E_at(w.q, w.t, PH_I),
-                                               G[w.q][w.t], st);
-                pg.sx_slot[s] = pg.tensors[v2.first].slot;
-                local_norm[std::make_pair(w.q, w.t)] = pg.tensors[v2.second].slot;
+                // the site's <X>, <Z> and the local norm <absorb(F[t-1], E_I), G[t]> in one pass
+                const auto v3 = bd.absorb_dot3(F[w.q][w.t - 1], E_at(w.q, w.t, PH_X), E_at(w.q, w.t, PH_Z),
+                                               E_at(w.q, w.t, PH_I), G[w.q][w.t], st);
+                pg.sx_slot[s] = pg.tensors[std::get<0>(v3)].slot;
+                pg.sz_slot[s] = pg.tensors[std::get<1>(v3)].slot;
+                local_norm[std::make_pair(w.q, w.t)] = pg.tensors[std::get<2>(v3)].slot;
             } else {
-                const int v = bd.absorb_dot(F[w.q][w.t - 1], E_at(w.q, w.t, PH_X), G[w.q][w.t], st);
-                pg.sx_slot[s] = pg.tensors[v].slot;
+                const int vx = bd.absorb_dot(F[w.q][w.t - 1], E_at(w.q, w.t, PH_X), G[w.q][w.t], st);
+                const int vz = bd.absorb_dot(F[w.q][w.t - 1], E_at(w.q, w.t, PH_Z), G[w.q][w.t], st);
+                pg.sx_slot[s] = pg.tensors[vx].slot;
+                pg.sz_slot[s] = pg.tensors[vz].slot;
             }
             pg.sx_den[s] = norm_at(w.q, w.t);
         }

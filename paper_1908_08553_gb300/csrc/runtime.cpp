@@ -42,6 +42,7 @@ int family_of(int kind) {
 // Build every launch and its task table.  With base == nullptr only sizes are
 // computed (footprint); otherwise task structs hold absolute device pointers.
 long long absorb_tiles_any(int var, long long P, long long S, int K, int N) {
+    if (var >= 20) return absorb_tiles_v(var - 20, P, S, K, N);   // triple dot of variants 1 / 2
     if (var >= 10) return absorb_tiles_v(var - 10, P, S, K, N);   // dual dot of variants 1 / 2
     if (var >= 3) return tc_absorb_tiles(P, S);
     return absorb_tiles_v(var, P, S, K, N);
@@ -63,7 +64,8 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         mb.slot_base = nslots;
         nslots += mb.pg->n_slots;
         mb.res_off = nres;
-        mb.res_elems = kResultHeader + (int64_t)mb.pg->sx_slot.size() + (int64_t)mb.pg->zz_slot.size();
+        mb.res_elems = kResultHeader + (int64_t)mb.pg->sx_slot.size() + (int64_t)mb.pg->zz_slot.size() +
+                       (int64_t)mb.pg->sz_slot.size();
         nres += mb.res_elems;
     }
     lay.nin = nin;
@@ -80,9 +82,11 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
             if (op.kind == OP_ABSORB || op.kind == OP_ABSORB_DOT) {
                 K = op.K; N = op.N;
                 // 3 / 4: tensor-core absorption with 2 / 3 split planes
-                // 3 / 4: tensor-core absorption with 2 / 3 split planes; 11 / 12: dual dot; else 0..2
+                // 3 / 4: tensor-core absorption with 2 / 3 split planes; 11 / 12: dual dot;
+                // 21 / 22: triple dot; else 0..2
                 var = op.nsplit ? 1 + op.nsplit : absorb_variant(b->dt, op.P, op.S, op.K, op.N);
-                if (op.E2 >= 0) var += 10;
+                if (op.E3 >= 0) var += 20;
+                else if (op.E2 >= 0) var += 10;
             } else if (op.kind == OP_GEMM || op.kind == OP_GEMM_DOT) {
                 var = gemm_variant(b->dt, op.gm, op.gn, op.gk, op.sam, op.sak, op.sbk, op.sbn);
             } else if (op.kind == OP_TC_GEMM || op.kind == OP_TC_GEMM_DOT) {
@@ -120,7 +124,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
             const Op& op = b->m[r.member].pg->ops[r.op];
             if (kind == OP_ABSORB_DOT) {
                 const int var = std::get<4>(kv.first);
-                npart += (op.E2 >= 0 ? 2 : 1) * absorb_tiles_any(var, op.P, op.S, op.K, op.N);
+                npart += (1 + (op.E2 >= 0) + (op.E3 >= 0)) * absorb_tiles_any(var, op.P, op.S, op.K, op.N);
             }
             else if (kind == OP_GEMM_DOT) {
                 int tn_;
@@ -202,11 +206,16 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 if (kind == OP_ABSORB_DOT) {
                     t.adj = tensor_ptr(r.member, op.adj);
                     t.slot_adj = slot_of(r.member, op.adj);
-                    t.partial = take_partial(op.E2 >= 0 ? 2 * nt : nt);
+                    t.partial = take_partial((1 + (op.E2 >= 0) + (op.E3 >= 0)) * nt);
                     if (op.E2 >= 0) {
                         t.E2 = tensor_ptr(r.member, op.E2);
                         t.slot_E2 = slot_of(r.member, op.E2);
                         t.slot_out2 = slot_of(r.member, op.out2);
+                    }
+                    if (op.E3 >= 0) {
+                        t.E3 = tensor_ptr(r.member, op.E3);
+                        t.slot_E3 = slot_of(r.member, op.E3);
+                        t.slot_out3 = slot_of(r.member, op.out3);
                     }
                 } else {
                     t.out = tensor_ptr(r.member, op.out);
@@ -326,7 +335,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
     }
     // final tasks and their slot tables
     b->h_final.clear();
-    struct Tbl { size_t sx, zz, sxd, zzd; };
+    struct Tbl { size_t sx, zz, sxd, zzd, sz; };
     std::vector<Tbl> tbl;   // offsets in ints
     for (int mi = 0; mi < (int)b->m.size(); ++mi) {
         const Member& mb = b->m[mi];
@@ -340,6 +349,8 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         for (int s : pg.sx_den) ints.push_back((int)(mb.slot_base + s));
         tb.zzd = ints.size();
         for (int s : pg.zz_den) ints.push_back((int)(mb.slot_base + s));
+        tb.sz = ints.size();
+        for (int s : pg.sz_slot) ints.push_back((int)(mb.slot_base + s));
         tbl.push_back(tb);
     }
     lay.task_bytes = tasks.size();
@@ -362,6 +373,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
             f.zz_slots = ib + tbl[mi].zz;
             f.sx_den = ib + tbl[mi].sxd;
             f.zz_den = ib + tbl[mi].zzd;
+            f.sz_slots = ib + tbl[mi].sz;
             f.out = reinterpret_cast<double*>(base + lay.res_off) + mb.res_off;
         }
         f.J = 1.0;

@@ -100,7 +100,8 @@ struct Op {
     int level = 0;
     // absorb
     int in = -1, E = -1, out = -1, adj = -1;
-    int E2 = -1, out2 = -1;       // dual absorb-dot: second site matrix and its scalar
+    int E2 = -1, out2 = -1;       // dual / triple absorb-dot: second site matrix and its scalar
+    int E3 = -1, out3 = -1;       // triple absorb-dot: third site matrix and its scalar
     int64_t P = 0, S = 0;
     int K = 0, N = 0;
     bool transE = false;
@@ -133,6 +134,7 @@ struct Program {
     int norm_slot = -1;
     std::vector<int> sx_slot;     // per site (row-major, original lattice)
     std::vector<int> zz_slot;     // per bond (output order)
+    std::vector<int> sz_slot;     // per site: <Z_k> numerator (denominator sx_den)
     // denominator of each ratio: <F[q][t], G[q][t]> at the step where the
     // observable meets its environment (the norm along the same rounding path),
     // or norm_slot for bonds across a cut

@@ -39,10 +39,12 @@ struct AbsorbTask {
     int transE;           // 1: use E[n][k] as E[k][n] (backward / environment sweep)
     int slot_in, slot_E, slot_out, slot_adj;
     int ntiles;
-    // dual dot mode: a second site matrix on the same input and adjoint, its
-    // result in slot_out2 (partials ntiles..2 ntiles-1)
+    // dual / triple dot modes: a second (third) site matrix on the same input
+    // and adjoint, its result in slot_out2 (slot_out3); partials of the k-th
+    // result at k * ntiles
     const void* E2;
-    int slot_E2, slot_out2;
+    const void* E3;
+    int slot_E2, slot_out2, slot_E3, slot_out3;
 };
 
 struct GemmTask {
@@ -94,7 +96,8 @@ struct FinalTask {
     const int* zz_slots;  // n_bonds
     const int* sx_den;    // n_sites: slot of each ratio's denominator
     const int* zz_den;    // n_bonds
-    double* out;          // kResultHeader + n_sites + n_bonds
+    const int* sz_slots;  // n_sites: <Z_k> numerators (same denominators as sx)
+    double* out;          // kResultHeader + 2 n_sites + n_bonds: <X_k>, <Z_i Z_j>, <Z_k>
     double J, h;
     int norm_slot;
     int n_sites, n_bonds;

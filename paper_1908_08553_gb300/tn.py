@@ -20,7 +20,7 @@ TN_ERR_CUDA, TN_ERR_TIMEOUT, TN_ERR_NUMERIC, TN_ERR_NO_DEVICE = -4, -5, -6, -7
 TN_FP64, TN_FP32, TN_BF16X3, TN_BF16X6 = 0, 1, 2, 3
 TN_SCHED_AUTO, TN_SCHED_ROW, TN_SCHED_COL, TN_SCHED_QUADRANT = 0, 1, 2, 3
 TN_WORK_NORM, TN_WORK_ENERGY = 0, 1
-TN_OP_NORM, TN_OP_X, TN_OP_ZZ = 0, 1, 2
+TN_OP_NORM, TN_OP_X, TN_OP_ZZ, TN_OP_Z = 0, 1, 2, 3
 
 PRECISIONS = {"fp64": TN_FP64, "fp32": TN_FP32, "bf16x3": TN_BF16X3, "bf16x6": TN_BF16X6}
 
@@ -32,7 +32,8 @@ class tn_scalar(ctypes.Structure):
 class tn_result(ctypes.Structure):
     _fields_ = [("energy", c_double), ("energy_per_site", c_double), ("norm", tn_scalar),
                 ("sx", POINTER(c_double)), ("szsz", POINTER(c_double)), ("err_bound_est", c_double),
-                ("precision", c_int), ("schedule_o", c_int), ("schedule_i", c_int), ("schedule_j", c_int)]
+                ("precision", c_int), ("schedule_o", c_int), ("schedule_i", c_int), ("schedule_j", c_int),
+                ("sz", POINTER(c_double)), ("czz", POINTER(c_double))]
 
 
 class tn_job(ctypes.Structure):
@@ -210,6 +211,16 @@ def tn_expectation(lat, prec: int, op: int, i: int, j: int = 0) -> float:
     v = c_double()
     check(lib().tn_expectation(lat, prec, op, i, j, byref(v)), "tn_expectation")
     return v.value
+
+
+def tn_energy_full(lat, J: float, h: float, prec: int, sched: int, L: int, W: int):
+    """(tn_result, sx, szsz, sz, czz): every observable of the energy evaluation."""
+    r, sx, zz, nb = _result_arrays(L, W)
+    sz, czz = np.zeros(L * W), np.zeros(max(nb, 1))
+    r.sz = sz.ctypes.data_as(POINTER(c_double))
+    r.czz = czz.ctypes.data_as(POINTER(c_double))
+    check(lib().tn_energy_sched(lat, J, h, prec, sched, byref(r)), "tn_energy")
+    return r, sx, zz[:nb], sz, czz[:nb]
 
 
 def tn_energy(lat, J: float, h: float, prec: int = TN_FP64, sched: int = TN_SCHED_AUTO,

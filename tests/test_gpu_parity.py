@@ -176,7 +176,7 @@ def test_batch_member_equals_alone_bitwise(ctx):
     off = 0
     for k, (L, W, D) in enumerate(shapes):
         nb = L * (W - 1) + W * (L - 1)
-        seg = res[off:off + 6 + L * W + nb]
+        seg = res[off:off + 6 + 2 * L * W + nb]
         off += seg.size
         A = inputs.random_lattice(L, W, D, inputs.lattice_seed(777, k))
         b1 = tn.tn_batch_create(ctx, [L], [W], [D], tn.TN_FP32)
