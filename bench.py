@@ -200,7 +200,7 @@ def run_large(args):
             tn.tn_batch_run(b, 1.0, hs)
             torch.cuda.synchronize()
             fam = {n: tn.tn_ctx_kernel_stats(ctx, k) for k, n in
-                   enumerate(["absorb", "absorb_dot", "gemm_simt", "gemm_tc", "other"])}
+                   enumerate(["absorb", "absorb_dot", "gemm_simt", "gemm_tc", "other", "absorb_pair"])}
             tn.tn_ctx_set_profiling(ctx, False)
             r = tn.tn_batch_results_host(b)
             entry = {"ms": ms, "evals_per_s": 1000.0 / ms, "log2_norm": float(r[1])}
@@ -579,7 +579,7 @@ def main():
         step()
     torch.cuda.synchronize()
     fams = {name: tn.tn_ctx_kernel_stats(ctx, k) for k, name in
-            enumerate(["absorb", "absorb_dot", "gemm_simt", "gemm_tc", "other"])}
+            enumerate(["absorb", "absorb_dot", "gemm_simt", "gemm_tc", "other", "absorb_pair"])}
     tn.tn_ctx_set_profiling(ctx, False)
     hbm, bf16, sm_max, src = _peaks()
     bf16_sus = _peak_key("bf16_tflops_sustained", bf16)
@@ -590,7 +590,7 @@ def main():
         fd = fams[name]
         if not fd["ms"]:
             return None
-        if name in ("absorb", "absorb_dot", "other"):
+        if name in ("absorb", "absorb_dot", "other", "absorb_pair"):
             achieved = fd["bytes"] / (fd["ms"] / 1e3) / 1e9
             traffic, note = None, None
             if name == "absorb" and prec == tn.TN_FP32:

@@ -283,8 +283,10 @@ const char *tn_status_string(tn_status s);
 const char *tn_last_error(void);
 /* Per kernel family since the last reset: launches, summed device time (ms,
  * from CUDA events around each launch, only while profiling is on),
- * algorithmic bytes and multiply-adds.  family: 0 absorb, 1 absorb-dot,
- * 2 SIMT dense product, 3 tensor-core dense product, 4 other. */
+ * algorithmic bytes and multiply-adds.  family: 0 absorb (one step),
+ * 1 absorb-dot (one step, with one to three site matrices), 2 SIMT dense
+ * product, 3 tensor-core dense product, 4 other, 5 two steps of a frame row
+ * fused (with or without the final dot). */
 tn_status tn_ctx_set_profiling(tn_ctx *ctx, int on);
 tn_status tn_ctx_kernel_stats(tn_ctx *ctx, int family, int64_t *launches, double *ms,
                               double *bytes, double *macs);

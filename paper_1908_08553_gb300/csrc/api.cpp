@@ -468,7 +468,7 @@ tn_status tn_ctx_set_profiling(tn_ctx* ctx, int on) {
 }
 
 tn_status tn_ctx_kernel_stats(tn_ctx* ctx, int family, int64_t* launches, double* ms, double* bytes, double* macs) {
-    if (!ctx || family < 0 || family > 4) return TN_ERR_INVALID;
+    if (!ctx || family < 0 || family >= kFamilies) return TN_ERR_INVALID;
     std::lock_guard<std::mutex> g(ctx->mu);
     const KStat& s = ctx->stats[family];
     if (launches) *launches = s.launches;

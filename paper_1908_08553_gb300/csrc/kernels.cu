@@ -518,6 +518,142 @@ k_absorb_generic(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restr
     }
 }
 
+// ---- two consecutive steps of one frame row in one pass (FP32, D = 2) ------
+//
+// Step c maps [P][K1 = (h, u_c)][U = u_{c+1}][S2] (K1 = 4 on a frame row's
+// first column, where h has dimension 1) to [P][DN = dn_c][H = h']
+// [U][S2] with E1 (K1 x DN*H); step c+1 maps the result, read as
+// [P*DN][(h', u_{c+1})][S2], to [P*DN][N2][S2] with E2 (H*U x N2).  One thread
+// owns one (p, s2): it loads its K1*U inputs (consecutive threads take
+// consecutive s2, so every load and store is coalesced), forms the H*U
+// intermediates of one dn at a time in registers and contracts them with E2
+// at once: the intermediate boundary never reaches memory, halving the bytes
+// of the pair.  MODE 1 stores with the rescaling max (exponent of the output:
+// input + both site matrices); MODE 2 dots with an adjoint [P*DN][N2][S2].
+constexpr int kA2Threads = 128;
+
+template <int K1, int N2, int MODE>
+__global__ void __launch_bounds__(kA2Threads, MODE == 2 ? 3 : 4)
+k_absorb2(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
+    constexpr int DN = 4, H = 4, U = 4;
+    __shared__ __align__(16) float E1s[K1 * DN * H];
+    __shared__ __align__(16) float E2s[H * U * N2];
+    __shared__ double red[32];
+    const long long tile = blockIdx.x;
+    const AbsorbTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
+    const long long local = tile - t.tile0;
+    for (int i = threadIdx.x; i < K1 * DN * H; i += blockDim.x) E1s[i] = static_cast<const float*>(t.E)[i];
+    for (int i = threadIdx.x; i < H * U * N2; i += blockDim.x) E2s[i] = static_cast<const float*>(t.E2)[i];
+    const int e_in = slot_shift(&slots[t.slot_in]);
+    const float sc_in = pow2<float>(-e_in);
+    int e_adj = 0;
+    float sc_adj = 1.0f;
+    if (MODE == 2) {
+        e_adj = slot_shift(&slots[t.slot_adj]);
+        sc_adj = pow2<float>(-e_adj);
+    }
+    __syncthreads();
+    const long long S2 = t.S;
+    const long long pos = local * kA2Threads + threadIdx.x;
+    float lmax = 0.0f;
+    CSum<float> acc;
+    if (pos < t.P * S2) {
+        const long long p = pos / S2, s2 = pos - p * S2;
+        const float* in = static_cast<const float*>(t.in) + p * K1 * U * S2 + s2;
+        float x[K1][U];
+#pragma unroll
+        for (int k = 0; k < K1; ++k)
+#pragma unroll
+            for (int u = 0; u < U; ++u) x[k][u] = __ldg(in + (k * U + u) * S2) * sc_in;
+        // one dn at a time (not unrolled: keeps the live set to x, mid and y)
+#pragma unroll 1
+        for (int dn = 0; dn < DN; ++dn) {
+            float mid[H][U];
+#pragma unroll
+            for (int h = 0; h < H; ++h)
+#pragma unroll
+                for (int u = 0; u < U; ++u) mid[h][u] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < K1; ++k) {
+                const float4 e = *reinterpret_cast<const float4*>(&E1s[k * DN * H + dn * H]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    mid[0][u] = fmaf(x[k][u], e.x, mid[0][u]);
+                    mid[1][u] = fmaf(x[k][u], e.y, mid[1][u]);
+                    mid[2][u] = fmaf(x[k][u], e.z, mid[2][u]);
+                    mid[3][u] = fmaf(x[k][u], e.w, mid[3][u]);
+                }
+            }
+            float y[N2];
+#pragma unroll
+            for (int n = 0; n < N2; ++n) y[n] = 0.0f;
+#pragma unroll
+            for (int h = 0; h < H; ++h)
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float m = mid[h][u];
+                    if (N2 >= 4) {
+#pragma unroll
+                        for (int nq = 0; nq < N2 / 4; ++nq) {
+                            const float4 e = *reinterpret_cast<const float4*>(&E2s[(h * U + u) * N2 + 4 * nq]);
+                            y[4 * nq] = fmaf(m, e.x, y[4 * nq]);
+                            y[4 * nq + 1] = fmaf(m, e.y, y[4 * nq + 1]);
+                            y[4 * nq + 2] = fmaf(m, e.z, y[4 * nq + 2]);
+                            y[4 * nq + 3] = fmaf(m, e.w, y[4 * nq + 3]);
+                        }
+                    } else {
+                        y[0] = fmaf(m, E2s[h * U + u], y[0]);
+                    }
+                }
+            const long long o = (p * DN + dn) * N2 * S2 + s2;
+            if (MODE == 1) {
+                float* out = static_cast<float*>(t.out) + o;
+#pragma unroll
+                for (int n = 0; n < N2; ++n) {
+                    out[n * S2] = y[n];
+                    lmax = fmaxf(lmax, fabsf(y[n]));
+                }
+            } else {
+                // the N2 terms of this dn summed first, then compensated
+                const float* adj = static_cast<const float*>(t.adj) + o;
+                float g = 0.0f;
+#pragma unroll
+                for (int n = 0; n < N2; ++n) g = fmaf(y[n], __ldg(adj + n * S2) * sc_adj, g);
+                acc.add(g);
+            }
+        }
+    }
+    if (MODE == 1) {
+        const double m = block_max((double)lmax, red);
+        if (threadIdx.x == 0) {
+            record_max(&slots[t.slot_out], m);
+            if (local == 0)
+                slots[t.slot_out].X = slots[t.slot_in].X + e_in + slots[t.slot_E].X + slots[t.slot_E2].X;
+        }
+    } else {
+        const double part = block_sum((double)acc.value(), red);
+        const long long X =
+            slots[t.slot_in].X + e_in + slots[t.slot_E].X + slots[t.slot_E2].X + slots[t.slot_adj].X + e_adj;
+        finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_out], X, red);
+    }
+}
+
+long long absorb2_tiles(long long P, long long S2) { return (P * S2 + kA2Threads - 1) / kA2Threads; }
+
+cudaError_t launch_absorb2(bool dot, int K1, int N2, const AbsorbTask* tasks, int ntasks, long long nblocks,
+                           Slot* slots, cudaStream_t st, const int* tmap) {
+    if (nblocks <= 0) return cudaSuccess;
+#define TN_A2(KK, NN)                                                                                       \
+    if (K1 == KK && N2 == NN) {                                                                             \
+        if (dot) k_absorb2<KK, NN, 2><<<(unsigned)nblocks, kA2Threads, 0, st>>>(tasks, ntasks, slots, tmap); \
+        else k_absorb2<KK, NN, 1><<<(unsigned)nblocks, kA2Threads, 0, st>>>(tasks, ntasks, slots, tmap);     \
+        return cudaGetLastError();                                                                          \
+    }
+    TN_A2(4, 1) TN_A2(4, 4) TN_A2(4, 16) TN_A2(16, 1) TN_A2(16, 4) TN_A2(16, 16)
+#undef TN_A2
+    return cudaErrorInvalidValue;
+}
+
 long long absorb_tiles(long long P, long long S, int K, int N) {
     (void)K; (void)N;
     return (P * S + kAbsorbThreads - 1) / kAbsorbThreads;

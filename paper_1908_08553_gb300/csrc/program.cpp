@@ -136,6 +136,47 @@ public:
         return out;
     }
 
+    // Whether two consecutive steps of one frame row can run fused (FP32, D = 2:
+    // the first step 4 or 16 -> (dn, h') = 4 x 4, the second (h', u) = 4 x 4 ->
+    // N2, at least 8 trailing positions so every warp access covers whole sectors).
+    bool pair_ok(const Step& a, const Step& b) const {
+        if (pg_.dt != DT_F32 || a.corner != b.corner || a.k != b.k || b.c != a.c + 1) return false;
+        if (!(a.K == 4 || a.K == 16) || a.N != 16 || b.K != 16 || !(b.N == 1 || b.N == 4 || b.N == 16)) return false;
+        return b.P == 4 * a.P && a.S == 4 * b.S && b.S >= 8;
+    }
+
+    // absorb(absorb(in, E1), E2) for the consecutive steps a, b (pair_ok).
+    int absorb2(int in, int E1, int E2, const Step& a, const Step& b) {
+        const int level = std::max({level_of(in), level_of(E1), level_of(E2), floor_}) + 1;
+        const int out = tensor(b.n_out, level);
+        Op op;
+        op.kind = OP_ABSORB2;
+        op.level = level;
+        op.in = in; op.E = E1; op.E2 = E2; op.out = out;
+        op.P = a.P; op.S = b.S; op.K = a.K; op.N = b.N;
+        op.bytes = (double)(a.n_in + b.n_out) * pg_.esize;
+        op.macs = (double)a.mac + (double)b.mac;
+        use(in, level); use(E1, level); use(E2, level);
+        add(op);
+        return out;
+    }
+
+    // <absorb(absorb(in, E1), E2), adj> for the consecutive steps a, b (pair_ok).
+    int absorb2_dot(int in, int E1, int E2, int adj, const Step& a, const Step& b) {
+        const int level = std::max({level_of(in), level_of(E1), level_of(E2), level_of(adj), floor_}) + 1;
+        const int out = scalar(level);
+        Op op;
+        op.kind = OP_ABSORB2_DOT;
+        op.level = level;
+        op.in = in; op.E = E1; op.E2 = E2; op.adj = adj; op.out = out;
+        op.P = a.P; op.S = b.S; op.K = a.K; op.N = b.N;
+        op.bytes = (double)(a.n_in + b.n_out) * pg_.esize;
+        op.macs = (double)a.mac + (double)b.mac + (double)b.n_out;
+        use(in, level); use(E1, level); use(E2, level); use(adj, level);
+        add(op);
+        return out;
+    }
+
     // Whether the FP32 streaming absorption serves this step (it has the triple dot).
     bool dual_ok(const Step& s) const {
         const int v = absorb_variant(pg_.dt == DT_F64 ? 0 : 1, s.P, s.S, s.K, s.N);
@@ -432,11 +473,32 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
             for (int c = 0; c < W; ++c) bonds.push_back({r * W + c, (r + 1) * W + c});
         int Xl = -1, Xr = -1;
         int den_cross[4] = {-1, -1, -1, -1};
+        // Chain of corner q over steps t0..t1 from x, Z at step t0 and I after;
+        // with adj >= 0 the last step is instead an absorb-dot with Z and adj.
+        // Consecutive steps of one frame row run as fused pairs where they can.
+        auto chain = [&](int q, int x, int t0, int t1, int adj) {
+            int u = t0;
+            while (u <= t1) {
+                const int op_u = u == t0 ? PH_Z : PH_I;
+                const bool last_dot = adj >= 0 && u == t1;
+                if (u < t1 && bd.pair_ok(step_of(q, u), step_of(q, u + 1))) {
+                    const int op_v = (adj >= 0 && u + 1 == t1) ? PH_Z : PH_I;
+                    if (adj >= 0 && u + 1 == t1)
+                        return bd.absorb2_dot(x, E_at(q, u, op_u), E_at(q, u + 1, op_v), adj, step_of(q, u),
+                                              step_of(q, u + 1));
+                    x = bd.absorb2(x, E_at(q, u, op_u), E_at(q, u + 1, op_v), step_of(q, u), step_of(q, u + 1));
+                    u += 2;
+                    continue;
+                }
+                if (last_dot) return bd.absorb_dot(x, E_at(q, u, PH_Z), adj, step_of(q, u));
+                x = bd.absorb(x, E_at(q, u, op_u), step_of(q, u), false);
+                ++u;
+            }
+            return x;
+        };
         auto regrow = [&](int q, int t) {
             const int T = (int)pl.corner[q].steps.size();
-            int x = bd.absorb(F[q][t - 1], E_at(q, t, PH_Z), step_of(q, t), false);
-            for (int u = t + 1; u <= T; ++u) x = bd.absorb(x, E_at(q, u, PH_I), step_of(q, u), false);
-            return x;
+            return chain(q, F[q][t - 1], t, T, -1);
         };
         pg.zz_slot.assign(bonds.size(), -1);
         pg.zz_den.assign(bonds.size(), pg.norm_slot);
@@ -471,9 +533,7 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
                 if (a.t > b.t) std::swap(a, b);
                 const int q = a.q;
                 begin_chain(2 * max_out(q, a.t, b.t));
-                int x = bd.absorb(F[q][a.t - 1], E_at(q, a.t, PH_Z), step_of(q, a.t), false);
-                for (int u = a.t + 1; u < b.t; ++u) x = bd.absorb(x, E_at(q, u, PH_I), step_of(q, u), false);
-                v = bd.absorb_dot(x, E_at(q, b.t, PH_Z), G[q][b.t], step_of(q, b.t));
+                v = chain(q, F[q][a.t - 1], a.t, b.t, G[q][b.t]);
                 end_chain(v);
                 pg.zz_den[bi] = norm_at(q, b.t);
             } else {

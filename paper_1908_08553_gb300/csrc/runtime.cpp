@@ -32,6 +32,7 @@ int family_of(int kind) {
     switch (kind) {
         case OP_ABSORB: return FAM_ABSORB;
         case OP_ABSORB_DOT: return FAM_ABSORB_DOT;
+        case OP_ABSORB2: case OP_ABSORB2_DOT: return FAM_PAIR;
         case OP_TC_SPLIT: return FAM_OTHER;
         case OP_GEMM: case OP_GEMM_DOT: return FAM_GEMM;
         case OP_TC_GEMM: case OP_TC_GEMM_DOT: return FAM_TC;
@@ -87,6 +88,8 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 var = op.nsplit ? 1 + op.nsplit : absorb_variant(b->dt, op.P, op.S, op.K, op.N);
                 if (op.E3 >= 0) var += 20;
                 else if (op.E2 >= 0) var += 10;
+            } else if (op.kind == OP_ABSORB2 || op.kind == OP_ABSORB2_DOT) {
+                K = op.K; N = op.N;
             } else if (op.kind == OP_GEMM || op.kind == OP_GEMM_DOT) {
                 var = gemm_variant(b->dt, op.gm, op.gn, op.gk, op.sam, op.sak, op.sbk, op.sbn);
             } else if (op.kind == OP_TC_GEMM || op.kind == OP_TC_GEMM_DOT) {
@@ -132,6 +135,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 npart += gemm_tiles_v(var, op.gm, op.gn, &tn_) * gemm_ksplit(var, true, op.gk);
             }
             else if (kind == OP_DOT) npart += (op.gm + kDotPerBlock - 1) / kDotPerBlock;
+            else if (kind == OP_ABSORB2_DOT) npart += absorb2_tiles(op.P, op.S);
             else if (kind == OP_TC_GEMM_DOT) {
                 const int bn = std::get<4>(kv.first) % 1000;
                 npart += ((op.gm + 127) / 128) * ((op.gn + bn - 1) / bn) * ((op.Kp + kGemmKSlice - 1) / kGemmKSlice);
@@ -217,6 +221,28 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                         t.slot_E3 = slot_of(r.member, op.E3);
                         t.slot_out3 = slot_of(r.member, op.out3);
                     }
+                } else {
+                    t.out = tensor_ptr(r.member, op.out);
+                }
+                off = append(&t, sizeof(t));
+                tile += nt;
+            } else if (kind == OP_ABSORB2 || kind == OP_ABSORB2_DOT) {
+                AbsorbTask t{};
+                t.in = tensor_ptr(r.member, op.in);
+                t.E = tensor_ptr(r.member, op.E);
+                t.E2 = tensor_ptr(r.member, op.E2);
+                t.P = op.P; t.S = op.S; t.K = op.K; t.N = op.N;
+                t.slot_in = slot_of(r.member, op.in);
+                t.slot_E = slot_of(r.member, op.E);
+                t.slot_E2 = slot_of(r.member, op.E2);
+                t.slot_out = slot_of(r.member, op.out);
+                t.tile0 = tile;
+                const long long nt = absorb2_tiles(op.P, op.S);
+                t.ntiles = (int)nt;
+                if (kind == OP_ABSORB2_DOT) {
+                    t.adj = tensor_ptr(r.member, op.adj);
+                    t.slot_adj = slot_of(r.member, op.adj);
+                    t.partial = take_partial(nt);
                 } else {
                     t.out = tensor_ptr(r.member, op.out);
                 }
@@ -313,8 +339,8 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         L.nblocks = tile;
         // block -> task table for launches of many short blocks (saves each
         // block a dependent binary search over the task list)
-        const bool mapped =
-            ((kind == OP_ABSORB || kind == OP_ABSORB_DOT) && (L.variant <= 2 || L.variant >= 10)) || kind == OP_DOT;
+        const bool mapped = ((kind == OP_ABSORB || kind == OP_ABSORB_DOT) && (L.variant <= 2 || L.variant >= 10)) ||
+                            kind == OP_DOT || kind == OP_ABSORB2 || kind == OP_ABSORB2_DOT;
         if (mapped && L.ntasks > 8) {
             tasks.resize((tasks.size() + 15) / 16 * 16);
             L.map_off = tasks.size();
@@ -532,6 +558,11 @@ cudaError_t issue(tn_batch* b, cudaStream_t st, std::vector<std::pair<cudaEvent_
             case OP_GEMM_DOT:
                 e = launch_gemm(L.dt, L.kind == OP_GEMM_DOT, static_cast<const GemmTask*>(tp), L.ntasks,
                                 L.nblocks, slots, st, L.variant);
+                break;
+            case OP_ABSORB2:
+            case OP_ABSORB2_DOT:
+                e = launch_absorb2(L.kind == OP_ABSORB2_DOT, L.K, L.N, static_cast<const AbsorbTask*>(tp), L.ntasks,
+                                   L.nblocks, slots, st, tmap);
                 break;
             case OP_DOT:
                 e = launch_dot(L.dt, static_cast<const DotTask*>(tp), L.ntasks, L.nblocks, slots, st, tmap);

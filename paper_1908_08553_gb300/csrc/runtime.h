@@ -17,7 +17,8 @@ namespace tn {
 
 void set_error(const std::string& msg);
 
-enum Family { FAM_ABSORB = 0, FAM_ABSORB_DOT = 1, FAM_GEMM = 2, FAM_TC = 3, FAM_OTHER = 4 };
+enum Family { FAM_ABSORB = 0, FAM_ABSORB_DOT = 1, FAM_GEMM = 2, FAM_TC = 3, FAM_OTHER = 4, FAM_PAIR = 5 };
+constexpr int kFamilies = 6;
 
 struct KStat {
     int64_t launches = 0;
@@ -65,7 +66,7 @@ struct tn_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     bool profiling = false;
-    tn::KStat stats[5];
+    tn::KStat stats[tn::kFamilies];
     std::mutex mu;          // guards stats and the server
     tn::Server* server = nullptr;
 };

@@ -79,6 +79,8 @@ enum OpKind {
     OP_TC_SPLIT,      // FP32 operand -> tiled BF16 planes (tensor-core input)
     OP_TC_GEMM,       // C = A B^T on tensor cores from split planes
     OP_TC_GEMM_DOT,   // scalar = <A B^T, C> on tensor cores
+    OP_ABSORB2,       // out = absorb(absorb(in, E), E2): two steps of one frame row
+    OP_ABSORB2_DOT,   // scalar = <absorb(absorb(in, E), E2), adj>
 };
 
 // Operator insertion on the physical leg.

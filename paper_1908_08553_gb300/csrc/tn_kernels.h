@@ -146,6 +146,13 @@ cudaError_t launch_absorb(int dt, bool dot, int K, int N, const AbsorbTask* task
                           const int* tmap = nullptr);
 int absorb_variant(int dt, long long P, long long S, int K, int N);
 long long absorb_tiles_v(int variant, long long P, long long S, int K, int N);
+// Two consecutive steps of one frame row fused (FP32, D = 2: K1 in {4, 16},
+// dn, h', u_{c+1} of dimension 4; N2 in {1, 4, 16}): tasks use P = P of the
+// first step, S = S of the second, K = K1, N = N2, E = first site matrix,
+// E2 = second.
+long long absorb2_tiles(long long P, long long S2);
+cudaError_t launch_absorb2(bool dot, int K1, int N2, const AbsorbTask* tasks, int ntasks, long long nblocks,
+                           Slot* slots, cudaStream_t st, const int* tmap = nullptr);
 // variant 0: 64x64 tiles, any dtype; 1: FP32 128x128 double-buffered with
 // 16-byte loads; 2: the same with scalar loads (odd extents, e.g. D = 3).
 cudaError_t launch_gemm(int dt, bool dot, const GemmTask* tasks, int ntasks, long long nblocks,
