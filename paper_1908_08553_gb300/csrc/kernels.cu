@@ -1023,8 +1023,23 @@ k_gemm2(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots
 // Full tiles (M and N multiples of 128, the k range a multiple of 8, operands
 // with a unit-stride axis and 16-byte aligned rows): the same 128 x 128 scheme
 // with the operand layouts as template parameters, one pointer increment per
-// k slice instead of per-load index arithmetic, and no bounds tests.
+// k slice instead of per-load index arithmetic, no bounds tests, and the
+// 8 x 8 register tile updated with paired FMAs (fma.rn.f32x2: a column pair
+// of accumulators per instruction, the A value duplicated into both lanes).
 // AK: A contiguous along k (else along m); BNC: B contiguous along n (else k).
+// Paired FP32 FMA (Blackwell f32x2): two independent lanes per instruction.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ void f2_fma(unsigned long long& acc, unsigned long long a, unsigned long long b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
 template <bool DOT, bool AK, bool BNC>
 __global__ void __launch_bounds__(256, 2)
 k_gemm3(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
@@ -1065,11 +1080,12 @@ k_gemm3(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots
             Bs[buf][b_kk + 2][b_nn] = rb.z * sB; Bs[buf][b_kk + 3][b_nn] = rb.w * sB;
         }
     };
-    float acc[8][8];
+    // accumulators in column pairs: acc2[i][q] = (C[i][2q], C[i][2q+1])
+    unsigned long long acc2[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+        for (int q = 0; q < 4; ++q) acc2[i][q] = 0ull;
     const int nk = (int)((kend - kbeg) / kG2K);
     store(0);
     __syncthreads();
@@ -1086,18 +1102,25 @@ k_gemm3(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots
         for (int kk = 0; kk < kG2K; ++kk) {
             const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][4 * ty]);
             const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + 4 * ty]);
-            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][4 * tx]);
-            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + 4 * tx]);
+            const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(&Bs[cur][kk][4 * tx]);
+            const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(&Bs[cur][kk][64 + 4 * tx]);
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            const unsigned long long b[4] = {b0.x, b0.y, b1.x, b1.y};
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 8; ++i) {
+                const unsigned long long ai = f2_pack(a[i], a[i]);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int q = 0; q < 4; ++q) f2_fma(acc2[i][q], ai, b[q]);
+            }
         }
         if (more) store(cur ^ 1);
         __syncthreads();
     }
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f2_unpack(acc2[i][q], acc[i][2 * q], acc[i][2 * q + 1]);
     auto row = [&](int i) { return m0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + (i - 4)); };
     const long long c0 = n0 + 4 * tx, c1 = n0 + 64 + 4 * tx;
     if (!DOT) {
