@@ -99,6 +99,19 @@ struct CSum<double> {
     __device__ __forceinline__ double value() const { return s; }
 };
 
+// Paired FP32 FMA (Blackwell f32x2): two independent lanes per instruction.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ void f2_fma(unsigned long long& acc, unsigned long long a, unsigned long long b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
 __device__ __forceinline__ void record_max(Slot* s, double m) {
     atomicMax(&s->maxbits, (unsigned long long)__double_as_longlong(m));
 }
@@ -239,9 +252,13 @@ constexpr int kV2Threads = 128;
 template <int K, int N, int MODE, bool ALONG_P>
 __global__ void __launch_bounds__(kV2Threads, MODE >= 4 ? 3 : 4)
 k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
-    __shared__ __align__(16) float Es[K * N];
-    __shared__ __align__(16) float Es2[MODE >= 4 ? K * N : 4];
-    __shared__ __align__(16) float Es3[MODE == 5 ? K * N : 4];
+    constexpr int NE = MODE == 5 ? 3 : (MODE == 4 ? 2 : 1);     // site matrices
+    // along s the 4 outer positions are paired into two-lane FMAs; the site
+    // matrices then live in shared memory as duplicated (e, e) pairs
+    __shared__ __align__(16) float Es[ALONG_P ? K * N : 4];
+    __shared__ __align__(16) float Es2[ALONG_P && MODE >= 4 ? K * N : 4];
+    __shared__ __align__(16) float Es3[ALONG_P && MODE == 5 ? K * N : 4];
+    __shared__ __align__(16) unsigned long long Ed[ALONG_P ? 2 : NE * K * N];
     __shared__ double red[32];
     const long long tile = blockIdx.x;
     const AbsorbTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
@@ -249,9 +266,18 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
     const float* E = static_cast<const float*>(t.E);
     for (int idx = threadIdx.x; idx < K * N; idx += blockDim.x) {
         const int k = idx / N, n = idx - k * N;
-        Es[idx] = t.transE ? E[n * K + k] : E[idx];
-        if (MODE >= 4) Es2[idx] = static_cast<const float*>(t.E2)[idx];
-        if (MODE == 5) Es3[idx] = static_cast<const float*>(t.E3)[idx];
+        const float e1 = t.transE ? E[n * K + k] : E[idx];
+        const float e2 = MODE >= 4 ? static_cast<const float*>(t.E2)[idx] : 0.0f;
+        const float e3 = MODE == 5 ? static_cast<const float*>(t.E3)[idx] : 0.0f;
+        if (ALONG_P) {
+            Es[idx] = e1;
+            if (MODE >= 4) Es2[idx] = e2;
+            if (MODE == 5) Es3[idx] = e3;
+        } else {
+            Ed[idx] = f2_pack(e1, e1);
+            if (MODE >= 4) Ed[K * N + idx] = f2_pack(e2, e2);
+            if (MODE == 5) Ed[2 * K * N + idx] = f2_pack(e3, e3);
+        }
     }
     const int e_in = slot_shift(&slots[t.slot_in]);
     const float sc_in = pow2<float>(-e_in);
@@ -267,7 +293,118 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
     const long long g = local * kV2Threads + threadIdx.x;
     float lmax = 0.0f;
     double ldot = 0.0, ldot2 = 0.0, ldot3 = 0.0;
-    if (g < ngroups) {
+    if (g < ngroups && !ALONG_P) {
+        // ---- 4 consecutive s of one p, two-lane FMAs over position pairs
+        const long long sq = S / 4, p = g / sq, s = (g - p * sq) * 4;
+        const float* in = static_cast<const float*>(t.in);
+        unsigned long long xv[K][2];     // (x_0, x_1), (x_2, x_3) per k, rescaled
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(in + (p * K + k) * S + s));
+            xv[k][0] = f2_pack(v.x * sc_in, v.y * sc_in);
+            xv[k][1] = f2_pack(v.z * sc_in, v.w * sc_in);
+        }
+        if (MODE >= 4) {
+            // dual / triple dot: 4 outputs n at a time for every site matrix
+            const float* adj = static_cast<const float*>(t.adj);
+            CSum<float> acc[NE];
+#pragma unroll
+            for (int nq = 0; nq < (N + 3) / 4; ++nq) {
+                constexpr int NW = N >= 4 ? 4 : 1;
+                unsigned long long z[NE][2][NW];
+#pragma unroll
+                for (int q = 0; q < NE; ++q)
+#pragma unroll
+                    for (int vp = 0; vp < 2; ++vp)
+#pragma unroll
+                        for (int j = 0; j < NW; ++j) z[q][vp][j] = 0ull;
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+#pragma unroll
+                    for (int q = 0; q < NE; ++q) {
+                        unsigned long long e[NW];
+                        if (NW == 4) {
+                            const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(&Ed[q * K * N + k * N + 4 * nq]);
+                            const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(&Ed[q * K * N + k * N + 4 * nq + 2]);
+                            e[0] = a.x; e[1] = a.y; e[2] = b.x; e[3] = b.y;
+                        } else {
+                            e[0] = Ed[q * K * N + k];
+                        }
+#pragma unroll
+                        for (int vp = 0; vp < 2; ++vp)
+#pragma unroll
+                            for (int j = 0; j < NW; ++j) f2_fma(z[q][vp][j], xv[k][vp], e[j]);
+                    }
+#pragma unroll
+                for (int j = 0; j < NW; ++j) {
+                    const float4 w = __ldg(reinterpret_cast<const float4*>(adj + (p * N + NW * nq + j) * S + s));
+#pragma unroll
+                    for (int q = 0; q < NE; ++q) {
+                        float z0, z1, z2, z3;
+                        f2_unpack(z[q][0][j], z0, z1);
+                        f2_unpack(z[q][1][j], z2, z3);
+                        // the 4 outer positions of this column summed first, then compensated
+                        float gq = z0 * (w.x * sc_adj);
+                        gq = fmaf(z1, w.y * sc_adj, gq);
+                        gq = fmaf(z2, w.z * sc_adj, gq);
+                        gq = fmaf(z3, w.w * sc_adj, gq);
+                        acc[q].add(gq);
+                    }
+                }
+            }
+            ldot = (double)acc[0].value();
+            if (NE >= 2) ldot2 = (double)acc[NE >= 2 ? 1 : 0].value();
+            if (NE == 3) ldot3 = (double)acc[NE - 1].value();
+        } else {
+            constexpr int NC = N >= 8 ? 8 : N;      // output columns per pass
+            CSum<float> acc;
+#pragma unroll
+            for (int h = 0; h < N / NC; ++h) {
+                unsigned long long y[2][NC];
+#pragma unroll
+                for (int vp = 0; vp < 2; ++vp)
+#pragma unroll
+                    for (int j = 0; j < NC; ++j) y[vp][j] = 0ull;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    unsigned long long e[NC];
+                    if (NC >= 2) {
+#pragma unroll
+                        for (int jq = 0; jq < NC / 2; ++jq) {
+                            const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(&Ed[k * N + h * NC + 2 * jq]);
+                            e[2 * jq] = a.x; e[2 * jq + 1] = a.y;
+                        }
+                    } else {
+                        e[0] = Ed[k * N + h * NC];
+                    }
+#pragma unroll
+                    for (int vp = 0; vp < 2; ++vp)
+#pragma unroll
+                        for (int j = 0; j < NC; ++j) f2_fma(y[vp][j], xv[k][vp], e[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < NC; ++j) {
+                    float y0, y1, y2, y3;
+                    f2_unpack(y[0][j], y0, y1);
+                    f2_unpack(y[1][j], y2, y3);
+                    if (MODE == 1) {
+                        *reinterpret_cast<float4*>(static_cast<float*>(t.out) + (p * N + h * NC + j) * S + s) =
+                            make_float4(y0, y1, y2, y3);
+                        lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(y0), fabsf(y1)), fmaxf(fabsf(y2), fabsf(y3))));
+                    } else {
+                        const float4 a = __ldg(reinterpret_cast<const float4*>(
+                            static_cast<const float*>(t.adj) + (p * N + h * NC + j) * S + s));
+                        float gq = y0 * (a.x * sc_adj);
+                        gq = fmaf(y1, a.y * sc_adj, gq);
+                        gq = fmaf(y2, a.z * sc_adj, gq);
+                        gq = fmaf(y3, a.w * sc_adj, gq);
+                        acc.add(gq);
+                    }
+                }
+            }
+            if (MODE == 2) ldot = (double)acc.value();
+        }
+    } else if (g < ngroups) {
         long long p, s;
         if (ALONG_P) { p = 4 * g; s = 0; }
         else { const long long sq = S / 4; p = g / sq; s = (g - p * sq) * 4; }
@@ -536,13 +673,19 @@ template <int K1, int N2, int MODE>
 __global__ void __launch_bounds__(kA2Threads, MODE == 2 ? 3 : 4)
 k_absorb2(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
     constexpr int DN = 4, H = 4, U = 4;
+    constexpr bool PAIRED = N2 >= 4;     // paired FMAs (fma.rn.f32x2) for N2 in {4, 16}
     __shared__ __align__(16) float E1s[K1 * DN * H];
+    __shared__ __align__(16) unsigned long long E1d[PAIRED ? K1 * DN * H : 2];   // (e, e) pairs
     __shared__ __align__(16) float E2s[H * U * N2];
     __shared__ double red[32];
     const long long tile = blockIdx.x;
     const AbsorbTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
     const long long local = tile - t.tile0;
-    for (int i = threadIdx.x; i < K1 * DN * H; i += blockDim.x) E1s[i] = static_cast<const float*>(t.E)[i];
+    for (int i = threadIdx.x; i < K1 * DN * H; i += blockDim.x) {
+        const float e = static_cast<const float*>(t.E)[i];
+        E1s[i] = e;
+        if (PAIRED) E1d[i] = f2_pack(e, e);
+    }
     for (int i = threadIdx.x; i < H * U * N2; i += blockDim.x) E2s[i] = static_cast<const float*>(t.E2)[i];
     const int e_in = slot_shift(&slots[t.slot_in]);
     const float sc_in = pow2<float>(-e_in);
@@ -565,6 +708,74 @@ k_absorb2(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
         for (int k = 0; k < K1; ++k)
 #pragma unroll
             for (int u = 0; u < U; ++u) x[k][u] = __ldg(in + (k * U + u) * S2) * sc_in;
+        if (PAIRED) {
+            // the same contraction order with two lanes per FMA: step 1 pairs
+            // adjacent u (E1 entries duplicated in shared memory), step 2 pairs
+            // adjacent outputs n (the intermediate duplicated into both lanes)
+            unsigned long long x2[K1][U / 2];
+#pragma unroll
+            for (int k = 0; k < K1; ++k)
+#pragma unroll
+                for (int up = 0; up < U / 2; ++up) x2[k][up] = f2_pack(x[k][2 * up], x[k][2 * up + 1]);
+#pragma unroll 1
+            for (int dn = 0; dn < DN; ++dn) {
+                unsigned long long mid2[H][U / 2];
+#pragma unroll
+                for (int h = 0; h < H; ++h)
+#pragma unroll
+                    for (int up = 0; up < U / 2; ++up) mid2[h][up] = 0ull;
+#pragma unroll
+                for (int k = 0; k < K1; ++k) {
+                    const ulonglong2 e01 = *reinterpret_cast<const ulonglong2*>(&E1d[k * DN * H + dn * H]);
+                    const ulonglong2 e23 = *reinterpret_cast<const ulonglong2*>(&E1d[k * DN * H + dn * H + 2]);
+                    const unsigned long long e[H] = {e01.x, e01.y, e23.x, e23.y};
+#pragma unroll
+                    for (int h = 0; h < H; ++h)
+#pragma unroll
+                        for (int up = 0; up < U / 2; ++up) f2_fma(mid2[h][up], e[h], x2[k][up]);
+                }
+                constexpr int NP = N2 >= 2 ? N2 / 2 : 1;
+                unsigned long long y2[NP];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) y2[q] = 0ull;
+#pragma unroll
+                for (int h = 0; h < H; ++h)
+#pragma unroll
+                    for (int up = 0; up < U / 2; ++up) {
+                        float m0, m1;
+                        f2_unpack(mid2[h][up], m0, m1);
+                        const unsigned long long mm[2] = {f2_pack(m0, m0), f2_pack(m1, m1)};
+#pragma unroll
+                        for (int uu = 0; uu < 2; ++uu) {
+                            const int u = 2 * up + uu;
+#pragma unroll
+                            for (int nq = 0; nq < N2 / 4; ++nq) {
+                                const ulonglong2 e = *reinterpret_cast<const ulonglong2*>(&E2s[(h * U + u) * N2 + 4 * nq]);
+                                f2_fma(y2[2 * nq], mm[uu], e.x);
+                                f2_fma(y2[2 * nq + 1], mm[uu], e.y);
+                            }
+                        }
+                    }
+                float y[2 * NP];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) f2_unpack(y2[q], y[2 * q], y[2 * q + 1]);
+                const long long o = (p * DN + dn) * N2 * S2 + s2;
+                if (MODE == 1) {
+                    float* out = static_cast<float*>(t.out) + o;
+#pragma unroll
+                    for (int n = 0; n < N2; ++n) {
+                        out[n * S2] = y[n];
+                        lmax = fmaxf(lmax, fabsf(y[n]));
+                    }
+                } else {
+                    const float* adj = static_cast<const float*>(t.adj) + o;
+                    float g = 0.0f;
+#pragma unroll
+                    for (int n = 0; n < N2; ++n) g = fmaf(y[n], __ldg(adj + n * S2) * sc_adj, g);
+                    acc.add(g);
+                }
+            }
+        } else {
         // one dn at a time (not unrolled: keeps the live set to x, mid and y)
 #pragma unroll 1
         for (int dn = 0; dn < DN; ++dn) {
@@ -621,6 +832,7 @@ k_absorb2(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
                 for (int n = 0; n < N2; ++n) g = fmaf(y[n], __ldg(adj + n * S2) * sc_adj, g);
                 acc.add(g);
             }
+        }
         }
     }
     if (MODE == 1) {
@@ -1027,19 +1239,6 @@ k_gemm2(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots
 // 8 x 8 register tile updated with paired FMAs (fma.rn.f32x2: a column pair
 // of accumulators per instruction, the A value duplicated into both lanes).
 // AK: A contiguous along k (else along m); BNC: B contiguous along n (else k).
-// Paired FP32 FMA (Blackwell f32x2): two independent lanes per instruction.
-__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ void f2_fma(unsigned long long& acc, unsigned long long a, unsigned long long b) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
-}
-
 template <bool DOT, bool AK, bool BNC>
 __global__ void __launch_bounds__(256, 2)
 k_gemm3(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
