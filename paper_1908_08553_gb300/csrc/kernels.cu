@@ -1150,11 +1150,12 @@ k_gemm2(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots
             for (int i = 0; i < 4; ++i) Bs[buf][b_kk + i][b_nn] = rb[i] * sB;
         }
     };
-    float acc[8][8];
+    // accumulators in column pairs, updated with two-lane FMAs (fma.rn.f32x2)
+    unsigned long long acc2[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+        for (int q = 0; q < 4; ++q) acc2[i][q] = 0ull;
     const long long nk = (kend - kbeg + kG2K - 1) / kG2K;
     load_a(kbeg);
     load_b(kbeg);
@@ -1167,18 +1168,25 @@ k_gemm2(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots
         for (int kk = 0; kk < kG2K; ++kk) {
             const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][4 * ty]);
             const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + 4 * ty]);
-            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][4 * tx]);
-            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + 4 * tx]);
+            const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(&Bs[cur][kk][4 * tx]);
+            const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(&Bs[cur][kk][64 + 4 * tx]);
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            const unsigned long long b[4] = {b0.x, b0.y, b1.x, b1.y};
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 8; ++i) {
+                const unsigned long long ai = f2_pack(a[i], a[i]);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int q = 0; q < 4; ++q) f2_fma(acc2[i][q], ai, b[q]);
+            }
         }
         if (kt + 1 < nk) store(cur ^ 1);
         __syncthreads();
     }
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f2_unpack(acc2[i][q], acc[i][2 * q], acc[i][2 * q + 1]);
     auto row = [&](int i) { return m0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + (i - 4)); };
     auto col = [&](int j) { return n0 + (j < 4 ? 4 * tx + j : 64 + 4 * tx + (j - 4)); };
     if (!DOT) {
