@@ -1,7 +1,9 @@
 // CUDA kernels of libtn (sm_103a): site absorption (Sec. 4's pairwise
 // contraction of one site into the boundary, the paper's `contract tVtl par`,
-// Sec. 7), dense ring products, dot products, site-matrix construction and the
-// final FP64 ratios.
+// Sec. 7) one step at a time or two steps of a frame row fused, dense ring
+// products, dot products, site-matrix construction and the final FP64 ratios.
+// The FP32 hot loops use Blackwell's two-lane FMA (fma.rn.f32x2); each lane
+// rounds exactly as fmaf, so pairing never changes a result.
 //
 // Every kernel takes a list of independent tasks; block b serves the task whose
 // [tile0, tile0 + ntiles) holds b.  Rescaling: a consumer multiplies each loaded
@@ -244,9 +246,13 @@ k_absorb_one(const __grid_constant__ AbsorbTask t) {
 // Each thread owns a group of 4 outer positions: 4 consecutive s of one p when
 // S % 4 == 0 (ALONG_P = false), or 4 consecutive p when S == 1 (ALONG_P =
 // true).  All K input vectors of the group are loaded (16-byte loads) before
-// the first FMA, so a thread has K loads in flight; E rows are read from
-// shared memory as 16-byte broadcasts, one per 16 FMAs; outputs leave as
-// 16-byte stores.  128 threads per block, 512 outer positions per tile.
+// the first FMA, so a thread has K loads in flight, and rescaled once; outputs
+// leave as 16-byte stores.  Along s the four positions form two lane pairs of
+// fma.rn.f32x2, the site matrices sit in shared memory as duplicated (e, e)
+// pairs read as 16-byte broadcasts, and outputs are formed 8 columns at a
+// time (store and single dot) or 4 at a time for every site matrix (dual and
+// triple dots: MODES 4 and 5).  Along p (S == 1) the same work runs on plain
+// FMAs.  128 threads per block, 512 outer positions per tile.
 constexpr int kV2Threads = 128;
 
 template <int K, int N, int MODE, bool ALONG_P>
