@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 L_, W_, D_ = 8, 8, 2
 H_FIELDS = (2.0, 3.04, 4.0)
 METRIC = "exact LxL Ising-PEPS energy evals/s"
-ABSORB_DRAM_PER_BYTE = 1023.75 / 1207.96   # k_absorb4<16,16,1,0> capture, profiles/k_absorb4_8x8_d2_batch64.md
+ABSORB_DRAM_PER_BYTE = 89.35 / 134.22      # k_absorb4<16,16,1,0> capture, profiles/k_absorb4_8x8_d2_batch64.md
 WORKLOAD = "8x8 open-boundary TFIM PEPS, D=2, E at h in {2.0, 3.04, 4.0}"
 
 
@@ -595,8 +595,8 @@ def main():
             traffic, note = None, None
             if name == "absorb" and prec == tn.TN_FP32:
                 # DRAM bytes per algorithmic byte of the interior FP32 absorption,
-                # from one ncu capture (8x8 D=2, 64 lattices: 1024 MB of DRAM
-                # traffic for 1208 MB in + out), applied to this run's average launch
+                # from one ncu capture (8x8 D=2, 64 lattices: 89.4 MB of DRAM
+                # traffic for 134.2 MB in + out), applied to this run's average launch
                 traffic = ABSORB_DRAM_PER_BYTE * fd["bytes"] / fd["launches"]
                 note = "ncu dram bytes/algorithmic bytes of one interior launch x mean bytes per launch"
             r = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
