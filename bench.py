@@ -110,6 +110,27 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
+    """The largest of every rank's x (the job's time is its slowest replica)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws: int, units_per_rank: int, steps: int, t_max: float) -> float:
+    """Whole-job throughput: the units all replicas processed over the slowest time."""
+    return ws * units_per_rank * steps / t_max
+
+
+def replica_seed(rank: int) -> int:
+    """Batch seed of a rank's replica: every rank contracts its own lattices."""
+    return 4242 + rank
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -511,7 +532,8 @@ def main():
     b = tn.tn_batch_create(ctx, [L_] * B, [W_] * B, [D_] * B, prec)
     n_in = tn.tn_batch_elems(b)
     host_in = torch.empty(n_in, dtype=torch.float64).pin_memory()
-    A = np.concatenate([inputs.random_lattice(L_, W_, D_, inputs.lattice_seed(4242 + rank, k)) for k in range(B)])
+    A = np.concatenate([inputs.random_lattice(L_, W_, D_, inputs.lattice_seed(replica_seed(rank), k))
+                        for k in range(B)])
     host_in.numpy()[:] = A
     n_res = tn.tn_batch_result_size(b)
     host_out = torch.empty(n_res, dtype=torch.float64).pin_memory()
@@ -544,12 +566,8 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     ms = [a.elapsed_time(e) for a, e in ev]
-    t_total = sum(ms) / 1000.0
-    if ws > 1:
-        t = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(t.item())
-    value = ws * B * args.steps / t_total
+    t_total = max_over_ranks(sum(ms) / 1000.0, ws)
+    value = job_rate(ws, B, args.steps, t_total)
     res = tn.tn_batch_results_host(b)
 
     # ---- end to end through the C-ABI with host buffers
@@ -565,12 +583,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         e2e_step()
-    t_e2e = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": ws * B * args.steps / t_e2e, "unit": "lattice evals/s",
+    t_e2e = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e = {"value": job_rate(ws, B, args.steps, t_e2e), "unit": "lattice evals/s",
            "h2d_bytes_per_step": int(n_in * 8), "d2h_bytes_per_step": int(n_res * 8)}
 
     # ---- per-kernel-family time with CUDA events around every launch (separate pass)
