@@ -110,6 +110,38 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def absorb_stream_roofline(ctx, stream, hbm: float, src: str) -> dict:
+    """The single-step absorption kernel on single tasks larger than L2: the
+    forced row scheme of one 12x12 D=2 norm (interior steps of 268 MB in and
+    268 MB out), timed per launch with CUDA events after two warm-up runs."""
+    import numpy as np
+    import torch
+
+    from paper_1908_08553_gb300 import inputs, tn
+    L, W, D = 12, 12, 2
+    b = tn.tn_batch_create(ctx, [L], [W], [D], tn.TN_FP32, tn.TN_SCHED_ROW, tn.TN_WORK_NORM)
+    try:
+        tn.tn_batch_set_tensors(b, inputs.random_lattice(L, W, D, 1214))
+        hs = np.array([3.04])
+        for _ in range(2):
+            tn.tn_batch_run(b, 1.0, hs)
+        torch.cuda.synchronize()
+        tn.tn_ctx_set_profiling(ctx, True)
+        for _ in range(3):
+            tn.tn_batch_run(b, 1.0, hs)
+        torch.cuda.synchronize()
+        a = tn.tn_ctx_kernel_stats(ctx, 0)
+        tn.tn_ctx_set_profiling(ctx, False)
+    finally:
+        tn.tn_batch_destroy(b)
+    achieved = a["bytes"] / (a["ms"] / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "kernel": "absorb (k_absorb4, single step)",
+            "workload": "12x12 D=2 norm, forced row scheme, FP32 (steps of 268 MB in + 268 MB out)",
+            "launches": a["launches"] / 3, "ms_per_run": a["ms"] / 3,
+            "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs (of {src})"}
+
+
 def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
     """The largest of every rank's x (the job's time is its slowest replica)."""
     if ws <= 1:
@@ -678,6 +710,7 @@ def main():
             line["fp64_gpu"] = {"value": B / t64, "unit": "lattice evals/s",
                                 "max_rel_energy_err_vs_fp64": rel}
             tn.tn_batch_destroy(b64)
+        line["roofline_absorb_stream"] = absorb_stream_roofline(ctx, stream, hbm, src)
         line["cpu_baseline"] = cpu_baseline(args.cpu_lattices, 4242)
     tn.tn_batch_destroy(b)
     tn.tn_ctx_destroy(ctx)
