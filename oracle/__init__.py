@@ -52,6 +52,8 @@ def lib():
         _lib.or_peps_expect_one.argtypes = [i32, i32, i32, P, i32, i32, i32, P, P, P]
         _lib.or_ising_enumerate.argtypes = [i32, i32, d, P, P, P]
         _lib.or_peps_sz.argtypes = [i32, i32, i32, P, P]
+        _lib.or_peps_bond_ops.argtypes = [i32, i32, i32, P, i32, i32, P]
+        _lib.or_peps_bond_ops.restype = i32
         for f in (_lib.or_grid_contract, _lib.or_peps_norm, _lib.or_peps_norm_all_cuts,
                   _lib.or_peps_observables, _lib.or_peps_energy, _lib.or_peps_expect_one,
                   _lib.or_ising_enumerate, _lib.or_num_threads, _lib.or_peps_sz):
@@ -135,6 +137,17 @@ def observables(L: int, W: int, D: int, A: np.ndarray, with_z: bool = False) -> 
         sz = np.zeros(L * W)
         lib().or_peps_sz(L, W, D, _ptr(A), _ptr(sz))
     return Observables(float(m[0]), int(e[0]), sx, szsz[:nb], sz)
+
+
+def bond_correlators(L: int, W: int, D: int, A: np.ndarray, op_a: str, op_b: str) -> np.ndarray:
+    """<A_i B_j> on every nearest-neighbour bond (szsz order, i the left or upper
+    site), A and B in {'x', 'z'}."""
+    A = _check_sites(L, W, D, A)
+    nb = L * (W - 1) + W * (L - 1)
+    out = np.zeros(max(nb, 1))
+    code = {"x": 1, "z": 2}
+    lib().or_peps_bond_ops(L, W, D, _ptr(A), code[op_a], code[op_b], _ptr(out))
+    return out[:nb]
 
 
 def expect_one(L: int, W: int, D: int, A: np.ndarray, op: str, i: int = 0, j: int = 0):

@@ -84,6 +84,25 @@ def sz(L: int, W: int, D: int, flat: np.ndarray) -> np.ndarray:
     return np.array([float(np.sum(w * np.where((idx >> k) & 1, 1.0, -1.0))) for k in range(L * W)]) / float(w.sum())
 
 
+def bond_correlators(L: int, W: int, D: int, flat: np.ndarray, op_a: str, op_b: str) -> np.ndarray:
+    """<A_i B_j> per nearest-neighbour bond from the state vector (X flips the
+    site's bit, Z multiplies by its sign)."""
+    from paper_1908_08553_gb300.inputs import bonds
+    psi = state_vector(L, W, D, flat)
+    idx = np.arange(psi.size)
+
+    def apply(op, k, v):
+        if op == "x":
+            return v[idx ^ (1 << k)]
+        return v * np.where((idx >> k) & 1, 1.0, -1.0)
+
+    out = []
+    for (ri, ci), (rj, cj) in bonds(L, W):
+        i, j = ri * W + ci, rj * W + cj
+        out.append(float(psi @ apply(op_a, i, apply(op_b, j, psi))))
+    return np.array(out) / float(psi @ psi)
+
+
 def hamiltonian(L: int, W: int, J: float, h: float):
     """Sparse TFIM Hamiltonian -J sum Z_i Z_j - h sum X_k on the 2^N basis."""
     import scipy.sparse as sp

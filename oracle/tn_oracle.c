@@ -435,6 +435,64 @@ int or_peps_sz(int L, int W, int D, const double *A, double *sz) {
     return 0;
 }
 
+/*
+ * Nearest-neighbour two-site correlators <A_i B_j> for every bond (i, j) in the
+ * output order of szsz (horizontal row-major, then vertical; i the left or
+ * upper site), A and B Pauli X (code 1) or Z (code 2), with cached boundaries
+ * (Sec. 5: one operator inserted on each of the two sites, then the ratio to
+ * the norm).  out[nb] is caller-owned.
+ */
+int or_peps_bond_ops(int L, int W, int D, const double *A, int op_a, int op_b, double *out) {
+    const double *oa = op_a == 1 ? OP_X : OP_Z, *ob = op_b == 1 ? OP_X : OP_Z;
+    grid_t g = norm_grid(L, W, D, A);
+    size_t *off = site_offsets(L, W, D);
+    bnd_t *tops = (bnd_t *)malloc(sizeof(bnd_t) * (L + 1));
+    bnd_t *bots = (bnd_t *)malloc(sizeof(bnd_t) * (L + 1));
+    top_boundaries(&g, tops);
+    bottom_boundaries(&g, bots);
+    double nm; int64_t ne;
+    bnd_dot(&tops[L], &bots[L], &nm, &ne);
+    double **over = (double **)calloc((size_t)W, sizeof(double *));
+    int k = 0, d[4];
+    for (int r = 0; r < L; ++r)
+        for (int c = 0; c + 1 < W; ++c) {
+            site_dims(L, W, D, r, c, d);
+            double *ea = double_layer(A + off[r * W + c], d, oa);
+            site_dims(L, W, D, r, c + 1, d);
+            double *eb = double_layer(A + off[r * W + c + 1], d, ob);
+            bnd_t b = bnd_copy(&tops[r]);
+            over[c] = ea; over[c + 1] = eb;
+            absorb_row(&g, r, over, &b);
+            over[c] = over[c + 1] = NULL;
+            double m; int64_t e;
+            bnd_dot(&b, &bots[r + 1], &m, &e);
+            out[k++] = ratio(m, e, nm, ne);
+            free(b.v); free(ea); free(eb);
+        }
+    for (int r = 0; r + 1 < L; ++r)
+        for (int c = 0; c < W; ++c) {
+            site_dims(L, W, D, r, c, d);
+            double *ea = double_layer(A + off[r * W + c], d, oa);
+            site_dims(L, W, D, r + 1, c, d);
+            double *eb = double_layer(A + off[(r + 1) * W + c], d, ob);
+            bnd_t b = bnd_copy(&tops[r]);
+            over[c] = ea;
+            absorb_row(&g, r, over, &b);
+            over[c] = eb;
+            absorb_row(&g, r + 1, over, &b);
+            over[c] = NULL;
+            double m; int64_t e;
+            bnd_dot(&b, &bots[r + 2], &m, &e);
+            out[k++] = ratio(m, e, nm, ne);
+            free(b.v); free(ea); free(eb);
+        }
+    free(over);
+    for (int r = 0; r <= L; ++r) { free(tops[r].v); free(bots[r].v); }
+    free(tops); free(bots); free(off);
+    grid_free(&g);
+    return 0;
+}
+
 /* E = -J sum <zz> - h sum <x>; also returns everything or_peps_observables does. */
 int or_peps_energy(int L, int W, int D, const double *A, double J, double h,
                    double *norm_m, int64_t *norm_e, double *sx, double *szsz,
