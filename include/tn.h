@@ -171,6 +171,14 @@ tn_status tn_expectation(tn_lattice *lat, tn_precision prec, int op, int i, int 
 /* Norm, every <X_k>, every <Z_i Z_j>, every <Z_k>, the connected c_ij and E
  * for (J, h) (blocking, AUTO schedule); each array of *out is filled if non-NULL. */
 tn_status tn_energy(tn_lattice *lat, double J, double h, tn_precision prec, tn_result *out);
+/* Nearest-neighbour two-site correlators <A_i B_j> (blocking, AUTO schedule):
+ * one Pauli operator on each site of every bond, A = op_a on the bond's first
+ * site i (left or upper) and B = op_b on j, op_a and op_b each TN_OP_X or
+ * TN_OP_Z (the insertion of Sec. 5 with operators other than Z Z; real
+ * arithmetic, so Y is not offered).  out: nb = L(W-1) + W(L-1) doubles,
+ * caller-owned, bonds in the order of tn_result.szsz.  TN_ERR_INVALID for
+ * other operators. */
+tn_status tn_bond_correlators(tn_lattice *lat, tn_precision prec, int op_a, int op_b, double *out);
 /* As tn_energy with an explicit schedule. */
 tn_status tn_energy_sched(tn_lattice *lat, double J, double h, tn_precision prec,
                           tn_schedule sched, tn_result *out);

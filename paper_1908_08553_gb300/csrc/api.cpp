@@ -341,6 +341,22 @@ tn_status tn_expectation(tn_lattice* lat, tn_precision prec, int op, int i, int 
     TN_GUARD_END
 }
 
+tn_status tn_bond_correlators(tn_lattice* lat, tn_precision prec, int op_a, int op_b, double* out) {
+    TN_GUARD_BEGIN
+    if (!lat || !out) return TN_ERR_INVALID;
+    auto phys = [](int op) { return op == TN_OP_X ? (int)PH_X : (op == TN_OP_Z ? (int)PH_Z : -1); };
+    const int a = phys(op_a), b = phys(op_b);
+    if (a < 0 || b < 0) { set_error("bond operators must be TN_OP_X or TN_OP_Z"); return TN_ERR_INVALID; }
+    const int L = lat->L, W = lat->W, nb = L * (W - 1) + W * (L - 1);
+    std::vector<double> r;
+    tn_status s = run_single(lat, prec, TN_SCHED_AUTO, work_bonds(a, b), 1.0, 0.0, &r, nullptr);
+    if (s != TN_OK) return s;
+    // result row: header, then the nb correlators (no site observables)
+    std::memcpy(out, r.data() + kResultHeader, sizeof(double) * nb);
+    return TN_OK;
+    TN_GUARD_END
+}
+
 // ------------------------------------------------------------- batches --
 
 tn_status tn_batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int* D, tn_precision prec,

@@ -131,8 +131,8 @@ Plan plan_choose(int L, int W, int D, tn_schedule sched, tn_work work) {
                 Plan c = plan_evaluate(L, W, D, o, i, j);
                 // energies cache every chain state: among cuts with the same
                 // bottleneck they prefer the smallest cached total
-                const int64_t kc = work == TN_WORK_ENERGY ? c.chain_elems : 0;
-                const int64_t kb = work == TN_WORK_ENERGY ? best.chain_elems : 0;
+                const int64_t kc = work != TN_WORK_NORM ? c.chain_elems : 0;
+                const int64_t kb = work != TN_WORK_NORM ? best.chain_elems : 0;
                 auto key = std::make_tuple(c.peak, kc, c.mac, c.centre, c.o, c.i, c.j);
                 auto bkey = std::make_tuple(best.peak, kb, best.mac, best.centre, best.o, best.i, best.j);
                 if (!have || key < bkey) { best = std::move(c); have = true; }

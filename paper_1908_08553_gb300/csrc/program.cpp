@@ -415,7 +415,12 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
     const int Mbot = bd.gemm(Qt[BL], Qt[BR], hbL, hbR, vrB, vrB, 1, 1, vrB);
     pg.norm_slot = pg.tensors[bd.dot(Mtop, Mbot, hbL * hbR)].slot;
 
-    if (work == TN_WORK_ENERGY) {
+    if (work != TN_WORK_NORM) {
+        // energies: every site and the ZZ bonds; bond work kinds: the bonds
+        // alone with operators A on each bond's first site and B on its second
+        const bool with_sites = work == TN_WORK_ENERGY;
+        const int bondA = work_is_bonds(work) ? work_bond_a(work) : PH_Z;
+        const int bondB = work_is_bonds(work) ? work_bond_b(work) : PH_Z;
         int Env[4] = {-1, -1, -1, -1};
         auto nonempty = [&](int q) { return !pl.corner[q].steps.empty(); };
         if (nonempty(TL)) Env[TL] = bd.gemm(Mbot, Qt[TR], hbL, vrT, hbR, hbR, 1, vrT, 1);
@@ -444,10 +449,10 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
             return sl;
         };
         // sites
-        pg.sx_slot.assign(nsite, -1);
-        pg.sz_slot.assign(nsite, -1);
-        pg.sx_den.assign(nsite, -1);
-        for (int s = 0; s < nsite; ++s) {
+        pg.sx_slot.assign(with_sites ? nsite : 0, -1);
+        pg.sz_slot.assign(with_sites ? nsite : 0, -1);
+        pg.sx_den.assign(with_sites ? nsite : 0, -1);
+        for (int s = 0; s < (with_sites ? nsite : 0); ++s) {
             const SiteRef& w = where[s];
             const Step& st = step_of(w.q, w.t);
             if (bd.dual_ok(st)) {
@@ -473,16 +478,17 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
             for (int c = 0; c < W; ++c) bonds.push_back({r * W + c, (r + 1) * W + c});
         int Xl = -1, Xr = -1;
         int den_cross[4] = {-1, -1, -1, -1};
-        // Chain of corner q over steps t0..t1 from x, Z at step t0 and I after;
-        // with adj >= 0 the last step is instead an absorb-dot with Z and adj.
-        // Consecutive steps of one frame row run as fused pairs where they can.
-        auto chain = [&](int q, int x, int t0, int t1, int adj) {
+        // Chain of corner q over steps t0..t1 from x, operator op0 at step t0
+        // and I after; with adj >= 0 the last step is instead an absorb-dot
+        // with operator op1 and adj.  Consecutive steps of one frame row run as
+        // fused pairs where they can.
+        auto chain = [&](int q, int x, int t0, int t1, int adj, int op0, int op1) {
             int u = t0;
             while (u <= t1) {
-                const int op_u = u == t0 ? PH_Z : PH_I;
+                const int op_u = u == t0 ? op0 : PH_I;
                 const bool last_dot = adj >= 0 && u == t1;
                 if (u < t1 && bd.pair_ok(step_of(q, u), step_of(q, u + 1))) {
-                    const int op_v = (adj >= 0 && u + 1 == t1) ? PH_Z : PH_I;
+                    const int op_v = (adj >= 0 && u + 1 == t1) ? op1 : PH_I;
                     if (adj >= 0 && u + 1 == t1)
                         return bd.absorb2_dot(x, E_at(q, u, op_u), E_at(q, u + 1, op_v), adj, step_of(q, u),
                                               step_of(q, u + 1));
@@ -490,15 +496,15 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
                     u += 2;
                     continue;
                 }
-                if (last_dot) return bd.absorb_dot(x, E_at(q, u, PH_Z), adj, step_of(q, u));
+                if (last_dot) return bd.absorb_dot(x, E_at(q, u, op1), adj, step_of(q, u));
                 x = bd.absorb(x, E_at(q, u, op_u), step_of(q, u), false);
                 ++u;
             }
             return x;
         };
-        auto regrow = [&](int q, int t) {
+        auto regrow = [&](int q, int t, int op) {
             const int T = (int)pl.corner[q].steps.size();
-            return chain(q, F[q][t - 1], t, T, -1);
+            return chain(q, F[q][t - 1], t, T, -1, op, PH_I);
         };
         pg.zz_slot.assign(bonds.size(), -1);
         pg.zz_den.assign(bonds.size(), pg.norm_slot);
@@ -528,21 +534,22 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
         };
         for (size_t bi = 0; bi < bonds.size(); ++bi) {
             SiteRef a = where[bonds[bi].first], b = where[bonds[bi].second];
+            int opa = bondA, opb = bondB;
             int v = -1;
             if (a.q == b.q) {
-                if (a.t > b.t) std::swap(a, b);
+                if (a.t > b.t) { std::swap(a, b); std::swap(opa, opb); }
                 const int q = a.q;
                 begin_chain(2 * max_out(q, a.t, b.t));
-                v = chain(q, F[q][a.t - 1], a.t, b.t, G[q][b.t]);
+                v = chain(q, F[q][a.t - 1], a.t, b.t, G[q][b.t], opa, opb);
                 end_chain(v);
                 pg.zz_den[bi] = norm_at(q, b.t);
             } else {
                 int qa = a.q, qb = b.q;
                 int ta = a.t, tb = b.t;
-                if (qa > qb) { std::swap(qa, qb); std::swap(ta, tb); }
+                if (qa > qb) { std::swap(qa, qb); std::swap(ta, tb); std::swap(opa, opb); }
                 const int Ta = (int)pl.corner[qa].steps.size(), Tb = (int)pl.corner[qb].steps.size();
                 begin_chain(2 * max_out(qa, ta, Ta) + 2 * max_out(qb, tb, Tb));
-                const int Za = regrow(qa, ta), Zb = regrow(qb, tb);
+                const int Za = regrow(qa, ta, opa), Zb = regrow(qb, tb, opb);
                 // each class of cut-crossing bond is normalised by the same fused
                 // product on the unmodified corners (the norm through the same path)
                 if (qa == TL && qb == TR) {

@@ -436,7 +436,7 @@ tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int
     if (!opts) opts = &defaults;
     if (n <= 0 || !L || !W || !D) { set_error("empty batch"); return TN_ERR_INVALID; }
     if (prec < TN_FP64 || prec > TN_BF16X6 || sched < TN_SCHED_AUTO || sched > TN_SCHED_QUADRANT ||
-        work < TN_WORK_NORM || work > TN_WORK_ENERGY) {
+        !work_valid(work)) {
         set_error("bad enum"); return TN_ERR_INVALID;
     }
     for (int k = 0; k < n; ++k)

@@ -148,6 +148,19 @@ struct Program {
     std::vector<int> site_dims;          // 4 per site
 };
 
+// Internal work kinds beyond tn_work: the nearest-neighbour correlators
+// <A_i B_j> alone, A = PhysOp a and B = PhysOp b (X or Z).
+inline tn_work work_bonds(int a, int b) { return (tn_work)(16 + 4 * a + b); }
+inline bool work_is_bonds(tn_work w) { return (int)w >= 16; }
+inline int work_bond_a(tn_work w) { return ((int)w - 16) / 4; }
+inline int work_bond_b(tn_work w) { return ((int)w - 16) % 4; }
+inline bool work_valid(tn_work w) {
+    if (w == TN_WORK_NORM || w == TN_WORK_ENERGY) return true;
+    if (!work_is_bonds(w)) return false;
+    const int a = work_bond_a(w), b = work_bond_b(w);
+    return (a == PH_X || a == PH_Z) && (b == PH_X || b == PH_Z) && (int)w < 32;
+}
+
 std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sched,
                                              tn_precision prec, tn_work work);
 // the same for a given plan (any orientation and cut)

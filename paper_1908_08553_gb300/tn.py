@@ -58,6 +58,7 @@ SIGNATURES = {
     "tn_contract_norm": (c_int, [c_void_p, c_int, c_int, POINTER(tn_scalar)]),
     "tn_expectation": (c_int, [c_void_p, c_int, c_int, c_int, c_int, POINTER(c_double)]),
     "tn_energy": (c_int, [c_void_p, c_double, c_double, c_int, POINTER(tn_result)]),
+    "tn_bond_correlators": (c_int, [c_void_p, c_int, c_int, c_int, POINTER(c_double)]),
     "tn_energy_sched": (c_int, [c_void_p, c_double, c_double, c_int, c_int, POINTER(tn_result)]),
     "tn_batch_create": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int,
                                 POINTER(c_void_p)]),
@@ -211,6 +212,15 @@ def tn_expectation(lat, prec: int, op: int, i: int, j: int = 0) -> float:
     v = c_double()
     check(lib().tn_expectation(lat, prec, op, i, j, byref(v)), "tn_expectation")
     return v.value
+
+
+def tn_bond_correlators(lat, prec: int, op_a: int, op_b: int, L: int, W: int) -> np.ndarray:
+    """<A_i B_j> on every nearest-neighbour bond, A, B in {TN_OP_X, TN_OP_Z}."""
+    nb = L * (W - 1) + W * (L - 1)
+    out = np.zeros(max(nb, 1))
+    check(lib().tn_bond_correlators(lat, prec, op_a, op_b, out.ctypes.data_as(POINTER(c_double))),
+          "tn_bond_correlators")
+    return out[:nb]
 
 
 def tn_energy_full(lat, J: float, h: float, prec: int, sched: int, L: int, W: int):
