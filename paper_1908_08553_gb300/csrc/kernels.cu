@@ -1472,24 +1472,23 @@ cudaError_t launch_dot(int dt, const DotTask* tasks, int ntasks, long long nbloc
 // frexp exponent of max|A| (so the matrix is O(1) and its slot carries 2 e_A).
 // The two copies are the bra and ket layers of Sec. 5 (real amplitudes, no
 // conjugation); O is I, X or Z = diag(-1, +1).
+// One warp per site matrix (8 per 256-thread block): the max of |A| by warp
+// shuffles, then each lane forms every 32nd entry.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_sitemat(const SiteMatTask* __restrict__ tasks, Slot* __restrict__ slots) {
-    __shared__ double red[32];
-    const SiteMatTask& t = tasks[blockIdx.x];
+k_sitemat(const SiteMatTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+    const int lane = threadIdx.x & 31;
+    const int ti = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (ti >= ntasks) return;
+    const SiteMatTask& t = tasks[ti];
     const int* dm = t.dims;
     const int nA = 2 * dm[0] * dm[1] * dm[2] * dm[3];
     double mx = 0.0;
-    for (int k = threadIdx.x; k < nA; k += blockDim.x) mx = fmax(mx, fabs(t.A[k]));
-    mx = block_max(mx, red);
-    __shared__ int eA;
-    if (threadIdx.x == 0) {
-        int e = 0;
-        if (mx > 0.0) frexp(mx, &e);
-        eA = e;
-        slots[t.slot_E].X = 2 * e;
-    }
-    __syncthreads();
+    for (int k = lane; k < nA; k += 32) mx = fmax(mx, fabs(t.A[k]));
+    mx = warp_max(mx);
+    int eA = 0;
+    if (mx > 0.0) frexp(mx, &eA);
+    if (lane == 0) slots[t.slot_E].X = 2 * eA;
     const double sc = ldexp(1.0, -2 * eA);
     const int fu = dm[t.map[0]], fl = dm[t.map[1]], fd = dm[t.map[2]], fr = dm[t.map[3]];
     double o00, o01, o10, o11;
@@ -1501,7 +1500,7 @@ k_sitemat(const SiteMatTask* __restrict__ tasks, Slot* __restrict__ slots) {
     // shapes are checked on the host; never read outside A if they disagree
     const bool shape_ok = (K == fl * fl * fu * fu) && (N == fd * fd * fr * fr);
     const long long stride_p = (long long)dm[0] * dm[1] * dm[2] * dm[3];
-    for (int idx = threadIdx.x; idx < K * N; idx += blockDim.x) {
+    for (int idx = lane; idx < K * N; idx += 32) {
         const int k = idx / N, n = idx - k * N;
         const int uu = k % (fu * fu), hh = k / (fu * fu);
         const int rr = n % (fr * fr), dd = n / (fr * fr);
@@ -1516,15 +1515,16 @@ k_sitemat(const SiteMatTask* __restrict__ tasks, Slot* __restrict__ slots) {
         const double a0 = t.A[ia], a1 = t.A[stride_p + ia];
         const double b0 = t.A[ib], b1 = t.A[stride_p + ib];
         const double v = a0 * (o00 * b0 + o01 * b1) + a1 * (o10 * b0 + o11 * b1);
-        E[idx] = shape_ok ? (T)(v * sc) : T(0);
+        E[idx] = (T)(v * sc);
     }
 }
 
 cudaError_t launch_sitemat(int dt, const SiteMatTask* tasks, int ntasks, Slot* slots,
                            cudaStream_t st) {
     if (ntasks <= 0) return cudaSuccess;
-    if (dt == 0) k_sitemat<double><<<ntasks, 256, 0, st>>>(tasks, slots);
-    else k_sitemat<float><<<ntasks, 256, 0, st>>>(tasks, slots);
+    const unsigned blocks = (unsigned)((ntasks + 7) / 8);
+    if (dt == 0) k_sitemat<double><<<blocks, 256, 0, st>>>(tasks, ntasks, slots);
+    else k_sitemat<float><<<blocks, 256, 0, st>>>(tasks, ntasks, slots);
     return cudaGetLastError();
 }
 
