@@ -1,7 +1,8 @@
 // Program builder: turns a plan (planner.cpp) into the list of pairwise
-// contractions that yield the norm and, for TN_WORK_ENERGY, every <X_k> and
-// every nearest-neighbour <Z_i Z_j> (Sec. 5: "the network must be similarly
-// fully contracted for every site and pair").
+// contractions that yield the norm and, for TN_WORK_ENERGY, every <X_k>,
+// every <Z_k> and every nearest-neighbour <Z_i Z_j> (Sec. 5 contracts the
+// network once more for every site and every pair); the bond work kinds give
+// <A_i B_j> on every bond for A, B in {X, Z} instead.
 //
 // Structure (oriented lattice, corners TL, TR, BL, BR):
 //   F[q][t]   forward chain of corner q: F[q][t] = absorb(F[q][t-1], E_I(site t))
@@ -9,10 +10,13 @@
 //   Env[TL] = M_bot TR, Env[TR] = M_bot^T TL, Env[BL] = M_top BR, Env[BR] = M_top^T BL
 //   G[q][t]   environment sweep: G[q][T] = Env[q],
 //             G[q][t-1] = absorb(G[q][t], E_I(site t)^T), so <F[q][t], G[q][t]> = norm
-//   site k at step t:      <absorb(F[q][t-1], E_X), G[q][t]>
+//   site k at step t:      <absorb(F[q][t-1], E_O), G[q][t]> for O = X, Z and
+//                          I (the local norm) in one pass where the FP32
+//                          kernel serves the step
 //   bond inside corner q:  Z inserted at the first site, the chain carried to
 //                          the second site (1 step, or one frame row), Z there,
-//                          dotted with G at that step
+//                          dotted with G at that step; consecutive steps of one
+//                          frame row fused in pairs
 //   bond across a cut:     both corners regrown with Z to their last step, then
 //                          one dense product with the rest of the ring.
 // Every value is exact (no truncation); reusing the unchanged corners and
