@@ -2,11 +2,11 @@
 
 Sec. 4: the network is contracted as a chain of pairwise contractions; the
 size of a pairwise result follows d(B) = d(A1) d(A2) / d(x) (x = shared legs)
-and the largest intermediate is the "bottleneck contraction", which the
-heuristic minimises: "select the order which minimizes the bottleneck
-contraction size and partition the lattice around the ring of tensors".  The
-candidates are the row scheme (Fig. 2a), the quadrant scheme (Fig. 2b) and the
-cuts "somewhere between" the two.
+and the largest intermediate is the bottleneck contraction.  The heuristic
+picks the contraction order with the smallest bottleneck and splits the
+lattice into parts around the ring that closes the contraction.  The
+candidates are the row scheme (Fig. 2a), the quadrant scheme (Fig. 2b) and
+the cuts that lie between the two.
 
 Reading used here (the paper gives no formula for the candidates):
   * orientation o in {0, 1}: o = 1 works on the transposed lattice

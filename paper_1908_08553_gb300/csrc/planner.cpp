@@ -1,7 +1,8 @@
-// Partition and contraction-order choice of Sec. 4 ("select the order which
-// minimizes the bottleneck contraction size and partition the lattice around
-// the ring of tensors"), with the size rule d(B) = d(A1) d(A2) / d(x) of the
-// same section applied to every site absorption and ring product.
+// Partition and contraction-order choice of Sec. 4: among the candidate
+// partitions, take the one whose largest pairwise contraction (the bottleneck)
+// is smallest and split the lattice into corners around the closing ring,
+// with the size rule d(B) = d(A1) d(A2) / d(x) of the same section applied to
+// every site absorption and ring product.
 //
 // Candidates: orientation o (o = 1: transposed lattice) and a cut (i, j) of
 // the oriented Lp x Wp lattice into corners TL, TR, BL, BR (rows [0,i) /
