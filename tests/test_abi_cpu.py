@@ -120,6 +120,20 @@ def test_invalid_arguments(cpu_ctx):
         with pytest.raises(tn.TNError) as e:
             tn.tn_contract_norm(lat, tn.TN_FP64)
         assert e.value.status == tn.TN_ERR_NO_DEVICE
+        # observables: arguments are checked before any device work
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_expectation(lat, tn.TN_FP64, tn.TN_OP_Z, 9)
+        assert e.value.status == tn.TN_ERR_INVALID
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_expectation(lat, tn.TN_FP64, tn.TN_OP_Z, 4)
+        assert e.value.status == tn.TN_ERR_NO_DEVICE
+        for a, b in ((tn.TN_OP_ZZ, tn.TN_OP_X), (tn.TN_OP_X, tn.TN_OP_NORM), (7, tn.TN_OP_Z)):
+            with pytest.raises(tn.TNError) as e:
+                tn.tn_bond_correlators(lat, tn.TN_FP64, a, b, 3, 3)
+            assert e.value.status == tn.TN_ERR_INVALID
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_bond_correlators(lat, tn.TN_FP64, tn.TN_OP_X, tn.TN_OP_Z, 3, 3)
+        assert e.value.status == tn.TN_ERR_NO_DEVICE
     finally:
         tn.tn_destroy_lattice(lat)
     with pytest.raises(tn.TNError) as e:
