@@ -289,6 +289,13 @@ tn_status tn_absorb_dot_noalloc(int dtype, const void *in, const void *E, const 
 const char *tn_status_string(tn_status s);
 /* Message of the last failing call on this host thread ("" if none). */
 const char *tn_last_error(void);
+/* Bounded-wait self-check (no counterpart in the paper; failure detection of
+ * the library's device waits): launches one thread that waits on a device flag
+ * nothing sets, bounded by limit_ms of GPU clock, as every pipelined kernel's
+ * wait is; *expired receives 1 when the wait ran out and the kernel exited
+ * cleanly (the context stays usable), 0 otherwise.  Allocates 8 bytes of
+ * device memory for the call.  TN_ERR_INVALID for limit_ms outside (0, 10000]. */
+tn_status tn_wait_selfcheck(tn_ctx *ctx, double limit_ms, int *expired);
 /* Per kernel family since the last reset: launches, summed device time (ms,
  * from CUDA events around each launch, only while profiling is on),
  * algorithmic bytes and multiply-adds.  family: 0 absorb (one step),

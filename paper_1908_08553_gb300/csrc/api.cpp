@@ -483,6 +483,32 @@ tn_status tn_ctx_set_profiling(tn_ctx* ctx, int on) {
     return TN_OK;
 }
 
+tn_status tn_wait_selfcheck(tn_ctx* ctx, double limit_ms, int* expired) {
+    TN_GUARD_BEGIN
+    if (!ctx || !expired || !(limit_ms > 0.0 && limit_ms <= 10000.0)) return TN_ERR_INVALID;
+    if (ctx->device < 0) { set_error("context has no device"); return TN_ERR_NO_DEVICE; }
+    cudaSetDevice(ctx->device);
+    int khz = 0;   // SM clock in kHz = cycles per ms (2 GHz if the query is unavailable)
+    if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device) != cudaSuccess || khz <= 0) {
+        cudaGetLastError();
+        khz = 2000000;
+    }
+    const long long cycles = (long long)(limit_ms * (double)khz);
+    cudaError_t e;
+    int* d = nullptr;   // [flag, status]
+    if ((e = cudaMalloc(&d, 2 * sizeof(int))) != cudaSuccess) return cuda_status(e, "self-check allocation");
+    int h[2] = {1, 1};
+    e = cudaMemsetAsync(d, 0, 2 * sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = launch_wait_probe(d, cycles, d + 1, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_status(e, "self-check");
+    *expired = (h[0] == 0 && h[1] == 1) ? 1 : 0;
+    return TN_OK;
+    TN_GUARD_END
+}
+
 tn_status tn_ctx_kernel_stats(tn_ctx* ctx, int family, int64_t* launches, double* ms, double* bytes, double* macs) {
     if (!ctx || family < 0 || family >= kFamilies) return TN_ERR_INVALID;
     std::lock_guard<std::mutex> g(ctx->mu);

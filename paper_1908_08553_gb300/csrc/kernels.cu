@@ -1528,6 +1528,27 @@ cudaError_t launch_sitemat(int dt, const SiteMatTask* tasks, int ntasks, Slot* s
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------- wait self-check --
+
+// Spins on a device flag that nothing sets, bounded by limit_cycles of
+// clock64 (the form every wait of the library's pipelined kernels takes), then
+// records the expiry in *status and returns: the failure path exercised on
+// purpose, with no trap and no hang.
+__global__ void k_wait_probe(const volatile int* flag, long long limit_cycles, int* status) {
+    const long long t0 = clock64();
+    while (*flag == 0) {
+        if (clock64() - t0 > limit_cycles) {
+            atomicExch(status, 1);
+            return;
+        }
+    }
+}
+
+cudaError_t launch_wait_probe(const int* flag, long long limit_cycles, int* status, cudaStream_t st) {
+    k_wait_probe<<<1, 1, 0, st>>>(flag, limit_cycles, status);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- init ------
 
 __global__ void k_init(Slot* slots, long long nslots, const ConstOne* ones, int nones, int dt) {

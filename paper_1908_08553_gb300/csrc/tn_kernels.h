@@ -161,6 +161,9 @@ int gemm_variant(int dt, long long M, long long N, long long K, long long sam, l
                  long long sbn);
 long long gemm_tiles_v(int variant, long long M, long long N, int* tiles_n);
 long long gemm_ksplit(int variant, bool dot, long long K);
+// Bounded-wait self-check: one thread waits on *flag (never set by the
+// library) for at most limit_cycles, then sets *status to 1.
+cudaError_t launch_wait_probe(const int* flag, long long limit_cycles, int* status, cudaStream_t st);
 cudaError_t launch_dot(int dt, const DotTask* tasks, int ntasks, long long nblocks, Slot* slots,
                        cudaStream_t st, const int* tmap = nullptr);
 cudaError_t launch_sitemat(int dt, const SiteMatTask* tasks, int ntasks, Slot* slots,

@@ -58,6 +58,7 @@ SIGNATURES = {
     "tn_contract_norm": (c_int, [c_void_p, c_int, c_int, POINTER(tn_scalar)]),
     "tn_expectation": (c_int, [c_void_p, c_int, c_int, c_int, c_int, POINTER(c_double)]),
     "tn_energy": (c_int, [c_void_p, c_double, c_double, c_int, POINTER(tn_result)]),
+    "tn_wait_selfcheck": (c_int, [c_void_p, c_double, POINTER(c_int)]),
     "tn_bond_correlators": (c_int, [c_void_p, c_int, c_int, c_int, POINTER(c_double)]),
     "tn_energy_sched": (c_int, [c_void_p, c_double, c_double, c_int, c_int, POINTER(tn_result)]),
     "tn_batch_create": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int,
@@ -212,6 +213,13 @@ def tn_expectation(lat, prec: int, op: int, i: int, j: int = 0) -> float:
     v = c_double()
     check(lib().tn_expectation(lat, prec, op, i, j, byref(v)), "tn_expectation")
     return v.value
+
+
+def tn_wait_selfcheck(ctx, limit_ms: float) -> bool:
+    """True when a bounded device wait on a flag nothing sets expired cleanly."""
+    v = c_int()
+    check(lib().tn_wait_selfcheck(ctx, limit_ms, byref(v)), "tn_wait_selfcheck")
+    return bool(v.value)
 
 
 def tn_bond_correlators(lat, prec: int, op_a: int, op_b: int, L: int, W: int) -> np.ndarray:

@@ -137,6 +137,12 @@ def test_invalid_arguments(cpu_ctx):
     finally:
         tn.tn_destroy_lattice(lat)
     with pytest.raises(tn.TNError) as e:
+        tn.tn_wait_selfcheck(cpu_ctx, 0.0)
+    assert e.value.status == tn.TN_ERR_INVALID
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_wait_selfcheck(cpu_ctx, 20.0)
+    assert e.value.status == tn.TN_ERR_NO_DEVICE
+    with pytest.raises(tn.TNError) as e:
         tn.tn_absorb(1, 0, 0, 0, 1, 16, 16, 1)
     assert e.value.status == tn.TN_ERR_INVALID
     assert tn.lib().tn_status_string(tn.TN_ERR_OVER_BUDGET).decode().startswith("footprint")
