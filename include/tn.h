@@ -160,6 +160,19 @@ tn_status tn_plan(const tn_lattice *lat, tn_schedule sched, int64_t *out, size_t
 tn_status tn_plan_work(const tn_lattice *lat, tn_schedule sched, tn_work work, int64_t *out, size_t cap,
                        size_t *n);
 
+/* Contraction program of the lattice (host only, no device needed): builds it
+ * as a contraction would and checks it -- every pairwise contraction runs
+ * after the contractions producing its inputs and within their lifetimes, and
+ * no two tensors alive at the same time share memory (TN_ERR_NUMERIC with the
+ * reason in tn_last_error otherwise).  Writes at most cap words to out and the
+ * full length to *n:
+ *   [0] contractions (ops)   [1] waves   [2] arena bytes   [3] footprint bytes
+ *   [4] absorption-family algorithmic bytes (single steps, fused step pairs
+ *       and absorb-dots)      [5] fused step pairs   [6] product multiply-adds
+ * work: TN_WORK_NORM or TN_WORK_ENERGY. */
+tn_status tn_program_info(const tn_lattice *lat, tn_precision prec, tn_schedule sched, tn_work work,
+                          int64_t *out, size_t cap, size_t *n);
+
 /* ---------------------------------------------------------- contraction -- */
 
 /* <Psi|Psi> (blocking). */

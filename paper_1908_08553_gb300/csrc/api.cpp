@@ -262,6 +262,39 @@ tn_status tn_plan(const tn_lattice* lat, tn_schedule sched, int64_t* out, size_t
     return tn_plan_work(lat, sched, TN_WORK_NORM, out, cap, n);
 }
 
+tn_status tn_program_info(const tn_lattice* lat, tn_precision prec, tn_schedule sched, tn_work work,
+                          int64_t* out, size_t cap, size_t* n) {
+    TN_GUARD_BEGIN
+    if (!lat || !n || prec < TN_FP64 || prec > TN_BF16X6 || sched < TN_SCHED_AUTO || sched > TN_SCHED_QUADRANT ||
+        (work != TN_WORK_NORM && work != TN_WORK_ENERGY))
+        return TN_ERR_INVALID;
+    const auto pg = program_cached(lat->L, lat->W, lat->D, sched, prec, work);
+    const std::string why = program_verify(*pg);
+    if (!why.empty()) { set_error("inconsistent program: " + why); return TN_ERR_NUMERIC; }
+    double absorb_bytes = 0, product_macs = 0;
+    int64_t pairs = 0;
+    for (const Op& op : pg->ops) {
+        if (op.kind == OP_ABSORB || op.kind == OP_ABSORB_DOT || op.kind == OP_ABSORB2 || op.kind == OP_ABSORB2_DOT)
+            absorb_bytes += op.bytes;
+        if (op.kind == OP_ABSORB2 || op.kind == OP_ABSORB2_DOT) ++pairs;
+        if (op.kind == OP_GEMM || op.kind == OP_GEMM_DOT || op.kind == OP_TC_GEMM || op.kind == OP_TC_GEMM_DOT)
+            product_macs += op.macs;
+    }
+    size_t footprint = 0;
+    tn_batch* b = nullptr;
+    const int L = lat->L, W = lat->W, D = lat->D;
+    const tn_status fs = batch_create(lat->ctx, 1, &L, &W, &D, prec, sched, work, false, &b, &footprint);
+    if (b) delete b;
+    if (fs != TN_OK) return fs;
+    const int64_t w[7] = {(int64_t)pg->ops.size(), (int64_t)pg->n_levels, pg->arena_bytes, (int64_t)footprint,
+                          (int64_t)absorb_bytes, pairs, (int64_t)product_macs};
+    *n = 7;
+    if (out)
+        for (size_t k = 0; k < 7 && k < cap; ++k) out[k] = w[k];
+    return TN_OK;
+    TN_GUARD_END
+}
+
 tn_status tn_plan_work(const tn_lattice* lat, tn_schedule sched, tn_work work, int64_t* out, size_t cap,
                        size_t* n) {
     TN_GUARD_BEGIN

@@ -593,4 +593,40 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
     return pgp;
 }
 
+std::string program_verify(const Program& pg) {
+    const auto& T = pg.tensors;
+    auto bad_id = [&](int id) { return id < 0 || id >= (int)T.size(); };
+    // waves: every op runs after the ops that produce its inputs, at its outputs' wave
+    for (size_t k = 0; k < pg.ops.size(); ++k) {
+        const Op& op = pg.ops[k];
+        for (int in : {op.in, op.E, op.E2, op.E3, op.adj, op.A, op.B, op.C}) {
+            if (in < 0) continue;
+            if (bad_id(in)) return "op " + std::to_string(k) + " reads an unknown tensor";
+            const Tensor& t = T[in];
+            if (t.level >= op.level && !t.is_site)
+                return "op " + std::to_string(k) + " reads a tensor produced at its own or a later wave";
+            if (t.last_use < op.level) return "op " + std::to_string(k) + " reads a tensor after its last use";
+        }
+        for (int o : {op.out, op.out2, op.out3}) {
+            if (o < 0) continue;
+            if (bad_id(o)) return "op " + std::to_string(k) + " writes an unknown tensor";
+            if (T[o].level != op.level) return "op " + std::to_string(k) + " writes outside its wave";
+        }
+    }
+    // arena: tensors alive in a common wave never share bytes, all lie inside it
+    struct Iv { int64_t lo, hi; int l0, l1; };
+    std::vector<Iv> iv;
+    for (const Tensor& t : T) {
+        if (t.n == 0 || t.is_site) continue;
+        const int64_t len = t.n * pg.esize;
+        if (t.offset < 0 || t.offset + len > pg.arena_bytes) return "tensor outside the arena";
+        iv.push_back({t.offset, t.offset + len, t.level, std::max(t.level, t.last_use)});
+    }
+    std::sort(iv.begin(), iv.end(), [](const Iv& a, const Iv& b) { return a.lo < b.lo; });
+    for (size_t a = 0; a < iv.size(); ++a)
+        for (size_t b = a + 1; b < iv.size() && iv[b].lo < iv[a].hi; ++b)
+            if (iv[a].l0 <= iv[b].l1 && iv[b].l0 <= iv[a].l1) return "two live tensors share arena bytes";
+    return "";
+}
+
 }  // namespace tn

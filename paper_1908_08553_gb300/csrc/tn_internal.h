@@ -165,6 +165,9 @@ std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sc
                                              tn_precision prec, tn_work work);
 // the same for a given plan (any orientation and cut)
 std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision prec, tn_work work);
-int64_t program_footprint(const Program& p);   // arena + inputs + slots + results + scratch
+// Consistency of a built program ("" if sound): every op runs after the
+// producers of its inputs and within their lifetimes, and no two tensors alive
+// in a common wave share arena bytes.
+std::string program_verify(const Program& pg);
 
 }  // namespace tn

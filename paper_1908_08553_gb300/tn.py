@@ -58,6 +58,7 @@ SIGNATURES = {
     "tn_contract_norm": (c_int, [c_void_p, c_int, c_int, POINTER(tn_scalar)]),
     "tn_expectation": (c_int, [c_void_p, c_int, c_int, c_int, c_int, POINTER(c_double)]),
     "tn_energy": (c_int, [c_void_p, c_double, c_double, c_int, POINTER(tn_result)]),
+    "tn_program_info": (c_int, [c_void_p, c_int, c_int, c_int, POINTER(c_int64), c_size_t, POINTER(c_size_t)]),
     "tn_wait_selfcheck": (c_int, [c_void_p, c_double, POINTER(c_int)]),
     "tn_bond_correlators": (c_int, [c_void_p, c_int, c_int, c_int, POINTER(c_double)]),
     "tn_energy_sched": (c_int, [c_void_p, c_double, c_double, c_int, c_int, POINTER(tn_result)]),
@@ -98,7 +99,8 @@ def lib(build_if_needed: bool = True):
         path = _build.build() if build_if_needed else _build.LIB
         if not os.path.exists(path):
             raise RuntimeError(f"libtn not built at {path}")
-        _lib = ctypes.CDLL(path)
+        # bind every symbol at load: a missing definition fails here, not mid-run
+        _lib = ctypes.CDLL(path, mode=os.RTLD_NOW | os.RTLD_LOCAL)
         for name, (res, args) in SIGNATURES.items():
             f = getattr(_lib, name)
             f.restype = res
@@ -213,6 +215,16 @@ def tn_expectation(lat, prec: int, op: int, i: int, j: int = 0) -> float:
     v = c_double()
     check(lib().tn_expectation(lat, prec, op, i, j, byref(v)), "tn_expectation")
     return v.value
+
+
+def tn_program_info(lat, prec: int, sched: int = TN_SCHED_AUTO, work: int = TN_WORK_ENERGY) -> dict:
+    """Build and check the lattice's contraction program (host only)."""
+    out = np.zeros(7, dtype=np.int64)
+    n = c_size_t()
+    check(lib().tn_program_info(lat, prec, sched, work, out.ctypes.data_as(POINTER(c_int64)), out.size, byref(n)),
+          "tn_program_info")
+    keys = ["ops", "waves", "arena_bytes", "footprint_bytes", "absorb_bytes", "fused_pairs", "product_macs"]
+    return dict(zip(keys, (int(v) for v in out)))
 
 
 def tn_wait_selfcheck(ctx, limit_ms: float) -> bool:
