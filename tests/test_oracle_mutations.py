@@ -88,3 +88,63 @@ def test_unmutated_oracle_passes(tmp_path):
 def test_mutant_is_caught(name, tmp_path):
     lib = _build_mutant(name, tmp_path)
     assert not _pins_pass(lib), f"planted mistake {name} was not caught"
+
+
+# ---- single-site <Z_k> and two-site correlators (their own pins) ----------
+
+MUTATIONS_Z = {
+    # <Z_k> computed with the X site matrix
+    "sz_uses_x": ("double *ez = double_layer(A + off[r * W + c], d, OP_Z);",
+                  "double *ez = double_layer(A + off[r * W + c], d, OP_X);"),
+    # <Z_k> closed with the bottom boundary of the wrong row
+    "sz_bottom_row": ("bnd_dot(&b, &bots[r + 1], &m, &e);\n            sz[r * W + c]",
+                      "bnd_dot(&b, &bots[r], &m, &e);\n            sz[r * W + c]"),
+    # the first operator of a bond ignored (always Z)
+    "bond_ignores_op_a": ("const double *oa = op_a == 1 ? OP_X : OP_Z,",
+                          "const double *oa = OP_Z,"),
+    # vertical bonds: the two operators exchanged between the rows
+    "bond_vertical_swapped": ("            over[c] = ea;\n            absorb_row(&g, r, over, &b);\n            over[c] = eb;",
+                              "            over[c] = eb;\n            absorb_row(&g, r, over, &b);\n            over[c] = ea;"),
+}
+
+
+def _build_mutant_z(name, tmp_path):
+    old, new = MUTATIONS_Z[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / f"{name}.so"
+    subprocess.check_call(["gcc", "-O1", "-fopenmp", "-shared", "-fPIC", "-std=c11",
+                           "-o", str(so), str(path), "-lm"])
+    lib = ctypes.CDLL(str(so))
+    P, i32 = ctypes.c_void_p, ctypes.c_int
+    lib.or_peps_sz.argtypes = [i32, i32, i32, P, P]
+    lib.or_peps_bond_ops.argtypes = [i32, i32, i32, P, i32, i32, P]
+    return lib
+
+
+def _z_pins_pass(lib):
+    """The state-vector pins of <Z_k> and of the X-X and X-Z bond correlators."""
+    L, W, D = 3, 3, 2
+    A = inputs.random_lattice(L, W, D, 4343)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    sz = np.zeros(L * W)
+    lib.or_peps_sz(L, W, D, p(A), p(sz))
+    ok = np.allclose(sz, brute.sz(L, W, D, A), atol=1e-12)
+    nb = L * (W - 1) + W * (L - 1)
+    for a, b, ca, cb in (("x", "x", 1, 1), ("x", "z", 1, 2)):
+        out = np.zeros(nb)
+        lib.or_peps_bond_ops(L, W, D, p(A), ca, cb, p(out))
+        ok &= np.allclose(out, brute.bond_correlators(L, W, D, A, a, b), atol=1e-12)
+    return bool(ok)
+
+
+def test_unmutated_oracle_passes_z_pins():
+    assert _z_pins_pass(oracle.lib())
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS_Z))
+def test_z_mutant_is_caught(name, tmp_path):
+    lib = _build_mutant_z(name, tmp_path)
+    assert not _z_pins_pass(lib), f"planted mistake {name} was not caught"
