@@ -72,7 +72,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
     lay.nin = nin;
     lay.nslots = nslots;
     lay.nres = nres;
-    // --- group operations: (level, kind, K, N) -> op refs (member-major order)
+    // --- group operations: (level, kind, K, N, variant) -> op refs (member-major order)
     std::map<std::tuple<int, int, int, int, int>, std::vector<OpRef>> groups;
     int64_t npart = 0;
     for (int mi = 0; mi < (int)b->m.size(); ++mi) {
@@ -82,9 +82,8 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
             int K = 0, N = 0, var = 0;
             if (op.kind == OP_ABSORB || op.kind == OP_ABSORB_DOT) {
                 K = op.K; N = op.N;
-                // 3 / 4: tensor-core absorption with 2 / 3 split planes
-                // 3 / 4: tensor-core absorption with 2 / 3 split planes; 11 / 12: dual dot;
-                // 21 / 22: triple dot; else 0..2
+                // 0..2: SIMT (generic, 4 positions along s, 4 along p); 3 / 4: tensor
+                // cores with 2 / 3 split planes; +10: dual dot; +20: triple dot
                 var = op.nsplit ? 1 + op.nsplit : absorb_variant(b->dt, op.P, op.S, op.K, op.N);
                 if (op.E3 >= 0) var += 20;
                 else if (op.E2 >= 0) var += 10;
