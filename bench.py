@@ -33,6 +33,7 @@ L_, W_, D_ = 8, 8, 2
 H_FIELDS = (2.0, 3.04, 4.0)
 METRIC = "exact LxL Ising-PEPS energy evals/s"
 ABSORB_DRAM_PER_BYTE = 89.35 / 134.22      # k_absorb4<16,16,1,0> capture, profiles/k_absorb4_8x8_d2_batch64.md
+GEMM_DRAM_PER_MAC = 373.1e6 / (640 * 256.0 ** 3)   # k_gemm3<1,0,1> capture, profiles/k_gemm3_8x8_d2_batch64.md
 WORKLOAD = "8x8 open-boundary TFIM PEPS, D=2, E at h in {2.0, 3.04, 4.0}"
 
 
@@ -663,9 +664,15 @@ def main():
             peak = 152 * 64 * 2 * sm_max * 1e6 / 1e12 / 32    # FP64: 1/64 of the FP32 lane rate
         else:
             peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # FP32 FMA lanes x 2 flop x max clock
-        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": name,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max clock (derived)"}
+        r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+             "traffic": None, "kernel": name,
+             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max clock (derived)"}
+        if name == "gemm_simt" and prec == tn.TN_FP32 and fd["launches"]:
+            # DRAM bytes per multiply-add of the batched 256^3 products, from one
+            # ncu capture (640 products: 373.1 MB), times this run's mean per launch
+            r["traffic"] = GEMM_DRAM_PER_MAC * fd["macs"] / fd["launches"]
+            r["traffic_source"] = "ncu dram bytes/multiply-add of one product launch x mean multiply-adds per launch"
+        return r
 
     esize = 4 if prec != tn.TN_FP64 else 8
     roof = roofline_of(dom)
