@@ -46,16 +46,17 @@ def lib():
         P = ctypes.c_void_p
         _lib.or_grid_contract.argtypes = [i32, i32, P, P, P, P]
         _lib.or_peps_norm.argtypes = [i32, i32, i32, P, P, P]
+        _lib.or_peps_sweep_rows.argtypes = [i32, i32, i32, P, i32, i32, P, P]
+        _lib.or_peps_sweep_rows.restype = i32
         _lib.or_peps_norm_all_cuts.argtypes = [i32, i32, i32, P, P, P]
         _lib.or_peps_observables.argtypes = [i32, i32, i32, P, P, P, P, P]
-        _lib.or_peps_energy.argtypes = [i32, i32, i32, P, d, d, P, P, P, P, P]
         _lib.or_peps_expect_one.argtypes = [i32, i32, i32, P, i32, i32, i32, P, P, P]
         _lib.or_ising_enumerate.argtypes = [i32, i32, d, P, P, P]
         _lib.or_peps_sz.argtypes = [i32, i32, i32, P, P]
         _lib.or_peps_bond_ops.argtypes = [i32, i32, i32, P, i32, i32, P]
         _lib.or_peps_bond_ops.restype = i32
         for f in (_lib.or_grid_contract, _lib.or_peps_norm, _lib.or_peps_norm_all_cuts,
-                  _lib.or_peps_observables, _lib.or_peps_energy, _lib.or_peps_expect_one,
+                  _lib.or_peps_observables, _lib.or_peps_expect_one,
                   _lib.or_ising_enumerate, _lib.or_num_threads, _lib.or_peps_sz):
             f.restype = i32
     return _lib
@@ -92,6 +93,54 @@ def norm(L: int, W: int, D: int, A: np.ndarray) -> tuple[float, int]:
     m, e = np.zeros(1), np.zeros(1, np.int64)
     lib().or_peps_norm(L, W, D, _ptr(A), _ptr(m), _ptr(e))
     return float(m[0]), int(e[0])
+
+
+def sweep_rows(L: int, W: int, D: int, A: np.ndarray, nrows: int, ncols: int = 0) -> tuple[float, int]:
+    """The first nrows rows of the row sweep, then the first ncols sites of the
+    next row (a bounded timing sample)."""
+    A = _check_sites(L, W, D, A)
+    m, e = np.zeros(1), np.zeros(1, np.int64)
+    if lib().or_peps_sweep_rows(L, W, D, _ptr(A), nrows, ncols, _ptr(m), _ptr(e)) != 0:
+        raise ValueError("nrows / ncols out of range")
+    return float(m[0]), int(e[0])
+
+
+def sweep_macs(L: int, W: int, D: int, nrows: int, ncols: int = 0) -> int:
+    """Multiply-adds of sweep_rows(L, W, D, A, nrows, ncols): a site absorption
+    of the row sweep maps [P, h, u, S] to [P, dn, rt, S] with P * S * (h u)(dn rt)
+    multiply-adds (double-layer dimensions, each leg D^2 or 1 on the edge)."""
+    d = D * D
+
+    def leg(on_edge):
+        return 1 if on_edge else d
+
+    total = 0
+    for r in range(min(nrows + 1, L)):
+        cols = W if r < nrows else ncols
+        for c in range(cols):
+            P = 1
+            for k in range(c):
+                P *= leg(r == L - 1)                 # dn legs of the sites already absorbed
+            S = 1
+            for k in range(c + 1, W):
+                S *= leg(r == 0)                     # u legs of the sites still to come
+            h, u = leg(c == 0), leg(r == 0)
+            dn, rt = leg(r == L - 1), leg(c == W - 1)
+            total += P * S * h * u * dn * rt
+    return total
+
+
+def energy_macs(L: int, W: int, D: int) -> int:
+    """Multiply-adds of observables(): the cached top and bottom sweeps, one row
+    per site and per horizontal bond, two rows per vertical bond, each row
+    absorbed into the cached boundary above it (its cost is sweep_macs of that
+    row; the bottom sweep mirrors the top one)."""
+    row = [sweep_macs(L, W, D, r + 1) - sweep_macs(L, W, D, r) for r in range(L)]
+    total = 2 * sum(row)
+    total += sum(W * row[r] for r in range(L))              # sites
+    total += sum((W - 1) * row[r] for r in range(L))        # horizontal bonds
+    total += sum(W * (row[r] + row[r + 1]) for r in range(L - 1))   # vertical bonds
+    return total
 
 
 def norm_all_cuts(L: int, W: int, D: int, A: np.ndarray):

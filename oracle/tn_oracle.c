@@ -135,9 +135,9 @@ static void absorb(const double *in, double *out, size_t P, int Dh, int Du,
  * tensor of some columns of the row (operator insertions); NULL entries mean
  * the grid's own tensor.  On return b holds the dn legs of row r.
  */
-static void absorb_row(const grid_t *g, int r, double *const *over, bnd_t *b) {
+static void absorb_row_part(const grid_t *g, int r, double *const *over, bnd_t *b, int ncols) {
     int W = g->W;
-    for (int c = 0; c < W; ++c) {
+    for (int c = 0; c < ncols; ++c) {
         const int *d = g->dim + 4 * (r * W + c);
         const double *T = (over && over[c]) ? over[c] : g->t[r * W + c];
         size_t P = 1, S = 1;
@@ -151,6 +151,10 @@ static void absorb_row(const grid_t *g, int r, double *const *over, bnd_t *b) {
         b->v = o; b->n = nout;
         rescale(b);
     }
+}
+
+static void absorb_row(const grid_t *g, int r, double *const *over, bnd_t *b) {
+    absorb_row_part(g, r, over, b, g->W);
 }
 
 static bnd_t bnd_one(void) {
@@ -304,6 +308,23 @@ int or_peps_norm_all_cuts(int L, int W, int D, const double *A, double *m, int64
     return 0;
 }
 
+/* The first nrows rows of the norm network, then the first ncols sites of row
+ * nrows, absorbed into the top boundary: a bounded timing sample of the row
+ * sweep.  Returns the boundary's first entry as (*m, *e) so the work is
+ * observable. */
+int or_peps_sweep_rows(int L, int W, int D, const double *A, int nrows, int ncols, double *m, int64_t *e) {
+    if (nrows < 0 || nrows > L || ncols < 0 || ncols > W || (nrows == L && ncols > 0)) return -1;
+    grid_t g = norm_grid(L, W, D, A);
+    bnd_t b = bnd_one();
+    for (int r = 0; r < nrows; ++r) absorb_row(&g, r, NULL, &b);
+    if (ncols > 0) absorb_row_part(&g, nrows, NULL, &b, ncols);
+    *m = b.v[0];
+    *e = b.e;
+    free(b.v);
+    grid_free(&g);
+    return 0;
+}
+
 /* Norm by the plain top-to-bottom row sweep. */
 int or_peps_norm(int L, int W, int D, const double *A, double *m, int64_t *e) {
     grid_t g = norm_grid(L, W, D, A);
@@ -325,7 +346,7 @@ static double ratio(double mo, int64_t eo, double mn, int64_t en) {
  *   norm_m, norm_e        the norm as mantissa * 2^exp
  *   sx[L*W]               <X_k> in row-major site order
  *   szsz[nb]              <Z_i Z_j>, horizontal bonds row-major, then vertical
- * Energy is assembled by the caller (or or_peps_energy).
+ * Energy is assembled by the caller.
  */
 int or_peps_observables(int L, int W, int D, const double *A,
                         double *norm_m, int64_t *norm_e, double *sx, double *szsz) {
@@ -494,18 +515,6 @@ int or_peps_bond_ops(int L, int W, int D, const double *A, int op_a, int op_b, d
 }
 
 /* E = -J sum <zz> - h sum <x>; also returns everything or_peps_observables does. */
-int or_peps_energy(int L, int W, int D, const double *A, double J, double h,
-                   double *norm_m, int64_t *norm_e, double *sx, double *szsz,
-                   double *energy) {
-    or_peps_observables(L, W, D, A, norm_m, norm_e, sx, szsz);
-    int nb = L * (W - 1) + W * (L - 1);
-    double szz = 0.0, sxx = 0.0;
-    for (int k = 0; k < nb; ++k) szz += szsz[k];
-    for (int k = 0; k < L * W; ++k) sxx += sx[k];
-    *energy = -J * szz - h * sxx;
-    return 0;
-}
-
 /*
  * One observable alone, keeping only two boundaries (for sampled checks of
  * lattices too large for the cached version).  op: 0 = norm (i, j ignored),

@@ -59,7 +59,7 @@ def test_energy_equals_hamiltonian_expectation(h):
     ob = oracle.observables(L, W, D, A)
     e_tn = ob.energy(1.0, h)
     e_h = brute.energy(L, W, D, A, 1.0, h)
-    assert abs(e_tn - e_h) <= 1e-12 * max(1.0, abs(e_h))
+    assert abs(e_tn - e_h) <= 1e-12 * abs(e_h)
 
 
 def test_energy_above_exact_ground_state():
@@ -382,3 +382,26 @@ def test_planner_auto_prefers_quadrant_on_squares():
         assert p["peak"] == (D * D) ** L
     p = planner.plan(4, 10, 2)
     assert p["peak"] == 4 ** 5       # thin lattices: sweep along the long side
+
+
+@pytest.mark.parametrize("L,W,D", [(4, 4, 2), (5, 3, 2), (3, 6, 3), (12, 12, 2), (8, 8, 3)])
+def test_sweep_macs_equal_row_scheme_macs(L, W, D):
+    """The multiply-adds the bench's CPU sample scales by: a full row sweep
+    counted site by site (oracle.sweep_macs) equals the summed multiply-adds
+    of the oracle planner's row-scheme chain (Fig. 2a, cut (L, W)), counted
+    from its own leg bookkeeping; a partial sweep lies strictly between."""
+    import oracle.planner as planner
+    full = oracle.sweep_macs(L, W, D, L)
+    assert full == sum(st["mac"] for st in planner.evaluate(L, W, D, 0, L, W)["steps"])
+    part = oracle.sweep_macs(L, W, D, 1, 2)
+    assert oracle.sweep_macs(L, W, D, 1) < part < full
+
+
+def test_sweep_rows_sample_matches_norm():
+    """A full sweep by sweep_rows is the norm; a partial one runs and returns."""
+    L, W, D = 4, 5, 2
+    A = inputs.random_lattice(L, W, D, 31)
+    assert oracle.sweep_rows(L, W, D, A, L) == oracle.norm(L, W, D, A)
+    oracle.sweep_rows(L, W, D, A, 2, 3)
+    with pytest.raises(ValueError):
+        oracle.sweep_rows(L, W, D, A, L, 1)
