@@ -168,3 +168,36 @@ def test_submit_needs_a_device(cpu_ctx):
     with pytest.raises(tn.TNError) as e:
         tn.tn_submit(cpu_ctx, 4, 4, 2, tn.TN_FP32, 1.0, 3.04, seed=1)
     assert e.value.status == tn.TN_ERR_NO_DEVICE
+
+
+@pytest.mark.parametrize("entry", ["tn_absorb", "tn_absorb_dot", "tn_absorb_dot_noalloc"])
+@pytest.mark.parametrize("P,S", [(2 ** 62, 2 ** 62), (2 ** 40, 2 ** 40), (2 ** 33, 2 ** 31), (1, 2 ** 63 - 1)])
+def test_kernel_entries_reject_overflowing_sizes(entry, P, S):
+    """Sizes whose product P * S (or P * 16 * S) would overflow int64 are rejected
+    before any product is formed or any device call is made (the dummy pointers
+    are never dereferenced)."""
+    fake = 0x1000
+    lib = tn.lib()
+    if entry == "tn_absorb":
+        st = lib.tn_absorb(1, tn.c_void_p(fake), tn.c_void_p(fake), tn.c_void_p(fake), P, 16, 16, S, None)
+    else:
+        st = getattr(lib, entry)(1, tn.c_void_p(fake), tn.c_void_p(fake), tn.c_void_p(fake), P, 16, 16, S,
+                                 tn.c_void_p(fake), None)
+    assert st == tn.TN_ERR_INVALID
+
+
+def test_noalloc_rejects_beyond_its_fixed_scratch():
+    fake = 0x1000
+    lib = tn.lib()
+    # 16,777,217 outer positions: one more than the 65,536 tiles of 256 positions
+    st = lib.tn_absorb_dot_noalloc(1, tn.c_void_p(fake), tn.c_void_p(fake), tn.c_void_p(fake), 16777217, 16, 16, 1,
+                                   tn.c_void_p(fake), None)
+    assert st == tn.TN_ERR_INVALID
+    assert "16777216" in lib.tn_last_error().decode()
+
+
+def test_inject_wait_timeout_arguments(cpu_ctx):
+    tn.tn_ctx_inject_wait_timeout(cpu_ctx, 0)
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_ctx_inject_wait_timeout(cpu_ctx, -1)
+    assert e.value.status == tn.TN_ERR_INVALID
