@@ -309,6 +309,20 @@ const char *tn_last_error(void);
  * cleanly (the context stays usable), 0 otherwise.  Allocates 8 bytes of
  * device memory for the call.  TN_ERR_INVALID for limit_ms outside (0, 10000]. */
 tn_status tn_wait_selfcheck(tn_ctx *ctx, double limit_ms, int *expired);
+/* Measured FMA rate of the context's device in TFLOP/s (no counterpart in the
+ * paper; the denominator of the ALU-bound roofline figures): dtype 0 = FP64
+ * fma, 1 = FP32 fma.rn.f32x2, 8 independent chains per thread, 2048 threads
+ * per SM, best of three launches timed with CUDA events on the context's
+ * stream.  Allocates 16 bytes of device memory for the call. */
+tn_status tn_peak_probe(tn_ctx *ctx, int dtype, double *tflops);
+/* Host-side fault injection (no counterpart in the paper; failure detection):
+ * the next `count` batch runs of this context -- served batches, tn_energy and
+ * the other blocking calls, tn_batch_run -- have their status word set after
+ * their kernels are queued, exactly as a bounded device wait that ran out
+ * would set it, so the error path (TN_ERR_TIMEOUT from tn_poll / tn_wait, the
+ * blocking calls and tn_batch_results_host) can be tested without disturbing
+ * any kernel.  count = 0 disarms.  TN_ERR_INVALID for count < 0. */
+tn_status tn_ctx_inject_wait_timeout(tn_ctx *ctx, int count);
 /* Per kernel family since the last reset: launches, summed device time (ms,
  * from CUDA events around each launch, only while profiling is on),
  * algorithmic bytes and multiply-adds.  family: 0 absorb (one step),

@@ -474,6 +474,14 @@ tn_status tn_batch_launch_count(const tn_batch* b, int64_t* n) {
 
 // ---------------------------------------------------------- kernel entry --
 
+namespace {
+// P * max(K, N) * S entries stay below 2^62 (checked without overflowing).
+bool sizes_fit(int64_t P, int32_t K, int32_t N, int64_t S) {
+    const int64_t cap = int64_t(1) << 62, kn = K > N ? K : N;
+    return P <= cap / S && P * S <= cap / kn;
+}
+}  // namespace
+
 tn_status tn_absorb(int dtype, const void* in, const void* E, void* out, int64_t P, int32_t K, int32_t N,
                     int64_t S, void* stream) {
     if ((dtype != 0 && dtype != 1) || !in || !E || !out || P <= 0 || K <= 0 || N <= 0 || S <= 0) {
@@ -481,6 +489,7 @@ tn_status tn_absorb(int dtype, const void* in, const void* E, void* out, int64_t
         return TN_ERR_INVALID;
     }
     if (!absorb_has_fast_path(K, N)) { set_error("K, N must be in {1, 4, 16} or {1, 9, 81}"); return TN_ERR_INVALID; }
+    if (!sizes_fit(P, K, N, S)) { set_error("P * max(K, N) * S exceeds 2^62 entries"); return TN_ERR_INVALID; }
     return cuda_status(launch_absorb_plain(dtype, in, E, out, P, K, N, S, static_cast<cudaStream_t>(stream)),
                        "absorb launch");
 }
@@ -492,6 +501,7 @@ tn_status tn_absorb_dot(int dtype, const void* in, const void* E, const void* ad
         return TN_ERR_INVALID;
     }
     if (!absorb_has_fast_path(K, N)) { set_error("K, N must be in {1, 4, 16} or {1, 9, 81}"); return TN_ERR_INVALID; }
+    if (!sizes_fit(P, K, N, S)) { set_error("P * max(K, N) * S exceeds 2^62 entries"); return TN_ERR_INVALID; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long tiles = absorb_tiles(P, S, K, N);
     if (tiles > INT32_MAX) { set_error("too many tiles"); return TN_ERR_INVALID; }
@@ -540,6 +550,51 @@ tn_status tn_wait_selfcheck(tn_ctx* ctx, double limit_ms, int* expired) {
     *expired = (h[0] == 0 && h[1] == 1) ? 1 : 0;
     return TN_OK;
     TN_GUARD_END
+}
+
+tn_status tn_peak_probe(tn_ctx* ctx, int dtype, double* tflops) {
+    TN_GUARD_BEGIN
+    if (!ctx || !tflops || (dtype != 0 && dtype != 1)) return TN_ERR_INVALID;
+    if (ctx->device < 0) { set_error("context has no device"); return TN_ERR_NO_DEVICE; }
+    cudaSetDevice(ctx->device);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || sms <= 0)
+        return cuda_status(cudaGetLastError(), "SM count");
+    const long long blocks = 8LL * sms;   // 2048 threads per SM
+    // FP64 runs far slower on this part: fewer rounds keep each launch near 0.1-0.3 s
+    const long long iters = dtype == 0 ? (1LL << 13) : (1LL << 17);
+    const double fmas_per_round = dtype == 0 ? 8.0 : 16.0;
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 16);
+    if (e != cudaSuccess) return cuda_status(e, "probe allocation");
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 0.0f;
+    e = launch_fma_probe(dtype, d, blocks, iters / 8, ctx->stream);   // warm-up
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(a, ctx->stream);
+        e = launch_fma_probe(dtype, d, blocks, iters, ctx->stream);
+        cudaEventRecord(b, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && (best == 0.0f || ms < best)) best = ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_status(e, "probe");
+    const double flops = 2.0 * fmas_per_round * (double)iters * (double)blocks * 256.0;
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return TN_OK;
+    TN_GUARD_END
+}
+
+tn_status tn_ctx_inject_wait_timeout(tn_ctx* ctx, int count) {
+    if (!ctx || count < 0) return TN_ERR_INVALID;
+    ctx->inject_timeouts.store(count);
+    return TN_OK;
 }
 
 tn_status tn_ctx_kernel_stats(tn_ctx* ctx, int family, int64_t* launches, double* ms, double* bytes, double* macs) {

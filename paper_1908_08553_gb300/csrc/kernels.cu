@@ -1549,6 +1549,58 @@ cudaError_t launch_wait_probe(const int* flag, long long limit_cycles, int* stat
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ FMA probe --
+
+// Device FMA rate (the roofline denominator of the ALU-bound kernels): every
+// thread runs 8 independent FMA chains for `iters` rounds; the chains contract
+// toward a fixed point, so values stay finite, and the sum is stored so the
+// compiler keeps every FMA.  FP32 uses the paired fma.rn.f32x2 the library's
+// FP32 kernels use (2 FMAs per instruction).
+__global__ void __launch_bounds__(256) k_fma_probe_f64(double* out, long long iters, double x, double y) {
+    double a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = 0.5 + 0.01 * i + 1e-3 * threadIdx.x;
+    for (long long k = 0; k < iters; ++k) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = fma(a[i], x, y);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += a[i];
+    if (s == 12345.678) out[0] = s;   // never true; keeps the chains live
+}
+
+__global__ void __launch_bounds__(256) k_fma_probe_f32(float* out, long long iters, float x, float y) {
+    unsigned long long a[8];
+    const unsigned long long xx = f2_pack(x, x), yy = f2_pack(y, y);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = f2_pack(0.5f + 0.01f * i, 0.25f + 1e-3f * threadIdx.x);
+    for (long long k = 0; k < iters; ++k) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            unsigned long long acc = yy;
+            asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a[i]), "l"(xx));
+            a[i] = acc;
+        }
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float lo, hi;
+        f2_unpack(a[i], lo, hi);
+        s += lo + hi;
+    }
+    if (s == 12345.678f) out[0] = s;
+}
+
+cudaError_t launch_fma_probe(int dt, void* out, long long blocks, long long iters, cudaStream_t st) {
+    if (dt == 0)
+        k_fma_probe_f64<<<(unsigned)blocks, 256, 0, st>>>(static_cast<double*>(out), iters, 0.999999, 1e-6);
+    else
+        k_fma_probe_f32<<<(unsigned)blocks, 256, 0, st>>>(static_cast<float*>(out), iters, 0.999f, 1e-3f);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- init ------
 
 __global__ void k_init(Slot* slots, long long nslots, const ConstOne* ones, int nones, int dt) {

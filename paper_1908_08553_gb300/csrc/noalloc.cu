@@ -63,10 +63,16 @@ extern "C" tn_status tn_absorb_dot_noalloc(int dtype, const void* in, const void
         tn::set_error("K, N must be in {1, 4, 16} or {1, 9, 81}");
         return TN_ERR_INVALID;
     }
+    // compare without forming P * S, which could overflow for huge arguments
+    constexpr long long kMaxOuter = kNoAllocMaxTiles * tn::kAbsorbThreads;   // 16,777,216
+    if (P > kMaxOuter / S) {
+        tn::set_error("P = " + std::to_string((long long)P) + ", S = " + std::to_string((long long)S) +
+                      ": P*S exceeds the 16777216 outer positions the fixed scratch holds");
+        return TN_ERR_INVALID;
+    }
     const long long tiles = tn::absorb_tiles(P, S, K, N);
     if (tiles > kNoAllocMaxTiles) {
-        tn::set_error("P*S = " + std::to_string((long long)P * S) +
-                      " needs more tiles than the fixed scratch holds (P*S must be <= 16777216)");
+        tn::set_error("more tiles than the fixed scratch holds");
         return TN_ERR_INVALID;
     }
     void* scratch = nullptr;

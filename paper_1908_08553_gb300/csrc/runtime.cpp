@@ -584,7 +584,27 @@ cudaError_t issue(tn_batch* b, cudaStream_t st, std::vector<std::pair<cudaEvent_
 
 }  // namespace
 
+tn_status batch_run_plain(tn_batch* b, cudaStream_t st);
+
+namespace {
+// Host-side fault injection: mark this run's status word as if a bounded
+// device wait had run out (no kernel is disturbed; tn_ctx_inject_wait_timeout).
+tn_status inject_after_run(tn_batch* b, cudaStream_t st, tn_status s) {
+    tn_ctx* ctx = b->ctx;
+    if (s != TN_OK) return s;
+    int v = ctx->inject_timeouts.load();
+    while (v > 0 && !ctx->inject_timeouts.compare_exchange_weak(v, v - 1)) {
+    }
+    if (v <= 0) return s;
+    return cuda_status(cudaMemsetAsync(b->buf + b->lay.status_off, 1, 1, st), "injected status");
+}
+}  // namespace
+
 tn_status batch_run(tn_batch* b, cudaStream_t st) {
+    return inject_after_run(b, st, batch_run_plain(b, st));
+}
+
+tn_status batch_run_plain(tn_batch* b, cudaStream_t st) {
     tn_ctx* ctx = b->ctx;
     cudaSetDevice(ctx->device);
     // the fields of the final step (J, h) change between runs: refresh them

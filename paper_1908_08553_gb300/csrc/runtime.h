@@ -66,6 +66,7 @@ struct tn_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     bool profiling = false;
+    std::atomic<int> inject_timeouts{0};   // host-side fault injection (tn_ctx_inject_wait_timeout)
     tn::KStat stats[tn::kFamilies];
     std::mutex mu;          // guards stats and the server
     tn::Server* server = nullptr;

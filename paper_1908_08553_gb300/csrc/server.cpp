@@ -77,10 +77,17 @@ void Server::retire_locked() {
         const cudaError_t q = cudaEventQuery(it->done);
         if (q == cudaErrorNotReady) { ++it; continue; }
         const double* r = pinned[it->slot];
+        // the batch's status word rides behind its results: nonzero when a
+        // bounded wait inside one of its kernels ran out (the results are then
+        // incomplete), so every job of the batch reports the timeout
+        int wait_status = 0;
+        if (q == cudaSuccess) std::memcpy(&wait_status, r + it->b->lay.nres, sizeof(int));
         for (size_t k = 0; k < it->jobs.size(); ++k) {
             SJob* j = it->jobs[k];
             const Member& mb = it->b->m[k];
-            if (q == cudaSuccess) {
+            if (q == cudaSuccess && wait_status) {
+                j->status = TN_ERR_TIMEOUT;
+            } else if (q == cudaSuccess) {
                 j->result.assign(r + mb.res_off, r + mb.res_off + mb.res_elems);
                 j->status = TN_OK;
             } else {
@@ -141,17 +148,22 @@ bool Server::admit(std::unique_lock<std::mutex>& lk) {
         st = cuda_status(cudaMemcpyAsync(b->buf + b->lay.in_off, in.data(), in.size() * 8,
                                          cudaMemcpyHostToDevice, b->stream), "served upload");
         if (st == TN_OK) st = batch_run(b, b->stream);
-        if (st == TN_OK && pinned_n[slot] < (size_t)b->lay.nres) {
+        // read-back buffer: the results, then one double holding the status word
+        const size_t need = (size_t)b->lay.nres + 1;
+        if (st == TN_OK && pinned_n[slot] < need) {
             // the slot is idle, so its old buffer is not in use
             if (pinned[slot]) cudaFreeHost(pinned[slot]);
             pinned[slot] = nullptr;
-            const size_t n = std::max((size_t)b->lay.nres, pinned_n[slot] * 2);
+            const size_t n = std::max(need, pinned_n[slot] * 2);
             st = cuda_status(cudaMallocHost(reinterpret_cast<void**>(&pinned[slot]), n * 8), "pinned buffer");
             pinned_n[slot] = st == TN_OK ? n : 0;
         }
         if (st == TN_OK)
             st = cuda_status(cudaMemcpyAsync(pinned[slot], b->buf + b->lay.res_off, (size_t)b->lay.nres * 8,
                                              cudaMemcpyDeviceToHost, b->stream), "served read-back");
+        if (st == TN_OK)
+            st = cuda_status(cudaMemcpyAsync(pinned[slot] + b->lay.nres, b->buf + b->lay.status_off, sizeof(int),
+                                             cudaMemcpyDeviceToHost, b->stream), "served status read-back");
         if (st == TN_OK) st = cuda_status(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
         if (st == TN_OK) st = cuda_status(cudaEventRecord(ev, b->stream), "event record");
     }

@@ -164,6 +164,9 @@ long long gemm_ksplit(int variant, bool dot, long long K);
 // Bounded-wait self-check: one thread waits on *flag (never set by the
 // library) for at most limit_cycles, then sets *status to 1.
 cudaError_t launch_wait_probe(const int* flag, long long limit_cycles, int* status, cudaStream_t st);
+// FMA-rate probe: `blocks` blocks of 256 threads, 8 FMA chains x iters each
+// (dt 0: FP64 fma; 1: FP32 fma.rn.f32x2, 16 FMAs per round).
+cudaError_t launch_fma_probe(int dt, void* out, long long blocks, long long iters, cudaStream_t st);
 cudaError_t launch_dot(int dt, const DotTask* tasks, int ntasks, long long nblocks, Slot* slots,
                        cudaStream_t st, const int* tmap = nullptr);
 cudaError_t launch_sitemat(int dt, const SiteMatTask* tasks, int ntasks, Slot* slots,

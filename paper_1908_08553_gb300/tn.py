@@ -85,6 +85,8 @@ SIGNATURES = {
     "tn_status_string": (c_char_p, [c_int]),
     "tn_last_error": (c_char_p, []),
     "tn_ctx_set_profiling": (c_int, [c_void_p, c_int]),
+    "tn_ctx_inject_wait_timeout": (c_int, [c_void_p, c_int]),
+    "tn_peak_probe": (c_int, [c_void_p, c_int, POINTER(c_double)]),
     "tn_ctx_kernel_stats": (c_int, [c_void_p, c_int, POINTER(c_int64), POINTER(c_double), POINTER(c_double),
                                     POINTER(c_double)]),
 }
@@ -383,6 +385,18 @@ def tn_absorb_dot_noalloc(dtype: int, x_in, E, adj, P: int, K: int, N: int, S: i
 
 def tn_ctx_set_profiling(ctx, on: bool):
     check(lib().tn_ctx_set_profiling(ctx, 1 if on else 0), "tn_ctx_set_profiling")
+
+
+def tn_peak_probe(ctx, dtype: int) -> float:
+    """Measured FMA rate of the device in TFLOP/s (dtype 0 FP64, 1 FP32)."""
+    v = c_double()
+    check(lib().tn_peak_probe(ctx, dtype, byref(v)), "tn_peak_probe")
+    return v.value
+
+
+def tn_ctx_inject_wait_timeout(ctx, count: int):
+    """Mark the next `count` batch runs as if a bounded device wait had run out."""
+    check(lib().tn_ctx_inject_wait_timeout(ctx, count), "tn_ctx_inject_wait_timeout")
 
 
 def tn_ctx_kernel_stats(ctx, family: int):
