@@ -661,6 +661,135 @@ k_absorb_generic(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restr
     }
 }
 
+// ---- interior D = 3 step as a ket pass and a bra pass (FP32 / FP64) ----------
+//
+// The double-layer matrix of an interior D = 3 step is E = sum_p Fa_p (x) Fb_p
+// over the physical index (Sec. 5: the bra and ket layers of the norm), so one
+// outer position's 81 outputs follow from its 81 inputs in two passes,
+//   T[p][i_b][o_a] = sum_{i_a} in[(i_a, i_b)] Fa[p][i_a][o_a]
+//   out[(o_a, o_b)] = sum_{p, i_b} T[p][i_b][o_a] Fb[p][i_b][o_b]
+// with 2 x 1458 multiply-adds instead of 81 x 81 = 6561.  (i, o) pairs index
+// the double-layer legs: the 81 inputs are ordered (x_a, x_b, y_a, y_b) for
+// the two legs (x, y) of the input side, i_a = (x_a, y_a), i_b = (x_b, y_b);
+// the outputs likewise.  The backward sweep (transE) swaps the factors' in
+// and out legs.  One outer position per thread; the factors live in shared
+// memory as [p][in][out], each output row of Fb read as one broadcast; FP64
+// keeps a thread's inputs in shared memory (FP64 multiply-adds are the limit
+// there, not shared-memory traffic), FP32 in registers.
+__device__ __forceinline__ constexpr int dl_index(int a, int b) {
+    return (a / 3) * 27 + (b / 3) * 9 + (a % 3) * 3 + (b % 3);
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kTwoPassThreads)
+k_absorb_2pass(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots,
+               const int* __restrict__ tmap) {
+    constexpr bool kInSmem = sizeof(T) == 8;
+    __shared__ T Fa[2][9][9], Fb[2][9][9];
+    __shared__ double red[32];
+    extern __shared__ __align__(16) unsigned char smem_raw[];   // FP64: 81 inputs per thread
+    const long long tile = blockIdx.x;
+    const AbsorbTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
+    const T* F = static_cast<const T*>(t.E);
+    for (int idx = threadIdx.x; idx < 2 * 162; idx += blockDim.x) {
+        const int half = idx / 162, rem = idx - half * 162;
+        const int p = rem / 81, io = rem - p * 81, i = io / 9, o = io - i * 9;
+        // forward: [p][in = (h u)][out = (dn rt)]; backward: in and out swap
+        const T v = F[idx];
+        if (half == 0) { if (t.transE) Fa[p][o][i] = v; else Fa[p][i][o] = v; }
+        else { if (t.transE) Fb[p][o][i] = v; else Fb[p][i][o] = v; }
+    }
+    int e_in = slot_shift(&slots[t.slot_in]), e_adj = 0;
+    const T sc_in = pow2<T>(-e_in);
+    T sc_adj = T(1);
+    if (MODE == 2) { e_adj = slot_shift(&slots[t.slot_adj]); sc_adj = pow2<T>(-e_adj); }
+    __syncthreads();
+    const long long S = t.S;
+    const long long local = tile - t.tile0;
+    const long long o = local * kTwoPassThreads + threadIdx.x;
+    double lmax = 0.0;
+    CSum<T> dacc;
+    if (o < t.P * S) {
+        const long long p0 = o / S, s = o - p0 * S;
+        const T* in = static_cast<const T*>(t.in) + p0 * 81 * S + s;
+        T xr[kInSmem ? 1 : 81];
+        T* xs = reinterpret_cast<T*>(smem_raw) + threadIdx.x;   // column of this thread, stride blockDim
+        auto X = [&](int k) -> T& { if constexpr (kInSmem) return xs[k * kTwoPassThreads]; else return xr[k]; };
+#pragma unroll
+        for (int k = 0; k < 81; ++k) X(k) = in[k * S] * sc_in;
+        T* out = MODE == 1 ? static_cast<T*>(t.out) + p0 * 81 * S + s : nullptr;
+        const T* adj = MODE == 2 ? static_cast<const T*>(t.adj) + p0 * 81 * S + s : nullptr;
+        T m = T(0);
+#pragma unroll 1
+        for (int oa = 0; oa < 9; ++oa) {
+            T tt[2][9];
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+                for (int ib = 0; ib < 9; ++ib) tt[p][ib] = T(0);
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+                for (int ia = 0; ia < 9; ++ia) {
+                    const T f = Fa[p][ia][oa];
+#pragma unroll
+                    for (int ib = 0; ib < 9; ++ib) tt[p][ib] = fma(X(dl_index(ia, ib)), f, tt[p][ib]);
+                }
+            T y[9];
+#pragma unroll
+            for (int ob = 0; ob < 9; ++ob) y[ob] = T(0);
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+                for (int ib = 0; ib < 9; ++ib) {
+                    const T tv = tt[p][ib];
+#pragma unroll
+                    for (int ob = 0; ob < 9; ++ob) y[ob] = fma(tv, Fb[p][ib][ob], y[ob]);
+                }
+            // output n = (oa, ob) sits at (oa / 3) * 27 + (oa % 3) * 3 + (ob / 3) * 9 + ob % 3
+            const long long nb = (long long)((oa / 3) * 27 + (oa % 3) * 3) * S;
+            if (MODE == 1) {
+#pragma unroll
+                for (int ob = 0; ob < 9; ++ob) {
+                    out[nb + ((ob / 3) * 9 + ob % 3) * S] = y[ob];
+                    m = fmax(m, fabs(y[ob]));
+                }
+            } else {
+                T part = T(0);
+#pragma unroll
+                for (int ob = 0; ob < 9; ++ob) part = fma(y[ob], __ldg(adj + nb + ((ob / 3) * 9 + ob % 3) * S), part);
+                dacc.add(part * sc_adj);
+            }
+        }
+        lmax = (double)m;
+    }
+    if (MODE == 1) {
+        const double mx = block_max(lmax, red);
+        if (threadIdx.x == 0) {
+            record_max(&slots[t.slot_out], mx);
+            if (local == 0) slots[t.slot_out].X = slots[t.slot_in].X + e_in + slots[t.slot_E].X;
+        }
+    } else {
+        const double part = block_sum((double)dacc.value(), red);
+        const long long X = slots[t.slot_in].X + e_in + slots[t.slot_E].X + slots[t.slot_adj].X + e_adj;
+        finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_out], X, red);
+    }
+}
+
+long long absorb_2pass_tiles(long long P, long long S) { return (P * S + kTwoPassThreads - 1) / kTwoPassThreads; }
+
+namespace {
+template <typename T, int MODE>
+cudaError_t launch_2pass_t(const AbsorbTask* tasks, int ntasks, long long nblocks, Slot* slots, cudaStream_t st,
+                           const int* tmap) {
+    const size_t smem = sizeof(T) == 8 ? (size_t)81 * kTwoPassThreads * sizeof(T) : 0;
+    auto fn = k_absorb_2pass<T, MODE>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    fn<<<(unsigned)nblocks, kTwoPassThreads, smem, st>>>(tasks, ntasks, slots, tmap);
+    return cudaGetLastError();
+}
+}  // namespace
+
 // ---- two consecutive steps of one frame row in one pass (FP32, D = 2) ------
 //
 // Step c maps [P][K1 = (h, u_c)][U = u_{c+1}][S2] (K1 = 4 on a frame row's
@@ -960,6 +1089,13 @@ cudaError_t launch_absorb(int dt, bool dot, int K, int N, const AbsorbTask* task
     if (variant == 12) return absorb4_dispatch<4, true>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
     if (variant == 21) return absorb4_dispatch<5, false>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
     if (variant == 22) return absorb4_dispatch<5, true>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
+    if (variant == kAbsorbTwoPass) {
+        if (dt == 0)
+            return dot ? launch_2pass_t<double, 2>(tasks, ntasks, nblocks, slots, st, tmap)
+                       : launch_2pass_t<double, 1>(tasks, ntasks, nblocks, slots, st, tmap);
+        return dot ? launch_2pass_t<float, 2>(tasks, ntasks, nblocks, slots, st, tmap)
+                   : launch_2pass_t<float, 1>(tasks, ntasks, nblocks, slots, st, tmap);
+    }
     if (dt == 0)
         return dot ? absorb_dispatch<double, 2>(K, N, tasks, ntasks, nblocks, slots, st, tmap)
                    : absorb_dispatch<double, 1>(K, N, tasks, ntasks, nblocks, slots, st, tmap);
@@ -1500,6 +1636,26 @@ k_sitemat(const SiteMatTask* __restrict__ tasks, int ntasks, Slot* __restrict__ 
     // shapes are checked on the host; never read outside A if they disagree
     const bool shape_ok = (K == fl * fl * fu * fu) && (N == fd * fd * fr * fr);
     const long long stride_p = (long long)dm[0] * dm[1] * dm[2] * dm[3];
+    if (t.factored) {
+        // the two layer factors (kFactorEntries): [Fa | Fb], each [p][(h u)][(dn rt)]
+        const double sa = ldexp(1.0, -eA);
+        const bool f_ok = shape_ok && fu == 3 && fl == 3 && fd == 3 && fr == 3;
+        for (int idx = lane; idx < kFactorEntries; idx += 32) {
+            const int half = idx / 162, rem = idx - half * 162;
+            const int p = rem / 81, io = rem - p * 81;
+            const int i = io / 9, o = io - i * 9;            // (h u), (dn rt)
+            int v[4];
+            v[t.map[0]] = i % 3; v[t.map[1]] = i / 3; v[t.map[2]] = o / 3; v[t.map[3]] = o % 3;
+            if (!f_ok) { E[idx] = T(0); continue; }
+            const long long ia = ((long long)(v[0] * dm[1] + v[1]) * dm[2] + v[2]) * dm[3] + v[3];
+            const double a0 = t.A[ia], a1 = t.A[stride_p + ia];
+            double val;
+            if (half == 0) val = p == 0 ? a0 : a1;
+            else val = p == 0 ? (o00 * a0 + o01 * a1) : (o10 * a0 + o11 * a1);
+            E[idx] = (T)(val * sa);
+        }
+        return;
+    }
     for (int idx = lane; idx < K * N; idx += 32) {
         const int k = idx / N, n = idx - k * N;
         const int uu = k % (fu * fu), hh = k / (fu * fu);

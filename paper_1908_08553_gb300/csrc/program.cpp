@@ -76,11 +76,16 @@ public:
         auto key = std::make_pair(site, phys);
         auto it = E_.find(key);
         if (it != E_.end()) return it->second;
-        const int e = tensor((int64_t)s.K * s.N, 0);
+        // interior D = 3 steps off the tensor cores: keep the two layer factors
+        // (Sec. 5, bra and ket layers) and absorb them one after the other
+        const bool factored = pg_.nsplit == 0 && s.K == 81 && s.N == 81;
+        const int e = tensor(factored ? (int64_t)kFactorEntries : (int64_t)s.K * s.N, 0);
+        pg_.tensors[e].factored = factored;
         Op op;
         op.kind = OP_SITEMAT;
         op.level = 0;
         op.out = e;
+        op.factored = factored;
         op.site = site;
         op.phys = phys;
         op.K = s.K;
@@ -91,7 +96,7 @@ public:
         const int fu = op.fdim[0], fl = op.fdim[1], fd = op.fdim[2], fr = op.fdim[3];
         if (s.K != fl * fl * fu * fu || s.N != fd * fd * fr * fr)
             throw std::logic_error("site matrix shape does not match its chain step");
-        op.bytes = (double)s.K * s.N * pg_.esize;
+        op.bytes = (double)pg_.tensors[e].n * pg_.esize;
         add(op);
         E_[key] = e;
         return e;
@@ -116,8 +121,10 @@ public:
         op.transE = trans;
         // wide double-layer steps (D = 3 interior, K = N = 81) go to the tensor cores
         if (pg_.nsplit && op.K == 81 && op.N == 81) op.nsplit = pg_.nsplit;
+        op.factored = pg_.tensors[E].factored;
         op.bytes = (double)(s.n_in + s.n_out) * pg_.esize;
-        op.macs = (double)s.mac;
+        // the factored form does 2 x 2 x 9^3 multiply-adds per outer position instead of 81^2
+        op.macs = op.factored ? (double)s.P * s.S * 2916.0 : (double)s.mac;
         use(in, level); use(E, level);
         add(op);
         return out;
@@ -133,8 +140,9 @@ public:
         op.in = in; op.E = E; op.adj = adj; op.out = out;
         op.P = s.P; op.S = s.S; op.K = s.K; op.N = s.N;
         if (pg_.nsplit && op.K == 81 && op.N == 81) op.nsplit = pg_.nsplit;
+        op.factored = pg_.tensors[E].factored;
         op.bytes = (double)(s.n_in + s.n_out) * pg_.esize;
-        op.macs = (double)s.mac + (double)s.n_out;
+        op.macs = (op.factored ? (double)s.P * s.S * 2916.0 : (double)s.mac) + (double)s.n_out;
         use(in, level); use(E, level); use(adj, level);
         add(op);
         return out;
@@ -441,9 +449,15 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
             for (int t = T; t >= 2; --t) G[q][t - 1] = bd.absorb(G[q][t], E_at(q, t, PH_I), step_of(q, t), true);
         }
         // norm along each step's path: <F[q][t], G[q][t]> (from the site's triple
-        // absorb-dot where the streaming kernel serves the step, else a dot)
+        // absorb-dot where the streaming kernel serves the step, else a dot).
+        // Dividing by it cancels the rounding the numerator shares with it;
+        // FP64 has no rounding worth cancelling at the library's tolerance, so
+        // there every ratio takes the ring's norm and the extra dots and ring
+        // products of the path norms are not built.
+        const bool path_norms = pg.dt != DT_F64;
         std::map<std::pair<int, int>, int> local_norm;
         auto norm_at = [&](int q, int t) {
+            if (!path_norms) return pg.norm_slot;
             auto key = std::make_pair(q, t);
             auto it = local_norm.find(key);
             if (it != local_norm.end()) return it->second;
@@ -558,23 +572,27 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
                 // product on the unmodified corners (the norm through the same path)
                 if (qa == TL && qb == TR) {
                     v = bd.gemm(Mbot, Zb, hbL, vrT, hbR, hbR, 1, vrT, 1, Za);
+                    if (!path_norms) den_cross[0] = pg.norm_slot;
                     if (den_cross[0] < 0)
                         den_cross[0] = pg.tensors[bd.gemm(Mbot, Qt[TR], hbL, vrT, hbR, hbR, 1, vrT, 1, Qt[TL])].slot;
                     pg.zz_den[bi] = den_cross[0];
                 } else if (qa == BL && qb == BR) {
                     v = bd.gemm(Mtop, Zb, hbL, vrB, hbR, hbR, 1, vrB, 1, Za);
+                    if (!path_norms) den_cross[1] = pg.norm_slot;
                     if (den_cross[1] < 0)
                         den_cross[1] = pg.tensors[bd.gemm(Mtop, Qt[BR], hbL, vrB, hbR, hbR, 1, vrB, 1, Qt[BL])].slot;
                     pg.zz_den[bi] = den_cross[1];
                 } else if (qa == TL && qb == BL) {
                     if (Xr < 0) Xr = bd.gemm(Qt[TR], Qt[BR], vrT, vrB, hbR, 1, vrT, vrB, 1);
                     v = bd.gemm(Za, Zb, vrT, vrB, hbL, 1, vrT, vrB, 1, Xr);
+                    if (!path_norms) den_cross[2] = pg.norm_slot;
                     if (den_cross[2] < 0)
                         den_cross[2] = pg.tensors[bd.gemm(Qt[TL], Qt[BL], vrT, vrB, hbL, 1, vrT, vrB, 1, Xr)].slot;
                     pg.zz_den[bi] = den_cross[2];
                 } else if (qa == TR && qb == BR) {
                     if (Xl < 0) Xl = bd.gemm(Qt[TL], Qt[BL], vrT, vrB, hbL, 1, vrT, vrB, 1);
                     v = bd.gemm(Za, Zb, vrT, vrB, hbR, 1, vrT, vrB, 1, Xl);
+                    if (!path_norms) den_cross[3] = pg.norm_slot;
                     if (den_cross[3] < 0)
                         den_cross[3] = pg.tensors[bd.gemm(Qt[TR], Qt[BR], vrT, vrB, hbR, 1, vrT, vrB, 1, Xl)].slot;
                     pg.zz_den[bi] = den_cross[3];

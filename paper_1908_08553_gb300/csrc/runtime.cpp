@@ -43,6 +43,7 @@ int family_of(int kind) {
 // Build every launch and its task table.  With base == nullptr only sizes are
 // computed (footprint); otherwise task structs hold absolute device pointers.
 long long absorb_tiles_any(int var, long long P, long long S, int K, int N) {
+    if (var == kAbsorbTwoPass) return absorb_2pass_tiles(P, S);
     if (var >= 20) return absorb_tiles_v(var - 20, P, S, K, N);   // triple dot of variants 1 / 2
     if (var >= 10) return absorb_tiles_v(var - 10, P, S, K, N);   // dual dot of variants 1 / 2
     if (var >= 3) return tc_absorb_tiles(P, S);
@@ -87,6 +88,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 var = op.nsplit ? 1 + op.nsplit : absorb_variant(b->dt, op.P, op.S, op.K, op.N);
                 if (op.E3 >= 0) var += 20;
                 else if (op.E2 >= 0) var += 10;
+                if (op.factored) var = kAbsorbTwoPass;   // 30: ket pass then bra pass (D = 3)
             } else if (op.kind == OP_ABSORB2 || op.kind == OP_ABSORB2_DOT) {
                 K = op.K; N = op.N;
             } else if (op.kind == OP_GEMM || op.kind == OP_GEMM_DOT) {
@@ -192,6 +194,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 t.phys = op.phys;
                 t.slot_E = slot_of(r.member, op.out);
                 t.K = op.K; t.N = op.N;
+                t.factored = op.factored ? 1 : 0;
                 off = append(&t, sizeof(t));
                 tile += 1;
             } else if (kind == OP_ABSORB || kind == OP_ABSORB_DOT) {
@@ -338,7 +341,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         L.nblocks = tile;
         // block -> task table for launches of many short blocks (saves each
         // block a dependent binary search over the task list)
-        const bool mapped = ((kind == OP_ABSORB || kind == OP_ABSORB_DOT) && (L.variant <= 2 || L.variant >= 10)) ||
+        const bool mapped = ((kind == OP_ABSORB || kind == OP_ABSORB_DOT) && (L.variant <= 2 || L.variant >= 10)) ||   // SIMT variants
                             kind == OP_DOT || kind == OP_ABSORB2 || kind == OP_ABSORB2_DOT;
         if (mapped && L.ntasks > 8) {
             tasks.resize((tasks.size() + 15) / 16 * 16);

@@ -95,6 +95,7 @@ struct Tensor {
     bool is_const_one = false;
     bool is_site = false;    // raw FP64 site tensor (lattice input), offset into the input area
     int site = -1;
+    bool factored = false;   // site matrix kept as its two layer factors (interior D = 3 steps)
 };
 
 struct Op {
@@ -114,6 +115,7 @@ struct Op {
     // tensor cores: source tensors of the split operands (their slots carry the scale)
     int A_src = -1, B_src = -1;
     int nsplit = 0;               // tensor cores: 2 or 3 split planes (products and D=3 absorption)
+    bool factored = false;        // sitemat: write the layer factors; absorb: ket pass then bra pass
     long long Rp = 0, Kp = 0;
     // sitemat
     int site = -1, phys = PH_I;

@@ -85,7 +85,15 @@ struct SiteMatTask {
     int phys;             // 0 I, 1 X, 2 Z
     int slot_E;
     int K, N;
+    int factored;         // 1: the two layer factors of the double-layer matrix (kFactorEntries)
 };
+
+// Interior D = 3 steps (K = N = 81, every frame leg of dimension 3) keep the
+// double-layer site matrix as its two layer factors, 2 x 9 x 9 entries each:
+//   Fa[p][(h u)][(dn rt)] = A[p](frame legs of layer a) 2^-e_A
+//   Fb[p][(h u)][(dn rt)] = sum_q O[p][q] A[q](frame legs of layer b) 2^-e_A
+// so that E[(h_a h_b)(u_a u_b)][(dn_a dn_b)(rt_a rt_b)] = sum_p Fa Fb.
+constexpr int kFactorEntries = 4 * 81;
 
 // Result header per member: E, log2 norm, norm mantissa, norm exponent,
 // sum <X>, sum <ZZ>; then <X_k> and <Z_i Z_j>.
@@ -207,5 +215,9 @@ constexpr int kGemmTile = 64;
 constexpr int kDotPerBlock = 4096;
 long long absorb_tiles(long long P, long long S, int K, int N);
 bool absorb_has_fast_path(int K, int N);
+// Variant of the factored D = 3 interior absorption (ket layer, then bra layer).
+constexpr int kAbsorbTwoPass = 30;
+constexpr int kTwoPassThreads = 128;
+long long absorb_2pass_tiles(long long P, long long S);
 
 }  // namespace tn
