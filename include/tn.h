@@ -297,6 +297,50 @@ tn_status tn_absorb_dot_noalloc(int dtype, const void *in, const void *E, const 
                                 int64_t P, int32_t K, int32_t N, int64_t S, double *result,
                                 void *stream);
 
+/* ------------------------------------------- imaginary time evolution --- */
+
+/* Parameters of an imaginary time evolution (Sec. 5): H = -J sum_<ij> Z_i Z_j
+ * - gamma sum_k X_k, steps of U(dtau) = U^Gamma(dtau/2) U^J(dtau) U^Gamma(dtau/2)
+ * (second-order Trotter-Suzuki).  A two-site update keeps the singular values
+ * with lambda_k / lambda_1 >= eps (Sec. 6), at most chi_max of them; chi_max
+ * must equal the lattice's bond dimension D, which is the storage dimension
+ * of every bond (bonds with fewer kept values are zero-padded, which leaves
+ * the state unchanged).  energy_every > 0 evaluates E by the exact
+ * contraction, in `precision`, after every energy_every-th step. */
+typedef struct {
+    double J, gamma, dtau;
+    int steps;
+    int chi_max;
+    double eps;
+    int energy_every;
+    int precision;        /* tn_precision of the energy evaluations */
+} tn_ite_params;
+
+/* Set the lattice to the initial state of Sec. 5, the uniform superposition
+ * prod_k (|+1> + |-1>) / sqrt 2: every site A[p][0][0][0][0] = 1/sqrt 2, all
+ * other entries (the padding of bonds of dimension 1) zero. */
+tn_status tn_ite_init_product(tn_lattice *lat);
+/* Evolve the lattice's state in place on the GPU (Sec. 5, Fig. 3):
+ * per step, the one-body gates exp(gamma dtau/2 X) on every site, then the
+ * two-body gates exp(J dtau Z_i Z_j) on every bond in four classes of disjoint
+ * bonds (horizontal bonds whose left site has an even column, then odd;
+ * vertical bonds whose upper site has an even row, then odd) -- each bond's
+ * gate contracted with its two sites, the result matricised (rows: the first
+ * site's physical index and other legs, columns: the second site's) and split
+ * by an FP64 one-sided Jacobi SVD into U sqrt(lambda) and sqrt(lambda) V^T --
+ * then the one-body gates again; after each of the three sets the state is
+ * divided by sqrt(<Psi|Psi>), the norm contracted exactly in FP64.
+ * energies: steps / energy_every doubles (caller-owned) or NULL; bond_dims:
+ * nb ints, the number of singular values each bond kept at its last update
+ * (bond order of tn_result.szsz), or NULL; max_discarded: the largest
+ * lambda_k / lambda_1 any truncation dropped, or NULL.  The lattice's host
+ * tensors hold the evolved state on return.  Device memory for the program
+ * buffers and an SVD workspace (m n + n^2 doubles per bond of a class, m, n
+ * <= 2 D^3) comes from the context's budget.  TN_ERR_INVALID for bad
+ * parameters, TN_ERR_NUMERIC for a non-finite energy. */
+tn_status tn_ite_run(tn_lattice *lat, const tn_ite_params *params, double *energies, int *bond_dims,
+                     double *max_discarded);
+
 /* ------------------------------------------------------------ misc -------- */
 
 const char *tn_status_string(tn_status s);

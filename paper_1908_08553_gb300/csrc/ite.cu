@@ -1,0 +1,265 @@
+// Imaginary time evolution kernels (Sec. 5, QMB Ground State Computation):
+// one-body gates on every site's physical index, the two-body update of a
+// class of disjoint bonds (gate, matricisation, SVD, split with sqrt(lambda),
+// Fig. 3), and the normalisation of the state by its norm.
+//
+// Site tensors are FP64 in the library's input layout with every bond padded
+// to the lattice's bond dimension D (= the largest bond the evolution keeps);
+// kept singular vectors fill the first k indices of a bond, the rest are zero,
+// which leaves the network unchanged.
+//
+// SVD: one-sided Jacobi (Hestenes; Demmel & Veselic 1992): the columns of the
+// m x n matrix Theta are rotated pairwise until mutually orthogonal, the same
+// rotations applied to V = I; then sigma_c = |column c|, U = column / sigma.
+// Pairs are scheduled round-robin (n - 1 rounds of n / 2 disjoint pairs per
+// sweep), one warp per pair, in a fixed order, so a run is deterministic.
+#include <cstdint>
+
+#include "tn_kernels.h"
+
+namespace tn {
+
+namespace {
+
+constexpr int kIteThreads = 256;
+constexpr int kIteMaxSweeps = 60;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace
+
+// exp(Gamma t X) applied to every site's physical index: A[0], A[1] -> g A.
+__global__ void k_ite_one_body(double* __restrict__ A, const long long* __restrict__ site_off, int nsites,
+                               double g00, double g01, double g10, double g11) {
+    const int site = blockIdx.x;
+    if (site >= nsites) return;
+    const long long off = site_off[site], half = (site_off[site + 1] - off) / 2;
+    double* a0 = A + off;
+    double* a1 = a0 + half;
+    for (long long k = threadIdx.x; k < half; k += blockDim.x) {
+        const double x = a0[k], y = a1[k];
+        a0[k] = g00 * x + g01 * y;
+        a1[k] = g10 * x + g11 * y;
+    }
+}
+
+// Multiply the state by 2^(-log2 N / (2 n_sites)) per site, N the norm read from
+// the norm program's result row (entry 1: log2 <Psi|Psi>), so <Psi|Psi> -> 1.
+__global__ void k_ite_scale(double* __restrict__ A, long long n, const double* __restrict__ log2norm,
+                            int nsites) {
+    const double f = exp2(-log2norm[0] / (2.0 * nsites));
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        A[k] *= f;
+}
+
+// One bond per block: Theta from the two sites and the diagonal gate, SVD,
+// truncation, and the two new site tensors written in place.
+__global__ void __launch_bounds__(kIteThreads)
+k_ite_bond(double* __restrict__ A, const IteBondTask* __restrict__ tasks, int ntasks, double* __restrict__ ws,
+           double g00, double g01, double g10, double g11, int chi_max, double eps,
+           int* __restrict__ kept, unsigned long long* __restrict__ max_disc) {
+    const int ti = blockIdx.x;
+    if (ti >= ntasks) return;
+    const IteBondTask& t = tasks[ti];
+    __shared__ double red[kIteThreads / 32];
+    __shared__ int sel[8];
+    __shared__ double sig[8];
+    __shared__ int nkeep_sh;
+    __shared__ int converged;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int* di = t.dims_i;     // p, u, l, dn, rt
+    const int* dj = t.dims_j;
+    const int Db = t.horizontal ? di[4] : di[3];      // the bond between the two sites
+    // rows: (p, three other legs of i); columns: (q, three other legs of j)
+    const int m = t.m, n = t.n, n2 = n + (n & 1);
+    double* Th = ws + t.ws_off;             // column-major: column c at Th + c * m
+    double* V = Th + (long long)m * n2;     // column-major n2 x n2 (column c at V + c * n2)
+    const double* Ai = A + t.off_i;
+    const double* Aj = A + t.off_j;
+    const long long si = (long long)di[1] * di[2] * di[3] * di[4];   // stride of p in site i
+    const long long sj = (long long)dj[1] * dj[2] * dj[3] * dj[4];
+    // ---- Theta[row, col] = g[p][q] sum_b Ai[p, ., b] Aj[q, ., b]
+    for (long long idx = threadIdx.x; idx < (long long)m * n2; idx += blockDim.x) {
+        const int col = (int)(idx / m), row = (int)(idx - (long long)col * m);
+        double v = 0.0;
+        if (col < n) {
+            int p, u, l, x;          // row legs of i
+            int q, y1, y2, y3;       // column legs of j
+            if (t.horizontal) {      // i: (p, u, l, dn) x b = rt ; j: (q, u, dn, rt), b = l
+                x = row % di[3]; int r = row / di[3];
+                l = r % di[2]; r /= di[2];
+                u = r % di[1]; p = r / di[1];
+                y3 = col % dj[4]; int c = col / dj[4];
+                y2 = c % dj[3]; c /= dj[3];
+                y1 = c % dj[1]; q = c / dj[1];
+                const double g = p == 0 ? (q == 0 ? g00 : g01) : (q == 0 ? g10 : g11);
+                const double* ai = Ai + p * si + (((long long)u * di[2] + l) * di[3] + x) * di[4];
+                const double* aj = Aj + q * sj + (long long)y1 * dj[2] * dj[3] * dj[4] + (long long)y2 * dj[4] + y3;
+                for (int b = 0; b < Db; ++b) v += ai[b] * aj[(long long)b * dj[3] * dj[4]];
+                v *= g;
+            } else {                 // i: (p, u, l, rt) x b = dn ; j: (q, l, dn, rt), b = u
+                x = row % di[4]; int r = row / di[4];
+                l = r % di[2]; r /= di[2];
+                u = r % di[1]; p = r / di[1];
+                y3 = col % dj[4]; int c = col / dj[4];
+                y2 = c % dj[3]; c /= dj[3];
+                y1 = c % dj[2]; q = c / dj[2];
+                const double g = p == 0 ? (q == 0 ? g00 : g01) : (q == 0 ? g10 : g11);
+                const double* ai = Ai + p * si + ((long long)u * di[2] + l) * di[3] * di[4] + x;
+                const double* aj = Aj + q * sj + ((long long)y1 * dj[3] + y2) * dj[4] + y3;
+                for (int b = 0; b < Db; ++b)
+                    v += ai[(long long)b * di[4]] * aj[(long long)b * dj[2] * dj[3] * dj[4]];
+                v *= g;
+            }
+        }
+        Th[idx] = v;
+    }
+    for (long long idx = threadIdx.x; idx < (long long)n2 * n2; idx += blockDim.x)
+        V[idx] = (idx / n2 == idx % n2) ? 1.0 : 0.0;
+    __syncthreads();
+
+    // ---- one-sided Jacobi sweeps
+    for (int sweep = 0; sweep < kIteMaxSweeps; ++sweep) {
+        if (threadIdx.x == 0) converged = 1;
+        __syncthreads();
+        for (int round = 0; round < n2 - 1; ++round) {
+            for (int k = warp; k < n2 / 2; k += nwarps) {
+                int a, b;
+                if (k == 0) { a = round; b = n2 - 1; }
+                else { a = (round + k) % (n2 - 1); b = (round - k + n2 - 1) % (n2 - 1); }
+                if (a > b) { const int tmp = a; a = b; b = tmp; }
+                if (b >= n) continue;             // the padding column is zero
+                double* ca = Th + (long long)a * m;
+                double* cb = Th + (long long)b * m;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int r = lane; r < m; r += 32) {
+                    const double x = ca[r], y = cb[r];
+                    al += x * x; be += y * y; ga += x * y;
+                }
+                al = warp_sum_d(al); be = warp_sum_d(be); ga = warp_sum_d(ga);
+                if (ga == 0.0 || al == 0.0 || be == 0.0) continue;
+                if (fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+                if (lane == 0) converged = 0;
+                const double zeta = (be - al) / (2.0 * ga);
+                const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
+                for (int r = lane; r < m; r += 32) {
+                    const double x = ca[r], y = cb[r];
+                    ca[r] = c * x - s * y;
+                    cb[r] = s * x + c * y;
+                }
+                double* va = V + (long long)a * n2;
+                double* vb = V + (long long)b * n2;
+                for (int r = lane; r < n2; r += 32) {
+                    const double x = va[r], y = vb[r];
+                    va[r] = c * x - s * y;
+                    vb[r] = s * x + c * y;
+                }
+            }
+            __syncthreads();
+        }
+        if (converged) break;
+        __syncthreads();
+    }
+
+    // ---- singular values: the k_max largest column norms (ties: lower index)
+    const int kmax = chi_max < Db ? chi_max : Db;
+    if (warp == 0) {
+        for (int j = 0; j < kmax + 1 && j < 8; ++j) {
+            double best = -1.0;
+            int bi = -1;
+            for (int c = lane; c < n; c += 32) {
+                bool taken = false;
+                for (int q = 0; q < j; ++q) taken |= (sel[q] == c);
+                if (taken) continue;
+                double s2 = 0.0;
+                const double* cc = Th + (long long)c * m;
+                for (int r = 0; r < m; ++r) s2 += cc[r] * cc[r];
+                if (s2 > best || (s2 == best && c < bi)) { best = s2; bi = c; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) { best = ob; bi = oi; }
+            }
+            if (lane == 0) { sel[j] = bi; sig[j] = bi >= 0 ? sqrt(best) : 0.0; }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            int k = 0;
+            for (int j = 0; j < kmax; ++j)
+                if (sig[0] > 0.0 && sig[j] >= eps * sig[0] && sel[j] >= 0) ++k;
+            if (k < 1) k = 1;
+            nkeep_sh = k;
+            kept[ti] = k;
+            const double disc = (k < n && k < 8 && sig[0] > 0.0 && sel[k] >= 0) ? sig[k] / sig[0] : 0.0;
+            atomicMax(max_disc, (unsigned long long)__double_as_longlong(disc));
+        }
+    }
+    __syncthreads();
+    const int k = nkeep_sh;
+
+    // ---- new tensors: Ai'[rows, b] = U[:, b] sqrt(sigma_b) = Theta[:, sel_b] / sqrt(sigma_b),
+    //      Aj'[b, cols] = sqrt(sigma_b) V[cols, sel_b]; bond indices >= k are zero
+    double* Aiw = A + t.off_i;
+    double* Ajw = A + t.off_j;
+    for (int idx = threadIdx.x; idx < m * Db; idx += blockDim.x) {
+        const int row = idx / Db, b = idx - row * Db;
+        double v = 0.0;
+        if (b < k && sig[b] > 0.0) v = Th[(long long)sel[b] * m + row] / sqrt(sig[b]);
+        long long dst;
+        if (t.horizontal) {          // row = (p, u, l, dn), b = rt
+            dst = (long long)row * di[4] + b;
+        } else {                     // row = (p, u, l, rt), b = dn
+            const int x = row % di[4], pul = row / di[4];
+            dst = ((long long)pul * di[3] + b) * di[4] + x;
+        }
+        Aiw[dst] = v;
+    }
+    for (int idx = threadIdx.x; idx < n * Db; idx += blockDim.x) {
+        const int col = idx / Db, b = idx - col * Db;
+        double v = 0.0;
+        if (b < k) v = sqrt(sig[b]) * V[(long long)sel[b] * n2 + col];
+        long long dst;
+        if (t.horizontal) {          // col = (q, u, dn, rt), b = l
+            const int y3 = col % dj[4], c1 = col / dj[4];
+            const int y2 = c1 % dj[3], c2 = c1 / dj[3];
+            const int y1 = c2 % dj[1], q = c2 / dj[1];
+            dst = ((((long long)q * dj[1] + y1) * dj[2] + b) * dj[3] + y2) * dj[4] + y3;
+        } else {                     // col = (q, l, dn, rt), b = u
+            const int y3 = col % dj[4], c1 = col / dj[4];
+            const int y2 = c1 % dj[3], c2 = c1 / dj[3];
+            const int y1 = c2 % dj[2], q = c2 / dj[2];
+            dst = ((((long long)q * dj[1] + b) * dj[2] + y1) * dj[3] + y2) * dj[4] + y3;
+        }
+        Ajw[dst] = v;
+    }
+}
+
+cudaError_t launch_ite_one_body(double* A, const long long* site_off, int nsites, const double g[4],
+                                cudaStream_t st) {
+    if (nsites <= 0) return cudaSuccess;
+    k_ite_one_body<<<nsites, 128, 0, st>>>(A, site_off, nsites, g[0], g[1], g[2], g[3]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ite_scale(double* A, long long n, const double* log2norm, int nsites, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+    k_ite_scale<<<(unsigned)blocks, 256, 0, st>>>(A, n, log2norm, nsites);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ite_bonds(double* A, const IteBondTask* tasks, int ntasks, double* ws, const double g[4],
+                             int chi_max, double eps, int* kept, unsigned long long* max_disc, cudaStream_t st) {
+    if (ntasks <= 0) return cudaSuccess;
+    k_ite_bond<<<ntasks, kIteThreads, 0, st>>>(A, tasks, ntasks, ws, g[0], g[1], g[2], g[3], chi_max, eps, kept,
+                                               max_disc);
+    return cudaGetLastError();
+}
+
+}  // namespace tn

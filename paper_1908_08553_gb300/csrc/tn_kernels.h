@@ -144,6 +144,18 @@ struct TcGemmTask {
     int slot_A, slot_B, slot_C, slot_D;   // slots of the FP32 sources / result
 };
 
+// One bond of an imaginary-time two-body update (Sec. 5, Fig. 3): sites i and j
+// (offsets in FP64 entries into the site array, dims {2, u, l, dn, rt}), the
+// bond between them (i's rt and j's l when horizontal, i's dn and j's u when
+// vertical), Theta of m x n (rows: i's p and other legs, columns: j's), and a
+// workspace of m * n2 + n2 * n2 doubles (n2 = n rounded up to even).
+struct IteBondTask {
+    long long off_i, off_j, ws_off;
+    int dims_i[5], dims_j[5];
+    int horizontal;
+    int m, n;
+};
+
 // ----------------------------------------------------------- launchers ---
 // Each returns cudaSuccess or the launch error.  dt: 0 FP64, 1 FP32.
 // variant 0: one outer position per thread (any dtype, K, N); 1 / 2: FP32 with
@@ -201,6 +213,13 @@ cudaError_t launch_tc_gemm(int nsplit, bool dot, int bn, const TcGemmTask* tasks
 constexpr long long kTcRowPad = 256;
 // Reduction (k) width of one staged block of a split operand.
 constexpr int kTcChunk = 32;
+// Imaginary time evolution (ite.cu): g = {g00, g01, g10, g11} (one-body: the
+// 2 x 2 gate; bonds: the diagonal two-body gate g[p_i][p_j]).
+cudaError_t launch_ite_one_body(double* A, const long long* site_off, int nsites, const double g[4],
+                                cudaStream_t st);
+cudaError_t launch_ite_scale(double* A, long long n, const double* log2norm, int nsites, cudaStream_t st);
+cudaError_t launch_ite_bonds(double* A, const IteBondTask* tasks, int ntasks, double* ws, const double g[4],
+                             int chi_max, double eps, int* kept, unsigned long long* max_disc, cudaStream_t st);
 cudaError_t launch_absorb_plain(int dt, const void* in, const void* E, void* out, long long P,
                                 int K, int N, long long S, cudaStream_t st);
 // <absorb(in, E), adj> into *result (device).  scratch: 16 B counter header

@@ -41,6 +41,11 @@ class tn_job(ctypes.Structure):
                 ("h", c_double), ("tensors", POINTER(c_double)), ("seed", c_uint64)]
 
 
+class tn_ite_params(ctypes.Structure):
+    _fields_ = [("J", c_double), ("gamma", c_double), ("dtau", c_double), ("steps", c_int), ("chi_max", c_int),
+                ("eps", c_double), ("energy_every", c_int), ("precision", c_int)]
+
+
 # name -> (restype, argtypes): the complete exported surface of include/tn.h
 SIGNATURES = {
     "tn_ctx_create": (c_int, [c_int, c_size_t, c_void_p, POINTER(c_void_p)]),
@@ -87,6 +92,8 @@ SIGNATURES = {
     "tn_ctx_set_profiling": (c_int, [c_void_p, c_int]),
     "tn_ctx_inject_wait_timeout": (c_int, [c_void_p, c_int]),
     "tn_peak_probe": (c_int, [c_void_p, c_int, POINTER(c_double)]),
+    "tn_ite_init_product": (c_int, [c_void_p]),
+    "tn_ite_run": (c_int, [c_void_p, POINTER(tn_ite_params), c_void_p, c_void_p, POINTER(c_double)]),
     "tn_ctx_kernel_stats": (c_int, [c_void_p, c_int, POINTER(c_int64), POINTER(c_double), POINTER(c_double),
                                     POINTER(c_double)]),
 }
@@ -385,6 +392,23 @@ def tn_absorb_dot_noalloc(dtype: int, x_in, E, adj, P: int, K: int, N: int, S: i
 
 def tn_ctx_set_profiling(ctx, on: bool):
     check(lib().tn_ctx_set_profiling(ctx, 1 if on else 0), "tn_ctx_set_profiling")
+
+
+def tn_ite_init_product(lat):
+    check(lib().tn_ite_init_product(lat), "tn_ite_init_product")
+
+
+def tn_ite_run(lat, L: int, W: int, J: float, gamma: float, dtau: float, steps: int, chi_max: int, eps: float,
+               energy_every: int = 2, prec: int = TN_FP64):
+    """Imaginary time evolution in place; returns (energies, bond_dims, max_discarded)."""
+    p = tn_ite_params(J, gamma, dtau, steps, chi_max, eps, energy_every, prec)
+    ne = steps // energy_every if energy_every > 0 else 0
+    en = np.zeros(max(ne, 1))
+    nb = L * (W - 1) + W * (L - 1)
+    dims = np.zeros(max(nb, 1), dtype=np.int32)
+    disc = c_double()
+    check(lib().tn_ite_run(lat, byref(p), _ptr(en), _ptr(dims), byref(disc)), "tn_ite_run")
+    return en[:ne], dims[:nb], disc.value
 
 
 def tn_peak_probe(ctx, dtype: int) -> float:

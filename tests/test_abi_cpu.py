@@ -201,3 +201,20 @@ def test_inject_wait_timeout_arguments(cpu_ctx):
     with pytest.raises(tn.TNError) as e:
         tn.tn_ctx_inject_wait_timeout(cpu_ctx, -1)
     assert e.value.status == tn.TN_ERR_INVALID
+
+
+def test_ite_arguments_and_initial_state(cpu_ctx):
+    """tn_ite_init_product writes the uniform superposition of Sec. 5 (host
+    only); tn_ite_run checks its parameters before any device work."""
+    import oracle.ite as ite
+    L, W, D = 3, 4, 2
+    lat = tn.tn_create_lattice(cpu_ctx, L, W, D)
+    try:
+        tn.tn_ite_init_product(lat)
+        got = tn.tn_get_site_tensors(lat, tn.tn_lattice_elems(L, W, D))
+        assert np.array_equal(got, ite.pad(ite.product_plus(L, W), L, W, D))
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_ite_run(lat, L, W, 1.0, 1.0, 0.01, 2, D, 0.01)
+        assert e.value.status == tn.TN_ERR_NO_DEVICE
+    finally:
+        tn.tn_destroy_lattice(lat)
