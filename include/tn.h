@@ -341,6 +341,31 @@ tn_status tn_ite_init_product(tn_lattice *lat);
 tn_status tn_ite_run(tn_lattice *lat, const tn_ite_params *params, double *energies, int *bond_dims,
                      double *max_discarded);
 
+/* -------------------------------------- boundary-MPS approximate contraction */
+
+/* Approximate contraction of the double-layer network by a boundary MPS of
+ * bond chi -- the environment approximation the paper names as the way past
+ * the exact method's memory limit (Sec. 7).  The top row is a matrix product
+ * state whose physical legs are the rows' down legs; each further row is
+ * applied as a matrix product operator and the result compressed back to bond
+ * chi (right-orthonormalised right to left, then cut by SVD left to right,
+ * keeping the chi largest singular values; FP64 one-sided Jacobi SVDs).  With
+ * chi >= (D^2)^floor(W/2) nothing is dropped and the result is exact.
+ * chi must satisfy max(chi, D^2) * D^2 <= 512.  Every network is contracted by
+ * one block of one launch, its workspace (about (2W + 2) B^2 D^2 + B^2 + D^8
+ * doubles, B = max(chi, D^2) D^2) taken from the context's budget for the call.
+ * tn_bmps_norm: <Psi|Psi>. */
+tn_status tn_bmps_norm(tn_lattice *lat, int chi, tn_scalar *out);
+/* <A_i> (op_j = 0) or <A_i B_j> (i != j) for A, B in {TN_OP_X, TN_OP_Z}, any
+ * sites: the network with the operators inserted over the norm, both by the
+ * boundary MPS (two networks, one launch). */
+tn_status tn_bmps_expectation(tn_lattice *lat, int chi, int op_i, int i, int op_j, int j, double *out);
+/* The norm, every <X_k> and every nearest-neighbour <Z_i Z_j> (1 + N + nb
+ * networks in one launch, Sec. 5's one contraction per observable, each by the
+ * boundary MPS), and E = -J sum <ZZ> - h sum <X>; out->sx / out->szsz filled if
+ * non-NULL; out->sz and out->czz untouched. */
+tn_status tn_bmps_energy(tn_lattice *lat, int chi, double J, double h, tn_result *out);
+
 /* ------------------------------------------------------------ misc -------- */
 
 const char *tn_status_string(tn_status s);

@@ -1,0 +1,312 @@
+// Boundary-MPS approximate contraction (the environment approximation the
+// paper names as the way past the exact method's memory limit, Sec. 7):
+// the top row of the double-layer network is a matrix product state whose
+// physical legs are the rows' down legs; every further row is applied to it as
+// a matrix product operator, and the grown state is compressed back to bond
+// chi before the next row:
+//   right to left, tensor c (a x p x b) is made right-orthonormal: the one-
+//     sided Jacobi SVD of its transpose gives M = (V Sigma) U^T; U^T (numerical
+//     rank k rows) stays, V Sigma is absorbed into tensor c - 1;
+//   left to right, tensor c viewed as (a p) x b is cut by its SVD, the chi
+//     largest singular values kept: U stays, Sigma V^T is absorbed into c + 1.
+// The last row closes the state into a scalar.  Every tensor is rescaled to
+// max |entry| in [1/2, 1) by an exact power of two after each row, the powers
+// summed in an integer exponent.  One block contracts one network (the norm,
+// or the norm with one or two Pauli operators inserted), FP64 throughout; its
+// tensors live in a global-memory workspace of its own.
+#include <cstdint>
+
+#include "jacobi.cuh"
+#include "tn_kernels.h"
+
+namespace tn {
+
+namespace {
+
+constexpr int kBmpsThreads = 256;
+constexpr int kBmpsMaxBond = 512;     // columns of any SVD (host-checked)
+
+__device__ __forceinline__ double bmps_block_max(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r = fmax(r, red[k]);
+    __syncthreads();
+    return r;
+}
+
+// Scale x[0..n) by 2^-e with e the frexp exponent of max |x|; returns e.
+__device__ int bmps_rescale(double* x, long long n, double* red) {
+    double m = 0.0;
+    for (long long k = threadIdx.x; k < n; k += blockDim.x) m = fmax(m, fabs(x[k]));
+    m = bmps_block_max(m, red);
+    if (!(m > 0.0) || !isfinite(m)) return 0;
+    int e;
+    frexp(m, &e);
+    const double f = ldexp(1.0, -e);
+    for (long long k = threadIdx.x; k < n; k += blockDim.x) x[k] *= f;
+    __syncthreads();
+    return e;
+}
+
+// Singular values (column norms) of the n columns of S after block_jacobi,
+// ordered: sel[0..k) = the columns with the k largest norms (ties: lower
+// index), k = min(kmax, numerical rank: sigma > 1e-14 sigma_max).  Returns k.
+__device__ int bmps_select(const double* S, int m, int n, long long lds, int kmax, double* sig, int* sel,
+                           double* red) {
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        double s2 = 0.0;
+        const double* cc = S + c * lds;
+        for (int r = 0; r < m; ++r) s2 += cc[r] * cc[r];
+        sig[c] = sqrt(s2);
+    }
+    __syncthreads();
+    double mx = 0.0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) mx = fmax(mx, sig[c]);
+    mx = bmps_block_max(mx, red);
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        int rank = 0;
+        for (int q = 0; q < n; ++q) rank += (sig[q] > sig[c]) || (sig[q] == sig[c] && q < c);
+        sel[rank] = c;
+    }
+    __syncthreads();
+    int k = 0;
+    for (int r = 0; r < n && r < kmax; ++r)
+        if (sig[sel[r]] > 1e-14 * mx) ++k;
+    return k > 0 ? k : 1;     // a zero tensor keeps one (zero) column
+}
+
+// Double-layer tensor of site (r, c): T[(u u')(l l')(dn dn')(rt rt')] =
+// sum_{p,q} A[p,u,l,dn,rt] O[p][q] A[q,u',l',dn',rt'] (O = I, X or Z).
+__device__ void bmps_site(const double* A, const int* d5, int op, double* T) {
+    const int u = d5[1], l = d5[2], dn = d5[3], rt = d5[4];
+    const long long half = (long long)u * l * dn * rt;
+    const int U = u * u, Lg = l * l, Dn = dn * dn, R = rt * rt;
+    const long long n = (long long)U * Lg * Dn * R;
+    double o00 = 1, o01 = 0, o10 = 0, o11 = 1;
+    if (op == 1) { o00 = 0; o01 = 1; o10 = 1; o11 = 0; }
+    else if (op == 2) { o00 = -1; o01 = 0; o10 = 0; o11 = 1; }
+    for (long long idx = threadIdx.x; idx < n; idx += blockDim.x) {
+        long long k = idx;
+        const int rr = (int)(k % R); k /= R;
+        const int dd = (int)(k % Dn); k /= Dn;
+        const int ll = (int)(k % Lg); k /= Lg;
+        const int uu = (int)k;
+        const int ua = uu / u, ub = uu % u, la = ll / l, lb = ll % l;
+        const int da = dd / dn, db = dd % dn, ra = rr / rt, rb = rr % rt;
+        const long long ia = (((long long)ua * l + la) * dn + da) * rt + ra;
+        const long long ib = (((long long)ub * l + lb) * dn + db) * rt + rb;
+        const double a0 = A[ia], a1 = A[half + ia], b0 = A[ib], b1 = A[half + ib];
+        T[idx] = a0 * (o00 * b0 + o01 * b1) + a1 * (o10 * b0 + o11 * b1);
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+long long bmps_workspace(int W, int D, int chi) {
+    const long long d = (long long)D * D, B = (long long)bmps_bond_max(D, chi);
+    const long long slot = B * d * B;
+    return (2LL * W + 2) * slot + B * B + d * d * d * d;
+}
+
+__global__ void __launch_bounds__(kBmpsThreads) k_bmps(const BmpsTask* __restrict__ tasks) {
+    const BmpsTask& t = tasks[blockIdx.x];
+    __shared__ int a[17];                     // a[c] = bond left of tensor c; a[0] = a[W] = 1
+    __shared__ int ph[16];                    // physical (down-leg) dimension of tensor c
+    __shared__ int d5[5];
+    __shared__ long long soff[257];
+    __shared__ double red[kBmpsThreads / 32];
+    __shared__ double sig[kBmpsMaxBond];
+    __shared__ int sel[kBmpsMaxBond];
+    __shared__ int flag;
+    const int L = t.L, W = t.W, D = t.D, chi = t.chi;
+    const int d = D * D;
+    const long long B = bmps_bond_max(D, chi);
+    const long long slot = B * d * B;
+    double* bufA = t.ws;
+    double* bufB = bufA + (long long)W * slot;
+    double* S = bufB + (long long)W * slot;
+    double* Tm = S + slot;
+    double* V = Tm + slot;
+    double* Ts = V + B * B;
+    long long ex = 0;                         // power-of-two exponent of the value
+    if (threadIdx.x == 0) {
+        soff[0] = 0;
+        for (int r = 0; r < L; ++r)
+            for (int c = 0; c < W; ++c) {
+                const int s = r * W + c;
+                const long long n = 2LL * (r == 0 ? 1 : D) * (c == 0 ? 1 : D) * (r == L - 1 ? 1 : D) *
+                                    (c == W - 1 ? 1 : D);
+                soff[s + 1] = soff[s] + n;
+            }
+    }
+    __syncthreads();
+    auto site = [&](int r, int c) {
+        if (threadIdx.x == 0) {
+            d5[0] = 2;
+            d5[1] = r == 0 ? 1 : D;
+            d5[2] = c == 0 ? 1 : D;
+            d5[3] = r == L - 1 ? 1 : D;
+            d5[4] = c == W - 1 ? 1 : D;
+        }
+        __syncthreads();
+        const int s = r * W + c;
+        int op = 0;
+        if (t.op_site[0] == s) op = t.op_code[0];
+        if (t.op_site[1] == s) op = t.op_code[1];
+        bmps_site(t.A + soff[s], d5, op, Ts);
+    };
+
+    // ---- row 0: M_c[a = l][p = dn][b = rt]
+    for (int c = 0; c < W; ++c) {
+        site(0, c);
+        const long long n = (long long)d5[2] * d5[2] * d5[3] * d5[3] * d5[4] * d5[4];
+        for (long long k = threadIdx.x; k < n; k += blockDim.x) bufA[c * slot + k] = Ts[k];
+        if (threadIdx.x == 0) {
+            a[c] = d5[2] * d5[2];
+            ph[c] = d5[3] * d5[3];
+            if (c == W - 1) a[W] = d5[4] * d5[4];
+        }
+        __syncthreads();
+    }
+    for (int c = 0; c < W; ++c) ex += bmps_rescale(bufA + c * slot, (long long)a[c] * ph[c] * a[c + 1], red);
+
+    for (int r = 1; r < L; ++r) {
+        // ---- apply row r: N[(a, l)][dn][(b, rt)] = sum_u M[a][u][b] T[u][l][dn][rt]
+        for (int c = 0; c < W; ++c) {
+            site(r, c);
+            const int lu = d5[1] * d5[1], ll = d5[2] * d5[2], ld = d5[3] * d5[3], lr = d5[4] * d5[4];
+            const int ac = a[c], bc = a[c + 1];
+            const double* M = bufA + c * slot;
+            double* N = bufB + c * slot;
+            const long long n = (long long)ac * ll * ld * bc * lr;
+            for (long long idx = threadIdx.x; idx < n; idx += blockDim.x) {
+                long long k = idx;
+                const int x = (int)(k % lr); k /= lr;
+                const int bb = (int)(k % bc); k /= bc;
+                const int dn = (int)(k % ld); k /= ld;
+                const int l = (int)(k % ll); k /= ll;
+                const int aa = (int)k;
+                double v = 0.0;
+                for (int u = 0; u < lu; ++u)
+                    v += M[((long long)aa * lu + u) * bc + bb] * Ts[(((long long)u * ll + l) * ld + dn) * lr + x];
+                N[idx] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) ph[c] = ld;
+        }
+        __syncthreads();
+        // new bonds: a[c] times the double-layer dimension of the row's horizontal
+        // leg between columns c - 1 and c (d inside the row, 1 at its two ends)
+        if (threadIdx.x == 0)
+            for (int c = 1; c < W; ++c) a[c] *= d;
+        __syncthreads();
+        { double* tmp = bufA; bufA = bufB; bufB = tmp; }
+
+        if (r < L - 1) {
+            // ---- right to left: right-orthonormalise
+            for (int c = W - 1; c >= 1; --c) {
+                const int ac = a[c], p = ph[c], bc = a[c + 1];
+                double* M = bufA + c * slot;
+                const int m = p * bc;
+                // M row-major [a][p b] is its transpose column-major: columns = the a rows
+                block_jacobi(M, m, ac, m, V, ac, &flag);
+                const int k = bmps_select(M, m, ac, m, ac, sig, sel, red);
+                // new tensor c: row j = column sel[j] / sigma
+                for (long long idx = threadIdx.x; idx < (long long)k * m; idx += blockDim.x) {
+                    const int j = (int)(idx / m), i = (int)(idx - (long long)j * m);
+                    const double sg = sig[sel[j]];
+                    Tm[idx] = sg > 0.0 ? M[(long long)sel[j] * m + i] / sg : 0.0;
+                }
+                __syncthreads();
+                // tensor c - 1 times V Sigma: [x][p'][a] -> [x][p'][j]
+                const int ap = a[c - 1] * ph[c - 1];
+                double* Mp = bufA + (c - 1) * slot;
+                for (long long idx = threadIdx.x; idx < (long long)ap * k; idx += blockDim.x) {
+                    const int xp = (int)(idx / k), j = (int)(idx - (long long)xp * k);
+                    const int cj = sel[j];
+                    double v = 0.0;
+                    for (int aa = 0; aa < ac; ++aa) v += Mp[(long long)xp * ac + aa] * V[(long long)cj * ac + aa];
+                    S[idx] = v * sig[cj];
+                }
+                __syncthreads();
+                for (long long idx = threadIdx.x; idx < (long long)k * m; idx += blockDim.x) M[idx] = Tm[idx];
+                for (long long idx = threadIdx.x; idx < (long long)ap * k; idx += blockDim.x) Mp[idx] = S[idx];
+                __syncthreads();
+                if (threadIdx.x == 0) a[c] = k;
+                __syncthreads();
+            }
+            // ---- left to right: truncate every bond to chi
+            for (int c = 0; c < W - 1; ++c) {
+                const int ac = a[c], p = ph[c], bc = a[c + 1];
+                double* M = bufA + c * slot;
+                const int m = ac * p;
+                for (long long idx = threadIdx.x; idx < (long long)m * bc; idx += blockDim.x) {
+                    const int i = (int)(idx / bc), j = (int)(idx - (long long)i * bc);
+                    S[(long long)j * m + i] = M[idx];
+                }
+                __syncthreads();
+                block_jacobi(S, m, bc, m, V, bc, &flag);
+                const int k = bmps_select(S, m, bc, m, chi, sig, sel, red);
+                for (long long idx = threadIdx.x; idx < (long long)m * k; idx += blockDim.x) {
+                    const int i = (int)(idx / k), j = (int)(idx - (long long)i * k);
+                    const double sg = sig[sel[j]];
+                    M[idx] = sg > 0.0 ? S[(long long)sel[j] * m + i] / sg : 0.0;
+                }
+                // tensor c + 1 := Sigma V^T (k x b) times [b][q]
+                const int q = ph[c + 1] * a[c + 2];
+                double* Mn = bufA + (c + 1) * slot;
+                for (long long idx = threadIdx.x; idx < (long long)k * q; idx += blockDim.x) {
+                    const int j = (int)(idx / q), qq = (int)(idx - (long long)j * q);
+                    const int cj = sel[j];
+                    double v = 0.0;
+                    for (int bb = 0; bb < bc; ++bb) v += V[(long long)cj * bc + bb] * Mn[(long long)bb * q + qq];
+                    Tm[idx] = sig[cj] * v;
+                }
+                __syncthreads();
+                for (long long idx = threadIdx.x; idx < (long long)k * q; idx += blockDim.x) Mn[idx] = Tm[idx];
+                __syncthreads();
+                if (threadIdx.x == 0) a[c + 1] = k;
+                __syncthreads();
+            }
+        }
+        for (int c = 0; c < W; ++c) ex += bmps_rescale(bufA + c * slot, (long long)a[c] * ph[c] * a[c + 1], red);
+    }
+
+    // ---- close: every physical leg has dimension 1 now; v := v M_c
+    double* v = S;
+    double* w = Tm;
+    if (threadIdx.x == 0) v[0] = 1.0;
+    __syncthreads();
+    for (int c = 0; c < W; ++c) {
+        const int ac = a[c], bc = a[c + 1];
+        const double* M = bufA + c * slot;   // [a][1][b]
+        for (int j = threadIdx.x; j < bc; j += blockDim.x) {
+            double s = 0.0;
+            for (int aa = 0; aa < ac; ++aa) s += v[aa] * M[(long long)aa * bc + j];
+            w[j] = s;
+        }
+        __syncthreads();
+        ex += bmps_rescale(w, bc, red);
+        double* tmp = v; v = w; w = tmp;
+    }
+    if (threadIdx.x == 0) {
+        int e = 0;
+        const double m = frexp(v[0], &e);
+        t.out[0] = m;
+        t.out[1] = (double)(ex + e);
+    }
+}
+
+cudaError_t launch_bmps(const BmpsTask* tasks, int ntasks, cudaStream_t st) {
+    if (ntasks <= 0) return cudaSuccess;
+    k_bmps<<<ntasks, kBmpsThreads, 0, st>>>(tasks);
+    return cudaGetLastError();
+}
+
+}  // namespace tn

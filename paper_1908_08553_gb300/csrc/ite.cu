@@ -8,13 +8,11 @@
 // kept singular vectors fill the first k indices of a bond, the rest are zero,
 // which leaves the network unchanged.
 //
-// SVD: one-sided Jacobi (Hestenes; Demmel & Veselic 1992): the columns of the
-// m x n matrix Theta are rotated pairwise until mutually orthogonal, the same
-// rotations applied to V = I; then sigma_c = |column c|, U = column / sigma.
-// Pairs are scheduled round-robin (n - 1 rounds of n / 2 disjoint pairs per
-// sweep), one warp per pair, in a fixed order, so a run is deterministic.
+// SVD: the block-wide one-sided Jacobi of jacobi.cuh on Theta; then
+// sigma_c = |column c|, U = column / sigma.
 #include <cstdint>
 
+#include "jacobi.cuh"
 #include "tn_kernels.h"
 
 namespace tn {
@@ -22,13 +20,6 @@ namespace tn {
 namespace {
 
 constexpr int kIteThreads = 256;
-constexpr int kIteMaxSweeps = 60;
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 }  // namespace
 
@@ -65,12 +56,11 @@ k_ite_bond(double* __restrict__ A, const IteBondTask* __restrict__ tasks, int nt
     const int ti = blockIdx.x;
     if (ti >= ntasks) return;
     const IteBondTask& t = tasks[ti];
-    __shared__ double red[kIteThreads / 32];
     __shared__ int sel[8];
     __shared__ double sig[8];
     __shared__ int nkeep_sh;
     __shared__ int converged;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int* di = t.dims_i;     // p, u, l, dn, rt
     const int* dj = t.dims_j;
     const int Db = t.horizontal ? di[4] : di[3];      // the bond between the two sites
@@ -118,53 +108,8 @@ k_ite_bond(double* __restrict__ A, const IteBondTask* __restrict__ tasks, int nt
         }
         Th[idx] = v;
     }
-    for (long long idx = threadIdx.x; idx < (long long)n2 * n2; idx += blockDim.x)
-        V[idx] = (idx / n2 == idx % n2) ? 1.0 : 0.0;
     __syncthreads();
-
-    // ---- one-sided Jacobi sweeps
-    for (int sweep = 0; sweep < kIteMaxSweeps; ++sweep) {
-        if (threadIdx.x == 0) converged = 1;
-        __syncthreads();
-        for (int round = 0; round < n2 - 1; ++round) {
-            for (int k = warp; k < n2 / 2; k += nwarps) {
-                int a, b;
-                if (k == 0) { a = round; b = n2 - 1; }
-                else { a = (round + k) % (n2 - 1); b = (round - k + n2 - 1) % (n2 - 1); }
-                if (a > b) { const int tmp = a; a = b; b = tmp; }
-                if (b >= n) continue;             // the padding column is zero
-                double* ca = Th + (long long)a * m;
-                double* cb = Th + (long long)b * m;
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int r = lane; r < m; r += 32) {
-                    const double x = ca[r], y = cb[r];
-                    al += x * x; be += y * y; ga += x * y;
-                }
-                al = warp_sum_d(al); be = warp_sum_d(be); ga = warp_sum_d(ga);
-                if (ga == 0.0 || al == 0.0 || be == 0.0) continue;
-                if (fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
-                if (lane == 0) converged = 0;
-                const double zeta = (be - al) / (2.0 * ga);
-                const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
-                for (int r = lane; r < m; r += 32) {
-                    const double x = ca[r], y = cb[r];
-                    ca[r] = c * x - s * y;
-                    cb[r] = s * x + c * y;
-                }
-                double* va = V + (long long)a * n2;
-                double* vb = V + (long long)b * n2;
-                for (int r = lane; r < n2; r += 32) {
-                    const double x = va[r], y = vb[r];
-                    va[r] = c * x - s * y;
-                    vb[r] = s * x + c * y;
-                }
-            }
-            __syncthreads();
-        }
-        if (converged) break;
-        __syncthreads();
-    }
+    block_jacobi(Th, m, n, m, V, n2, &converged);
 
     // ---- singular values: the k_max largest column norms (ties: lower index)
     const int kmax = chi_max < Db ? chi_max : Db;

@@ -1,0 +1,78 @@
+// Block-wide one-sided Jacobi SVD (Hestenes 1958; Demmel & Veselic 1992) on a
+// matrix in global memory, FP64.  The n columns of A (column-major, leading
+// dimension lda, m rows) are rotated pairwise until mutually orthogonal; the
+// same rotations applied to V (n x n, column-major, leading dimension ldv,
+// reset to the identity here) give A_in = A_out V^T with A_out = U Sigma, so
+// sigma_c = |column c of A_out|.  Pairs follow the round-robin (circle)
+// schedule: n2 - 1 rounds of n2 / 2 disjoint pairs per sweep (n2 = n rounded
+// up to even, the extra column treated as zero), one warp per pair, in a fixed
+// order, so a result is reproducible.  A sweep in which no pair needed a
+// rotation (|a.b| <= 1e-15 |a| |b| for every pair) ends the iteration.
+// Every thread of the block must call it; it synchronises the block.
+#pragma once
+
+namespace tn {
+
+constexpr int kJacobiMaxSweeps = 60;
+
+__device__ __forceinline__ double jacobi_warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// `flag` is one int of shared memory owned by the caller.
+__device__ inline void block_jacobi(double* A, int m, int n, long long lda, double* V, long long ldv, int* flag) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int n2 = n + (n & 1);
+    for (long long idx = threadIdx.x; idx < (long long)n * n; idx += blockDim.x) {
+        const int c = (int)(idx / n), r = (int)(idx - (long long)c * n);
+        V[c * ldv + r] = r == c ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < kJacobiMaxSweeps && n > 1; ++sweep) {
+        if (threadIdx.x == 0) *flag = 1;
+        __syncthreads();
+        for (int round = 0; round < n2 - 1; ++round) {
+            for (int k = warp; k < n2 / 2; k += nwarps) {
+                int a, b;
+                if (k == 0) { a = round; b = n2 - 1; }
+                else { a = (round + k) % (n2 - 1); b = (round - k + n2 - 1) % (n2 - 1); }
+                if (a > b) { const int t = a; a = b; b = t; }
+                if (b >= n) continue;              // the padding column is zero
+                double* ca = A + a * lda;
+                double* cb = A + b * lda;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int r = lane; r < m; r += 32) {
+                    const double x = ca[r], y = cb[r];
+                    al += x * x; be += y * y; ga += x * y;
+                }
+                al = jacobi_warp_sum(al); be = jacobi_warp_sum(be); ga = jacobi_warp_sum(ga);
+                if (ga == 0.0 || al == 0.0 || be == 0.0) continue;
+                if (fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+                if (lane == 0) *flag = 0;
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                for (int r = lane; r < m; r += 32) {
+                    const double x = ca[r], y = cb[r];
+                    ca[r] = c * x - s * y;
+                    cb[r] = s * x + c * y;
+                }
+                double* va = V + a * ldv;
+                double* vb = V + b * ldv;
+                for (int r = lane; r < n; r += 32) {
+                    const double x = va[r], y = vb[r];
+                    va[r] = c * x - s * y;
+                    vb[r] = s * x + c * y;
+                }
+            }
+            __syncthreads();
+        }
+        const bool done = *flag != 0;
+        __syncthreads();
+        if (done) break;
+    }
+}
+
+}  // namespace tn

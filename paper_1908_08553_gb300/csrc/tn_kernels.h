@@ -156,6 +156,26 @@ struct IteBondTask {
     int m, n;
 };
 
+// One network of a boundary-MPS contraction (bmps.cu): the double-layer norm
+// network of an L x W PEPS of bond D (FP64 site tensors in the input layout),
+// with up to two Pauli operators inserted (code 1 X, 2 Z at op_site; -1: none),
+// contracted with boundary bond chi; out receives (mantissa, exponent).
+struct BmpsTask {
+    const double* A;
+    double* ws;
+    double* out;
+    int L, W, D, chi;
+    int op_site[2], op_code[2];
+};
+// Boundary-MPS workspace (doubles) of one network of this shape.
+long long bmps_workspace(int W, int D, int chi);
+// Largest boundary bond after a row is applied: max(chi, d) * d, d = D^2.
+__host__ __device__ inline int bmps_bond_max(int D, int chi) {
+    const int d = D * D;
+    return (chi > d ? chi : d) * d;
+}
+cudaError_t launch_bmps(const BmpsTask* tasks, int ntasks, cudaStream_t st);
+
 // ----------------------------------------------------------- launchers ---
 // Each returns cudaSuccess or the launch error.  dt: 0 FP64, 1 FP32.
 // variant 0: one outer position per thread (any dtype, K, N); 1 / 2: FP32 with

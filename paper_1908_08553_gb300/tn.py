@@ -93,6 +93,9 @@ SIGNATURES = {
     "tn_ctx_inject_wait_timeout": (c_int, [c_void_p, c_int]),
     "tn_peak_probe": (c_int, [c_void_p, c_int, POINTER(c_double)]),
     "tn_ite_init_product": (c_int, [c_void_p]),
+    "tn_bmps_norm": (c_int, [c_void_p, c_int, POINTER(tn_scalar)]),
+    "tn_bmps_expectation": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, POINTER(c_double)]),
+    "tn_bmps_energy": (c_int, [c_void_p, c_int, c_double, c_double, POINTER(tn_result)]),
     "tn_ite_run": (c_int, [c_void_p, POINTER(tn_ite_params), c_void_p, c_void_p, POINTER(c_double)]),
     "tn_ctx_kernel_stats": (c_int, [c_void_p, c_int, POINTER(c_int64), POINTER(c_double), POINTER(c_double),
                                     POINTER(c_double)]),
@@ -392,6 +395,26 @@ def tn_absorb_dot_noalloc(dtype: int, x_in, E, adj, P: int, K: int, N: int, S: i
 
 def tn_ctx_set_profiling(ctx, on: bool):
     check(lib().tn_ctx_set_profiling(ctx, 1 if on else 0), "tn_ctx_set_profiling")
+
+
+def tn_bmps_norm(lat, chi: int):
+    """<Psi|Psi> by the boundary MPS of bond chi: (mantissa, exponent)."""
+    out = tn_scalar()
+    check(lib().tn_bmps_norm(lat, chi, byref(out)), "tn_bmps_norm")
+    return out.mant, out.exp2
+
+
+def tn_bmps_expectation(lat, chi: int, op_i: int, i: int, op_j: int = 0, j: int = -1) -> float:
+    v = c_double()
+    check(lib().tn_bmps_expectation(lat, chi, op_i, i, op_j, j, byref(v)), "tn_bmps_expectation")
+    return v.value
+
+
+def tn_bmps_energy(lat, chi: int, J: float, h: float, L: int, W: int):
+    """(tn_result, sx, szsz) by the boundary MPS of bond chi."""
+    r, sx, zz, nb = _result_arrays(L, W)
+    check(lib().tn_bmps_energy(lat, chi, J, h, byref(r)), "tn_bmps_energy")
+    return r, sx, zz[:nb]
 
 
 def tn_ite_init_product(lat):

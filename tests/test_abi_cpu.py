@@ -218,3 +218,22 @@ def test_ite_arguments_and_initial_state(cpu_ctx):
         assert e.value.status == tn.TN_ERR_NO_DEVICE
     finally:
         tn.tn_destroy_lattice(lat)
+
+
+def test_bmps_arguments(cpu_ctx):
+    lat = tn.tn_create_lattice(cpu_ctx, 4, 4, 2)
+    try:
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_bmps_norm(lat, 129)            # max(chi, 4) * 4 > 512
+        assert e.value.status == tn.TN_ERR_INVALID
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_bmps_norm(lat, 8)
+        assert e.value.status == tn.TN_ERR_NO_DEVICE
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_bmps_expectation(lat, 8, tn.TN_OP_ZZ, 0)
+        assert e.value.status == tn.TN_ERR_INVALID
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_bmps_expectation(lat, 8, tn.TN_OP_Z, 3, tn.TN_OP_Z, 3)
+        assert e.value.status == tn.TN_ERR_INVALID
+    finally:
+        tn.tn_destroy_lattice(lat)
