@@ -341,6 +341,38 @@ tn_status tn_ite_init_product(tn_lattice *lat);
 tn_status tn_ite_run(tn_lattice *lat, const tn_ite_params *params, double *energies, int *bond_dims,
                      double *max_discarded);
 
+/* ------------------------------------------------------------ autotuner -- */
+
+/* Program choices per lattice shape (no counterpart in the paper; the tuned
+ * tiles and schedules of the batched form).  Each choice is an exact
+ * reformulation -- only speed differs:
+ *   bit 0  FP32 D = 2: two steps of a frame row fused in one pass
+ *   bit 1  FP32 D <= 2: <X_k>, <Z_k> and the local norm in one absorb-dot
+ *   bit 2  FP32 / FP64 D = 3 interior steps: ket pass then bra pass
+ *   bit 3  BF16x3 / BF16x6: ring products on the tensor cores (else FP32 SIMT)
+ * 15 (all set) is the fixed default.  tn_autotune times every combination that
+ * changes the program of each distinct (L[k], W[k], D[k]) on a batch of
+ * copies of it (as many as fit max_bytes, 0 = 4 GiB, at most 64; shapes whose
+ * single footprint exceeds max_bytes are skipped), `reps` timed runs after one
+ * warm-up, CUDA events on the batch's stream, and stores the fastest (a
+ * combination replaces the current choice only when 2% faster) in a process-
+ * wide table keyed on (L, W, D, precision, work).  Batches, lattices and served
+ * jobs created afterwards use the table's choice for their shape, so a lattice
+ * is contracted the same way alone, in a batch and when served; tune before
+ * creating them.  work: TN_WORK_NORM or TN_WORK_ENERGY. */
+tn_status tn_autotune(tn_ctx *ctx, int n, const int *L, const int *W, const int *D, tn_precision prec,
+                      tn_work work, int reps, size_t max_bytes);
+/* The table's choice for a shape: knobs (15 if untuned), the tuned and the
+ * default mean ms per batch run of the tuning batch, tuned = 1 if present. */
+tn_status tn_autotune_lookup(int L, int W, int D, tn_precision prec, tn_work work, int *knobs, double *best_ms,
+                             double *default_ms, int *tuned);
+/* Set a shape's choice by hand (knobs 0..15). */
+tn_status tn_autotune_set(int L, int W, int D, tn_precision prec, tn_work work, int knobs);
+tn_status tn_autotune_clear(void);
+/* The table as text, one shape per line; load merges a saved table. */
+tn_status tn_autotune_save(const char *path);
+tn_status tn_autotune_load(const char *path);
+
 /* -------------------------------------- boundary-MPS approximate contraction */
 
 /* Approximate contraction of the double-layer network by a boundary MPS of

@@ -15,6 +15,7 @@
 #include <cfloat>
 #include <cstdint>
 
+#include "pdl.cuh"
 #include "tn_kernels.h"
 
 namespace tn {
@@ -225,6 +226,7 @@ __device__ __forceinline__ void absorb_tile(const AbsorbTask& t, long long local
 template <typename T, int K, int N, int MODE>
 __global__ void __launch_bounds__(kAbsorbThreads)
 k_absorb(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     const long long tile = blockIdx.x;
@@ -258,6 +260,7 @@ constexpr int kV2Threads = 128;
 template <int K, int N, int MODE, bool ALONG_P>
 __global__ void __launch_bounds__(kV2Threads, MODE >= 4 ? 3 : 4)
 k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
+    pdl_enter();
     constexpr int NE = MODE == 5 ? 3 : (MODE == 4 ? 2 : 1);     // site matrices
     // along s the 4 outer positions are paired into two-lane FMAs; the site
     // matrices then live in shared memory as duplicated (e, e) pairs
@@ -618,6 +621,7 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kAbsorbThreads)
 k_absorb_generic(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots,
                  const int* __restrict__ tmap) {
+    pdl_enter();
     __shared__ double red[32];
     const long long tile = blockIdx.x;
     const AbsorbTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
@@ -684,6 +688,7 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kTwoPassThreads)
 k_absorb_2pass(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots,
                const int* __restrict__ tmap) {
+    pdl_enter();
     constexpr bool kInSmem = sizeof(T) == 8;
     __shared__ T Fa[2][9][9], Fb[2][9][9];
     __shared__ double red[32];
@@ -785,7 +790,7 @@ cudaError_t launch_2pass_t(const AbsorbTask* tasks, int ntasks, long long nblock
     const size_t smem = sizeof(T) == 8 ? (size_t)81 * kTwoPassThreads * sizeof(T) : 0;
     auto fn = k_absorb_2pass<T, MODE>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    fn<<<(unsigned)nblocks, kTwoPassThreads, smem, st>>>(tasks, ntasks, slots, tmap);
+    TN_LAUNCH(fn, dim3((unsigned)nblocks), dim3(kTwoPassThreads), smem, st, tasks, ntasks, slots, tmap);
     return cudaGetLastError();
 }
 }  // namespace
@@ -807,6 +812,7 @@ constexpr int kA2Threads = 128;
 template <int K1, int N2, int MODE>
 __global__ void __launch_bounds__(kA2Threads, MODE == 2 ? 3 : 4)
 k_absorb2(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
+    pdl_enter();
     constexpr int DN = 4, H = 4, U = 4;
     constexpr bool PAIRED = N2 >= 4;     // paired FMAs (fma.rn.f32x2) for N2 in {4, 16}
     __shared__ __align__(16) float E1s[K1 * DN * H];
@@ -992,8 +998,8 @@ cudaError_t launch_absorb2(bool dot, int K1, int N2, const AbsorbTask* tasks, in
     if (nblocks <= 0) return cudaSuccess;
 #define TN_A2(KK, NN)                                                                                       \
     if (K1 == KK && N2 == NN) {                                                                             \
-        if (dot) k_absorb2<KK, NN, 2><<<(unsigned)nblocks, kA2Threads, 0, st>>>(tasks, ntasks, slots, tmap); \
-        else k_absorb2<KK, NN, 1><<<(unsigned)nblocks, kA2Threads, 0, st>>>(tasks, ntasks, slots, tmap);     \
+        if (dot) TN_LAUNCH(k_absorb2<KK, NN, 2>, dim3((unsigned)nblocks), dim3(kA2Threads), 0, st, tasks, ntasks, slots, tmap); \
+        else TN_LAUNCH(k_absorb2<KK, NN, 1>, dim3((unsigned)nblocks), dim3(kA2Threads), 0, st, tasks, ntasks, slots, tmap);     \
         return cudaGetLastError();                                                                          \
     }
     TN_A2(4, 1) TN_A2(4, 4) TN_A2(4, 16) TN_A2(16, 1) TN_A2(16, 4) TN_A2(16, 16)
@@ -1040,7 +1046,7 @@ cudaError_t absorb_dispatch(int K, int N, const AbsorbTask* tasks, int ntasks, l
         auto fn = k_absorb<T, KK, NN, MODE>;                                                \
         if (smem > 48 * 1024)                                                               \
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        fn<<<(unsigned)nblocks, kAbsorbThreads, smem, st>>>(tasks, ntasks, slots, tmap);    \
+        TN_LAUNCH(fn, dim3((unsigned)nblocks), dim3(kAbsorbThreads), smem, st, tasks, ntasks, slots, tmap);    \
         return cudaGetLastError();                                                          \
     }
     TN_ABSORB_CASE(1, 1)
@@ -1051,7 +1057,7 @@ cudaError_t absorb_dispatch(int K, int N, const AbsorbTask* tasks, int ntasks, l
     TN_ABSORB_CASE(1, 81) TN_ABSORB_CASE(81, 1) TN_ABSORB_CASE(9, 81) TN_ABSORB_CASE(81, 9)
     TN_ABSORB_CASE(81, 81)
 #undef TN_ABSORB_CASE
-    k_absorb_generic<T, MODE><<<(unsigned)nblocks, kAbsorbThreads, 0, st>>>(tasks, ntasks, slots, tmap);
+    TN_LAUNCH(k_absorb_generic<T, MODE>, dim3((unsigned)nblocks), dim3(kAbsorbThreads), 0, st, tasks, ntasks, slots, tmap);
     return cudaGetLastError();
 }
 
@@ -1065,7 +1071,7 @@ cudaError_t absorb4_dispatch(int K, int N, const AbsorbTask* tasks, int ntasks, 
                              cudaStream_t st, const int* tmap) {
 #define TN_A4_CASE(KK, NN)                                                                        \
     if (K == KK && N == NN) {                                                                     \
-        k_absorb4<KK, NN, MODE, ALONG_P><<<(unsigned)nblocks, kV2Threads, 0, st>>>(tasks, ntasks, slots, tmap); \
+        TN_LAUNCH(k_absorb4<KK, NN, MODE, ALONG_P>, dim3((unsigned)nblocks), dim3(kV2Threads), 0, st, tasks, ntasks, slots, tmap); \
         return cudaGetLastError();                                                                \
     }
     TN_A4_CASE(1, 1) TN_A4_CASE(1, 4) TN_A4_CASE(4, 1) TN_A4_CASE(4, 4)
@@ -1111,6 +1117,7 @@ cudaError_t launch_absorb(int dt, bool dot, int K, int N, const AbsorbTask* task
 template <typename T, bool DOT>
 __global__ void __launch_bounds__(256)
 k_gemm(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+    pdl_enter();
     constexpr int BM = kGemmTile, BN = kGemmTile, BK = 16;
     __shared__ T As[BK][BM + 4];
     __shared__ T Bs[BK][BN + 4];
@@ -1216,6 +1223,7 @@ constexpr int kG2M = 128, kG2N = 128, kG2K = 8;
 template <bool DOT, bool VEC4>
 __global__ void __launch_bounds__(256, 2)
 k_gemm2(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+    pdl_enter();
     __shared__ __align__(16) float As[2][kG2K][kG2M + 4];
     __shared__ __align__(16) float Bs[2][kG2K][kG2N + 4];
     __shared__ double red[32];
@@ -1392,6 +1400,7 @@ k_gemm2(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots
 template <bool DOT, bool AK, bool BNC>
 __global__ void __launch_bounds__(256, 2)
 k_gemm3(const GemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+    pdl_enter();
     __shared__ __align__(16) float As[2][kG2K][kG2M + 4];
     __shared__ __align__(16) float Bs[2][kG2K][kG2N + 4];
     __shared__ double red[32];
@@ -1540,30 +1549,30 @@ cudaError_t launch_gemm(int dt, bool dot, const GemmTask* tasks, int ntasks, lon
                         Slot* slots, cudaStream_t st, int variant) {
     if (nblocks <= 0) return cudaSuccess;
     if (variant == 1) {
-        if (dot) k_gemm2<true, true><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
-        else k_gemm2<false, true><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+        if (dot) TN_LAUNCH(k_gemm2<true, true>, dim3((unsigned)nblocks), dim3(256), 0, st, tasks, ntasks, slots);
+        else TN_LAUNCH(k_gemm2<false, true>, dim3((unsigned)nblocks), dim3(256), 0, st, tasks, ntasks, slots);
         return cudaGetLastError();
     }
     if (variant == 2) {
-        if (dot) k_gemm2<true, false><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
-        else k_gemm2<false, false><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+        if (dot) TN_LAUNCH(k_gemm2<true, false>, dim3((unsigned)nblocks), dim3(256), 0, st, tasks, ntasks, slots);
+        else TN_LAUNCH(k_gemm2<false, false>, dim3((unsigned)nblocks), dim3(256), 0, st, tasks, ntasks, slots);
         return cudaGetLastError();
     }
     if (variant >= 3 && variant <= 6) {
         const bool ak = variant >= 5, bn = (variant - 3) % 2 == 1;
 #define TN_G3(D_, A_, B_) \
-        if (dot == D_ && ak == A_ && bn == B_) k_gemm3<D_, A_, B_><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+        if (dot == D_ && ak == A_ && bn == B_) TN_LAUNCH(k_gemm3<D_, A_, B_>, dim3((unsigned)nblocks), dim3(256), 0, st, tasks, ntasks, slots);
         TN_G3(true, true, true) TN_G3(true, true, false) TN_G3(true, false, true) TN_G3(true, false, false)
         TN_G3(false, true, true) TN_G3(false, true, false) TN_G3(false, false, true) TN_G3(false, false, false)
 #undef TN_G3
         return cudaGetLastError();
     }
     if (dt == 0) {
-        if (dot) k_gemm<double, true><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
-        else k_gemm<double, false><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+        if (dot) TN_LAUNCH(k_gemm<double, true>, dim3((unsigned)nblocks), dim3(256), 0, st, tasks, ntasks, slots);
+        else TN_LAUNCH(k_gemm<double, false>, dim3((unsigned)nblocks), dim3(256), 0, st, tasks, ntasks, slots);
     } else {
-        if (dot) k_gemm<float, true><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
-        else k_gemm<float, false><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+        if (dot) TN_LAUNCH(k_gemm<float, true>, dim3((unsigned)nblocks), dim3(256), 0, st, tasks, ntasks, slots);
+        else TN_LAUNCH(k_gemm<float, false>, dim3((unsigned)nblocks), dim3(256), 0, st, tasks, ntasks, slots);
     }
     return cudaGetLastError();
 }
@@ -1573,6 +1582,7 @@ cudaError_t launch_gemm(int dt, bool dot, const GemmTask* tasks, int ntasks, lon
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_dot(const DotTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
+    pdl_enter();
     __shared__ double red[32];
     const long long tile = blockIdx.x;
     const DotTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
@@ -1595,8 +1605,8 @@ k_dot(const DotTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, c
 cudaError_t launch_dot(int dt, const DotTask* tasks, int ntasks, long long nblocks, Slot* slots,
                        cudaStream_t st, const int* tmap) {
     if (nblocks <= 0) return cudaSuccess;
-    if (dt == 0) k_dot<double><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots, tmap);
-    else k_dot<float><<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots, tmap);
+    if (dt == 0) TN_LAUNCH(k_dot<double>, dim3((unsigned)nblocks), dim3(256), 0, st, tasks, ntasks, slots, tmap);
+    else TN_LAUNCH(k_dot<float>, dim3((unsigned)nblocks), dim3(256), 0, st, tasks, ntasks, slots, tmap);
     return cudaGetLastError();
 }
 
@@ -1613,6 +1623,7 @@ cudaError_t launch_dot(int dt, const DotTask* tasks, int ntasks, long long nbloc
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_sitemat(const SiteMatTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots) {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int ti = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (ti >= ntasks) return;
@@ -1679,8 +1690,8 @@ cudaError_t launch_sitemat(int dt, const SiteMatTask* tasks, int ntasks, Slot* s
                            cudaStream_t st) {
     if (ntasks <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((ntasks + 7) / 8);
-    if (dt == 0) k_sitemat<double><<<blocks, 256, 0, st>>>(tasks, ntasks, slots);
-    else k_sitemat<float><<<blocks, 256, 0, st>>>(tasks, ntasks, slots);
+    if (dt == 0) TN_LAUNCH(k_sitemat<double>, dim3(blocks), dim3(256), 0, st, tasks, ntasks, slots);
+    else TN_LAUNCH(k_sitemat<float>, dim3(blocks), dim3(256), 0, st, tasks, ntasks, slots);
     return cudaGetLastError();
 }
 
@@ -1760,6 +1771,7 @@ cudaError_t launch_fma_probe(int dt, void* out, long long blocks, long long iter
 // ------------------------------------------------------------- init ------
 
 __global__ void k_init(Slot* slots, long long nslots, const ConstOne* ones, int nones, int dt) {
+    pdl_enter();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long k = i; k < nslots; k += stride) {
@@ -1779,7 +1791,7 @@ cudaError_t launch_init(Slot* slots, long long nslots, const ConstOne* ones, int
     long long blocks = (need + 255) / 256;
     if (blocks < 1) blocks = 1;
     if (blocks > 4096) blocks = 4096;
-    k_init<<<(unsigned)blocks, 256, 0, st>>>(slots, nslots, ones, nones, dt);
+    TN_LAUNCH(k_init, dim3((unsigned)blocks), dim3(256), 0, st, slots, nslots, ones, nones, dt);
     return cudaGetLastError();
 }
 
@@ -1790,6 +1802,7 @@ cudaError_t launch_init(Slot* slots, long long nslots, const ConstOne* ones, int
 // Output per member: [E, log2 norm, norm mantissa, norm exponent, sum <X>,
 // sum <ZZ>, <X_k>..., <Z_i Z_j>...].
 __global__ void k_final(const FinalTask* __restrict__ tasks, const Slot* __restrict__ slots) {
+    pdl_enter();
     const FinalTask& t = tasks[blockIdx.x];
     const Slot& nz = slots[t.norm_slot];
     const double mn = nz.mant;
@@ -1830,7 +1843,7 @@ __global__ void k_final(const FinalTask* __restrict__ tasks, const Slot* __restr
 
 cudaError_t launch_final(const FinalTask* tasks, int ntasks, const Slot* slots, cudaStream_t st) {
     if (ntasks <= 0) return cudaSuccess;
-    k_final<<<ntasks, 128, 0, st>>>(tasks, slots);
+    TN_LAUNCH(k_final, dim3(ntasks), dim3(128), 0, st, tasks, slots);
     return cudaGetLastError();
 }
 
@@ -1846,7 +1859,7 @@ cudaError_t absorb_plain(const AbsorbTask& t, long long nblocks, cudaStream_t st
         auto fn = k_absorb_one<T, KK, NN, MODE>;                                            \
         if (smem > 48 * 1024)                                                               \
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        fn<<<(unsigned)nblocks, kAbsorbThreads, smem, st>>>(t);                             \
+        fn<<<(unsigned)nblocks, kAbsorbThreads, smem, st>>>(t);                                               \
         return cudaGetLastError();                                                          \
     }
     TN_PLAIN_CASE(1, 1)

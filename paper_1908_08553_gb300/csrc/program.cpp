@@ -78,7 +78,7 @@ public:
         if (it != E_.end()) return it->second;
         // interior D = 3 steps off the tensor cores: keep the two layer factors
         // (Sec. 5, bra and ket layers) and absorb them one after the other
-        const bool factored = pg_.nsplit == 0 && s.K == 81 && s.N == 81;
+        const bool factored = pg_.nsplit == 0 && s.K == 81 && s.N == 81 && pg_.knobs.factor_d3;
         const int e = tensor(factored ? (int64_t)kFactorEntries : (int64_t)s.K * s.N, 0);
         pg_.tensors[e].factored = factored;
         Op op;
@@ -152,6 +152,7 @@ public:
     // the first step 4 or 16 -> (dn, h') = 4 x 4, the second (h', u) = 4 x 4 ->
     // N2, at least 8 trailing positions so every warp access covers whole sectors).
     bool pair_ok(const Step& a, const Step& b) const {
+        if (!pg_.knobs.fuse_pairs) return false;
         if (pg_.dt != DT_F32 || a.corner != b.corner || a.k != b.k || b.c != a.c + 1) return false;
         if (!(a.K == 4 || a.K == 16) || a.N != 16 || b.K != 16 || !(b.N == 1 || b.N == 4 || b.N == 16)) return false;
         return b.P == 4 * a.P && a.S == 4 * b.S && b.S >= 8;
@@ -191,6 +192,7 @@ public:
 
     // Whether the FP32 streaming absorption serves this step (it has the triple dot).
     bool dual_ok(const Step& s) const {
+        if (!pg_.knobs.site_triple) return false;
         const int v = absorb_variant(pg_.dt == DT_F64 ? 0 : 1, s.P, s.S, s.K, s.N);
         return pg_.dt == DT_F32 && !(pg_.nsplit && s.K == 81 && s.N == 81) && (v == 1 || v == 2);
     }
@@ -238,7 +240,7 @@ public:
     // C[m][n] = sum_k A(m,k) B(k,n); dot partner Cd -> scalar.
     int gemm(int A, int B, int64_t M, int64_t N, int64_t K, int64_t sam, int64_t sak,
              int64_t sbk, int64_t sbn, int Cd = -1) {
-        if (pg_.nsplit && M >= 128 && N >= 128 && K >= 64) {
+        if (pg_.nsplit && pg_.knobs.tc_products && M >= 128 && N >= 128 && K >= 64) {
             // tensor cores: C = A' B'^T with A'[m][k] = A(m,k) and B'[n][k] = B(k,n)
             const int Ap = tc_split(A, M, K, sam, sak);
             const int Bp = tc_split(B, N, K, sbn, sbk);
@@ -364,14 +366,15 @@ int64_t pack_arena(Program& pg) {
 }  // namespace
 
 std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sched,
-                                             tn_precision prec, tn_work work) {
-    return program_build_plan(plan_choose(L, W, D, sched, work), prec, work);
+                                             tn_precision prec, tn_work work, Knobs knobs) {
+    return program_build_plan(plan_choose(L, W, D, sched, work), prec, work, knobs);
 }
 
-std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision prec, tn_work work) {
+std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision prec, tn_work work, Knobs knobs) {
     auto pgp = std::make_shared<Program>();
     Program& pg = *pgp;
     pg.plan = plan;
+    pg.knobs = knobs;
     const int L = plan.L, W = plan.W, D = plan.D;
     pg.work = work;
     pg.dt = prec == TN_FP64 ? DT_F64 : DT_F32;

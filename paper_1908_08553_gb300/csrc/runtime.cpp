@@ -417,16 +417,18 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
 }  // namespace
 
 std::shared_ptr<const Program> program_cached(int L, int W, int D, tn_schedule sched, tn_precision prec,
-                                              tn_work work) {
+                                              tn_work work, int knobs_code) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, int, int>, std::shared_ptr<const Program>> cache;
-    const auto key = std::make_tuple(L, W, D, (int)sched, (int)prec, (int)work);
+    static std::map<std::tuple<int, int, int, int, int, int, int>, std::shared_ptr<const Program>> cache;
+    // the tuning table's choice for this shape unless the caller names one
+    if (knobs_code < 0) knobs_code = tuned_knobs(L, W, D, prec, work).code();
+    const auto key = std::make_tuple(L, W, D, (int)sched, (int)prec, (int)work, knobs_code);
     {
         std::lock_guard<std::mutex> g(mu);
         auto it = cache.find(key);
         if (it != cache.end()) return it->second;
     }
-    auto pg = program_build(L, W, D, sched, prec, work);
+    auto pg = program_build(L, W, D, sched, prec, work, Knobs::from_code(knobs_code));
     std::lock_guard<std::mutex> g(mu);
     return cache.emplace(key, pg).first->second;
 }
@@ -455,7 +457,7 @@ tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int
     for (int k = 0; k < n; ++k) {
         std::shared_ptr<const Program> pg;
         try {
-            pg = program_cached(L[k], W[k], D[k], sched, prec, work);
+            pg = program_cached(L[k], W[k], D[k], sched, prec, work, opts->knobs);
         } catch (const std::exception& e) {
             set_error(e.what());
             return TN_ERR_INVALID;

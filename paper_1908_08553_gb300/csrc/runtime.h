@@ -104,12 +104,13 @@ struct BatchOpts {
     cudaStream_t stream = nullptr;   // default: the context's stream
     bool async_alloc = false;        // cudaMallocAsync / cudaFreeAsync on that stream
     bool use_graph = true;           // capture the launch sequence on the first run
+    int knobs = -1;                  // program knobs (Knobs::code); -1: the tuning table's choice
 };
 tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int* D,
                        tn_precision prec, tn_schedule sched, tn_work work, bool alloc,
                        tn_batch** out, size_t* bytes, const BatchOpts* opts = nullptr);
 std::shared_ptr<const Program> program_cached(int L, int W, int D, tn_schedule sched, tn_precision prec,
-                                              tn_work work);
+                                              tn_work work, int knobs_code = -1);
 tn_status batch_run(tn_batch* b, cudaStream_t st);
 void batch_destroy(tn_batch* b);
 tn_status cuda_status(cudaError_t e, const char* what);

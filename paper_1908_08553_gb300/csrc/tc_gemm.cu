@@ -30,6 +30,7 @@
 #include <cuda_bf16.h>
 
 #include "ptx.cuh"
+#include "pdl.cuh"
 #include "tn_kernels.h"
 
 namespace tn {
@@ -153,6 +154,7 @@ __device__ __forceinline__ double block_reduce(double v, double* red, bool is_ma
 // One thread per (row, 8-wide k group) of the padded operand.
 __global__ void __launch_bounds__(256)
 k_tc_split(const TcSplitTask* __restrict__ tasks, int ntasks, const Slot* __restrict__ slots) {
+    pdl_enter();
     const long long tile = blockIdx.x;
     const TcSplitTask& t = tasks[find_task_tc(tasks, ntasks, tile)];
     const long long idx = (tile - t.tile0) * 256 + threadIdx.x;
@@ -195,6 +197,7 @@ k_tc_split(const TcSplitTask* __restrict__ tasks, int ntasks, const Slot* __rest
 template <int NSPLIT, bool DOT, int BN, int STAGES_>
 __global__ void __launch_bounds__(128, 1)
 k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, int* __restrict__ status) {
+    pdl_enter();
     constexpr int NB = BN / kTcM;                                   // 128-row B blocks per tile
     constexpr uint32_t kStageBytes = NSPLIT * (1 + NB) * kBlockBytes;   // A planes then B planes
     constexpr int STAGES =
@@ -416,6 +419,7 @@ __device__ __forceinline__ void split_store8(const float* x, unsigned char* base
 template <int NSPLIT, int MODE>
 __global__ void __launch_bounds__(128, 1)
 k_tc_absorb(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, int* __restrict__ status) {
+    pdl_enter();
     constexpr int NPROD = NSPLIT == 2 ? 3 : 6;
     constexpr int PA[6] = {NSPLIT == 2 ? 1 : 2, NSPLIT == 2 ? 0 : 1, NSPLIT == 2 ? 0 : 0, 1, 0, 0};
     constexpr int PB[6] = {NSPLIT == 2 ? 0 : 0, NSPLIT == 2 ? 1 : 1, NSPLIT == 2 ? 0 : 2, 0, 1, 0};
@@ -585,7 +589,7 @@ cudaError_t launch_tc_absorb(int nsplit, bool dot, const AbsorbTask* tasks, int 
         auto fn = k_tc_absorb<NS, MD>;                                                         \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                        \
-        fn<<<(unsigned)nblocks, 128, smem, st>>>(tasks, ntasks, slots, status);                \
+        TN_LAUNCH(fn, dim3((unsigned)nblocks), dim3(128), smem, st, tasks, ntasks, slots, status);                \
         return cudaGetLastError();                                                             \
     }
     if (nsplit == 2) { if (dot) TN_TCA_LAUNCH(2, 2) else TN_TCA_LAUNCH(2, 1) }
@@ -600,7 +604,7 @@ long long tc_split_tiles(long long Rp, long long Kp) { return (Rp * (Kp / 8) + 2
 cudaError_t launch_tc_split(const TcSplitTask* tasks, int ntasks, long long nblocks, const Slot* slots,
                             cudaStream_t st) {
     if (nblocks <= 0) return cudaSuccess;
-    k_tc_split<<<(unsigned)nblocks, 256, 0, st>>>(tasks, ntasks, slots);
+    TN_LAUNCH(k_tc_split, dim3((unsigned)nblocks), dim3(256), 0, st, tasks, ntasks, slots);
     return cudaGetLastError();
 }
 
@@ -623,7 +627,7 @@ cudaError_t launch_tc_gemm(int nsplit, bool dot, int bn, const TcGemmTask* tasks
             auto fn = k_tc_gemm<NS, DT, 128, SG>;                                              \
             cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
             if (e != cudaSuccess) return e;                                                    \
-            fn<<<(unsigned)nblocks, 128, smem, st>>>(tasks, ntasks, slots, status);            \
+            TN_LAUNCH(fn, dim3((unsigned)nblocks), dim3(128), smem, st, tasks, ntasks, slots, status);            \
             return cudaGetLastError();                                                         \
         }
         if (bn != 128) return cudaErrorInvalidValue;
@@ -636,7 +640,7 @@ cudaError_t launch_tc_gemm(int nsplit, bool dot, int bn, const TcGemmTask* tasks
         auto fn = k_tc_gemm<NS, DT, B, 0>;                                                     \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                        \
-        fn<<<(unsigned)nblocks, 128, smem, st>>>(tasks, ntasks, slots, status);                \
+        TN_LAUNCH(fn, dim3((unsigned)nblocks), dim3(128), smem, st, tasks, ntasks, slots, status);                \
         return cudaGetLastError();                                                             \
     }
     if (nsplit == 2 && bn == 256) { if (dot) TN_TC_LAUNCH(2, true, 256) else TN_TC_LAUNCH(2, false, 256) }

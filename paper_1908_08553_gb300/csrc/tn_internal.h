@@ -125,10 +125,28 @@ struct Op {
     double bytes = 0, macs = 0;
 };
 
+// Choices the program builder makes per lattice shape: each is exact (the
+// values computed are the same to rounding), only speed differs, so an
+// autotuner times them (autotune.cpp).  The defaults are the fixed rules.
+struct Knobs {
+    bool fuse_pairs = true;     // FP32 D = 2: two steps of a frame row in one pass (OP_ABSORB2)
+    bool site_triple = true;    // FP32 D <= 2: <X_k>, <Z_k> and the local norm in one absorb-dot
+    bool factor_d3 = true;      // FP32 / FP64 D = 3 interior steps: ket pass then bra pass
+    bool tc_products = true;    // BF16x3 / BF16x6: ring products on the tensor cores (else FP32 SIMT)
+    int code() const { return (fuse_pairs ? 1 : 0) | (site_triple ? 2 : 0) | (factor_d3 ? 4 : 0) | (tc_products ? 8 : 0); }
+    static Knobs from_code(int c) {
+        Knobs k;
+        k.fuse_pairs = c & 1; k.site_triple = c & 2; k.factor_d3 = c & 4; k.tc_products = c & 8;
+        return k;
+    }
+};
+constexpr int kDefaultKnobs = 15;
+
 // Result addressing inside one program: which scalar slots hold what.
 struct Program {
     Plan plan;
     tn_work work = TN_WORK_ENERGY;
+    Knobs knobs;
     DType dt = DT_F32;
     int nsplit = 0;               // 2 or 3: dense products on tensor cores (BF16 split)
     int esize = 4;
@@ -164,9 +182,12 @@ inline bool work_valid(tn_work w) {
 }
 
 std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sched,
-                                             tn_precision prec, tn_work work);
+                                             tn_precision prec, tn_work work, Knobs knobs = Knobs());
 // the same for a given plan (any orientation and cut)
-std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision prec, tn_work work);
+std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision prec, tn_work work,
+                                                  Knobs knobs = Knobs());
+// Knobs the tuning table holds for this shape (the defaults if it holds none).
+Knobs tuned_knobs(int L, int W, int D, tn_precision prec, tn_work work);
 // Consistency of a built program ("" if sound): every op runs after the
 // producers of its inputs and within their lifetimes, and no two tensors alive
 // in a common wave share arena bytes.

@@ -93,6 +93,13 @@ SIGNATURES = {
     "tn_ctx_inject_wait_timeout": (c_int, [c_void_p, c_int]),
     "tn_peak_probe": (c_int, [c_void_p, c_int, POINTER(c_double)]),
     "tn_ite_init_product": (c_int, [c_void_p]),
+    "tn_autotune": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_size_t]),
+    "tn_autotune_lookup": (c_int, [c_int, c_int, c_int, c_int, c_int, POINTER(c_int), POINTER(c_double),
+                                   POINTER(c_double), POINTER(c_int)]),
+    "tn_autotune_set": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int]),
+    "tn_autotune_clear": (c_int, []),
+    "tn_autotune_save": (c_int, [c_char_p]),
+    "tn_autotune_load": (c_int, [c_char_p]),
     "tn_bmps_norm": (c_int, [c_void_p, c_int, POINTER(tn_scalar)]),
     "tn_bmps_expectation": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, POINTER(c_double)]),
     "tn_bmps_energy": (c_int, [c_void_p, c_int, c_double, c_double, POINTER(tn_result)]),
@@ -395,6 +402,36 @@ def tn_absorb_dot_noalloc(dtype: int, x_in, E, adj, P: int, K: int, N: int, S: i
 
 def tn_ctx_set_profiling(ctx, on: bool):
     check(lib().tn_ctx_set_profiling(ctx, 1 if on else 0), "tn_ctx_set_profiling")
+
+
+def tn_autotune(ctx, Ls, Ws, Ds, prec: int, work: int = TN_WORK_ENERGY, reps: int = 3, max_bytes: int = 0):
+    """Time the program choices of every distinct shape and keep the fastest (see tn.h)."""
+    Ls, Ws, Ds = (np.ascontiguousarray(v, dtype=np.int32) for v in (Ls, Ws, Ds))
+    check(lib().tn_autotune(ctx, Ls.size, _ptr(Ls), _ptr(Ws), _ptr(Ds), prec, work, reps, max_bytes),
+          "tn_autotune")
+
+
+def tn_autotune_lookup(L: int, W: int, D: int, prec: int, work: int = TN_WORK_ENERGY) -> dict:
+    k, b, d, t = c_int(), c_double(), c_double(), c_int()
+    check(lib().tn_autotune_lookup(L, W, D, prec, work, byref(k), byref(b), byref(d), byref(t)),
+          "tn_autotune_lookup")
+    return {"knobs": k.value, "best_ms": b.value, "default_ms": d.value, "tuned": bool(t.value)}
+
+
+def tn_autotune_set(L: int, W: int, D: int, prec: int, work: int, knobs: int):
+    check(lib().tn_autotune_set(L, W, D, prec, work, knobs), "tn_autotune_set")
+
+
+def tn_autotune_clear():
+    check(lib().tn_autotune_clear(), "tn_autotune_clear")
+
+
+def tn_autotune_save(path: str):
+    check(lib().tn_autotune_save(path.encode()), "tn_autotune_save")
+
+
+def tn_autotune_load(path: str):
+    check(lib().tn_autotune_load(path.encode()), "tn_autotune_load")
 
 
 def tn_bmps_norm(lat, chi: int):

@@ -237,3 +237,40 @@ def test_bmps_arguments(cpu_ctx):
         assert e.value.status == tn.TN_ERR_INVALID
     finally:
         tn.tn_destroy_lattice(lat)
+
+
+def test_autotune_table_on_the_host(cpu_ctx, tmp_path):
+    """The tuning table: set / lookup / save / load / clear, and a shape's knobs
+    reach its program (no fused pairs when bit 0 is off)."""
+    tn.tn_autotune_clear()
+    try:
+        assert tn.tn_autotune_lookup(8, 8, 2, tn.TN_FP32) == {"knobs": 15, "best_ms": 0.0, "default_ms": 0.0,
+                                                             "tuned": False}
+        lat = tn.tn_create_lattice(cpu_ctx, 8, 8, 2)
+        try:
+            assert tn.tn_program_info(lat, tn.TN_FP32)["fused_pairs"] > 0
+            tn.tn_autotune_set(8, 8, 2, tn.TN_FP32, tn.TN_WORK_ENERGY, 14)
+            assert tn.tn_program_info(lat, tn.TN_FP32)["fused_pairs"] == 0
+        finally:
+            tn.tn_destroy_lattice(lat)
+        path = str(tmp_path / "tune.txt")
+        tn.tn_autotune_save(path)
+        tn.tn_autotune_clear()
+        assert not tn.tn_autotune_lookup(8, 8, 2, tn.TN_FP32)["tuned"]
+        tn.tn_autotune_load(path)
+        assert tn.tn_autotune_lookup(8, 8, 2, tn.TN_FP32) ["knobs"] == 14
+        with pytest.raises(tn.TNError):
+            tn.tn_autotune_set(8, 8, 2, tn.TN_FP32, tn.TN_WORK_ENERGY, 16)
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_autotune(cpu_ctx, [4], [4], [2], tn.TN_FP32)
+        assert e.value.status == tn.TN_ERR_NO_DEVICE
+        # D = 3 without the factored form builds the 81 x 81 site matrices again
+        lat = tn.tn_create_lattice(cpu_ctx, 4, 4, 3)
+        try:
+            f = tn.tn_program_info(lat, tn.TN_FP64)["arena_bytes"]
+            tn.tn_autotune_set(4, 4, 3, tn.TN_FP64, tn.TN_WORK_ENERGY, 15 & ~4)
+            assert tn.tn_program_info(lat, tn.TN_FP64)["arena_bytes"] > f
+        finally:
+            tn.tn_destroy_lattice(lat)
+    finally:
+        tn.tn_autotune_clear()
