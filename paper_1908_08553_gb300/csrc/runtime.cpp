@@ -95,7 +95,8 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 var = gemm_variant(b->dt, op.gm, op.gn, op.gk, op.sam, op.sak, op.sbk, op.sbn);
             } else if (op.kind == OP_TC_GEMM || op.kind == OP_TC_GEMM_DOT) {
                 // short k range (+10000), planes, tile width
-                var = (op.Kp <= kTcShortK ? 10000 : 0) + op.nsplit * 1000 + tc_gemm_bn(op.nsplit, op.gn, op.Kp);
+                var = (op.Kp <= kTcShortK ? 10000 : 0) + op.nsplit * 1000 +
+                      tc_gemm_bn(op.nsplit, op.kind == OP_TC_GEMM_DOT, op.gn, op.Kp);
             }
             groups[std::make_tuple(op.level, (int)op.kind, K, N, var)].push_back({mi, oi});
         }
@@ -139,7 +140,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
             else if (kind == OP_ABSORB2_DOT) npart += absorb2_tiles(op.P, op.S);
             else if (kind == OP_TC_GEMM_DOT) {
                 const int bn = std::get<4>(kv.first) % 1000;
-                npart += ((op.gm + 127) / 128) * ((op.gn + bn - 1) / bn) * ((op.Kp + kGemmKSlice - 1) / kGemmKSlice);
+                npart += ((op.gm + 127) / 128) * ((op.gn + bn - 1) / bn);   // one partial per tile
             }
         }
     }
@@ -305,9 +306,11 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 t.slot_C = slot_of(r.member, op.out);
                 t.tiles_m = (op.gm + 127) / 128;
                 t.tiles_n = (int)((op.gn + bn - 1) / bn);
-                const long long ksp = kind == OP_TC_GEMM_DOT ? (op.Kp + kGemmKSlice - 1) / kGemmKSlice : 1;
-                t.ksplit = (int)ksp;
-                t.kchunks = ksp > 1 ? kGemmKSlice / kTcChunk : op.Kp / kTcChunk;
+                // products fused with a dot keep the whole k range in one CTA (its
+                // 512-term slices are pipelined inside, launch_tc_gemm_dot)
+                const long long ksp = 1;
+                t.ksplit = 1;
+                t.kchunks = op.Kp / kTcChunk;
                 const long long nt = t.tiles_m * t.tiles_n * ksp;
                 t.ntiles = (int)nt;
                 t.tile0 = tile;
@@ -575,10 +578,13 @@ cudaError_t issue(tn_batch* b, cudaStream_t st, std::vector<std::pair<cudaEvent_
                 e = launch_tc_split(static_cast<const TcSplitTask*>(tp), L.ntasks, L.nblocks, slots, st);
                 break;
             case OP_TC_GEMM:
-            case OP_TC_GEMM_DOT:
-                e = launch_tc_gemm((L.variant % 10000) / 1000, L.kind == OP_TC_GEMM_DOT, L.variant % 1000,
+                e = launch_tc_gemm((L.variant % 10000) / 1000, false, L.variant % 1000,
                                    static_cast<const TcGemmTask*>(tp), L.ntasks, L.nblocks, slots, status, st,
                                    L.variant >= 10000);
+                break;
+            case OP_TC_GEMM_DOT:
+                e = launch_tc_gemm_dot((L.variant % 10000) / 1000, L.variant % 1000,
+                                       static_cast<const TcGemmTask*>(tp), L.ntasks, L.nblocks, slots, status, st);
                 break;
         }
         if (ev) cudaEventRecord((*ev)[li].second, st);

@@ -25,6 +25,7 @@
 // producer, and all four warps read the accumulator from tensor memory
 // (lane = output row) for the epilogue.  Every wait is bounded: on time-out
 // the kernel records an error code, drains, frees its tensor memory and exits.
+#include <algorithm>
 #include <cstdint>
 
 #include <cuda_bf16.h>
@@ -38,6 +39,7 @@ namespace tn {
 namespace {
 
 constexpr int kTcM = 128, kTcN = 128, kTcK = kTcChunk;   // tile rows, tile cols, k per chunk
+constexpr uint32_t kTcRingBytes = 221184;              // 216 KiB of stage ring (3 x 72 KiB for 3 planes x 256)
 constexpr uint32_t kBlockBytes = kTcM * kTcK * 2;     // one 128 x 32 BF16 block (8 KiB)
 constexpr uint32_t kTcSBO = (kTcK / 8) * 128;         // next 8-row group inside a block
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -201,7 +203,7 @@ k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
     constexpr int NB = BN / kTcM;                                   // 128-row B blocks per tile
     constexpr uint32_t kStageBytes = NSPLIT * (1 + NB) * kBlockBytes;   // A planes then B planes
     constexpr int STAGES =
-        STAGES_ > 0 ? STAGES_ : ((196608u / kStageBytes) >= 6 ? 6 : (int)(196608u / kStageBytes));
+        STAGES_ > 0 ? STAGES_ : ((kTcRingBytes / kStageBytes) >= 6 ? 6 : (int)(kTcRingBytes / kStageBytes));
     constexpr int NPROD = NSPLIT == 2 ? 3 : 6;
     // products (plane of A, plane of B), smallest terms first
     constexpr int PA[6] = {NSPLIT == 2 ? 1 : 2, NSPLIT == 2 ? 0 : 1, NSPLIT == 2 ? 0 : 0, 1, 0, 0};
@@ -367,6 +369,210 @@ k_tc_gemm(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
                 slots[t.slot_C].mant = acc;
                 slots[t.slot_C].X = slots[t.slot_A].X + eA + slots[t.slot_B].X + eB + slots[t.slot_D].X + eD;
             }
+        }
+    }
+}
+
+// ---- products fused with a dot: whole k range per CTA, slices pipelined ----
+//
+// <A B^T, Dm> over one 128 x BN output tile: the k range is cut into slices
+// of kGemmKSlice (512) terms; the tensor cores accumulate slice s into one of
+// two TMEM accumulators while four epilogue warps take the other: each reads
+// its rows of slice s - 1's product, forms the compensated FP32 dot with its
+// rows of Dm and adds it to an FP64 sum -- the same numerics as one CTA per
+// slice, without refilling the pipeline for every 512 terms.  Warp 0 stages
+// k-chunks (thread 0, cp.async.bulk), warp 1 issues the MMAs (thread 0) and
+// owns the tensor memory, warps 2.. are the epilogue: BN / 32 warps, warp w
+// reads TMEM lanes 32 (w mod 4) .. for the 128 columns (w - 2) / 4 and holds
+// that part of its row of the Dm tile in registers for every slice.  One FP64
+// partial per tile; the last tile to finish
+// sums them in index order.  Every wait is bounded; on a time-out the kernel
+// records the error, waits (bounded) for its copies and MMAs, frees its
+// tensor memory and exits.
+constexpr int kDotSlice = (int)(kGemmKSlice / kTcK);   // chunks per slice
+__host__ __device__ constexpr int dot_threads(int bn) { return 64 + 32 * (bn / 32); }
+
+template <int NSPLIT, int BN, int STAGES>
+__global__ void __launch_bounds__(dot_threads(BN), 1)
+k_tc_gemm_dot(const TcGemmTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, int* __restrict__ status) {
+    pdl_enter();
+    constexpr int NB = BN / kTcM;
+    constexpr uint32_t kStageBytes = NSPLIT * (1 + NB) * kBlockBytes;
+    constexpr int NPROD = NSPLIT == 2 ? 3 : 6;
+    constexpr int PA[6] = {NSPLIT == 2 ? 1 : 2, NSPLIT == 2 ? 0 : 1, NSPLIT == 2 ? 0 : 0, 1, 0, 0};
+    constexpr int PB[6] = {NSPLIT == 2 ? 0 : 0, NSPLIT == 2 ? 1 : 1, NSPLIT == 2 ? 0 : 2, 0, 1, 0};
+    constexpr uint32_t kIdescN = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                 ((uint32_t)(kTcM >> 4) << 24);
+    constexpr int kGroup = 8;
+    constexpr int kEpiWarps = BN / 32;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_full[2], acc_empty[2], done_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int fail_sh;
+    __shared__ double red[dot_threads(BN) / 32];
+    __shared__ int is_last;
+
+    const long long tile = blockIdx.x;
+    const TcGemmTask& t = tasks[find_task_tc(tasks, ntasks, tile)];
+    const long long local = tile - t.tile0;
+    const long long per_group = (long long)kGroup * t.tiles_n;
+    const long long g = local / per_group, gi = local % per_group;
+    const long long grows = min((long long)kGroup, t.tiles_m - g * kGroup);
+    const long long tm = g * kGroup + gi % grows, tn_ = gi / grows;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long nchunks = t.Kp / kTcK;
+    const int nslices = (int)((nchunks + kDotSlice - 1) / kDotSlice);
+    unsigned char* ring = smem + ((1024 - (smem_u32(smem) & 1023)) & 1023);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], kEpiWarps); }
+        mbar_init(&done_bar, 1);
+        fail_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(&tmem_base_sh, 2 * BN);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    const char* Ab = static_cast<const char*>(t.A) + tm * nchunks * (long long)kBlockBytes;
+    const char* Bb = static_cast<const char*>(t.B) + tn_ * NB * nchunks * (long long)kBlockBytes;
+    int armed[STAGES];
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) armed[s] = 0;
+    double dsum = 0.0;
+    if (warp == 0) {
+        if (lane == 0) {
+            for (long long c = 0; c < nchunks; ++c) {
+                const int s = (int)(c % STAGES);
+                if (c >= STAGES && !mbar_wait(&empty_bar[s], (uint32_t)((c / STAGES - 1) & 1))) {
+                    atomicExch(&fail_sh, 1);
+                    break;
+                }
+                if (*(volatile int*)&fail_sh) break;
+                unsigned char* st = ring + s * kStageBytes;
+                armed[s] += 1;
+                mbar_expect_tx(&full_bar[s], kStageBytes);
+                for (int p = 0; p < NSPLIT; ++p) {
+                    bulk_g2s(st + p * kBlockBytes, Ab + p * t.a_plane_bytes + c * kBlockBytes, kBlockBytes,
+                             &full_bar[s]);
+                    for (int h = 0; h < NB; ++h)
+                        bulk_g2s(st + (NSPLIT + p * NB + h) * kBlockBytes,
+                                 Bb + p * t.b_plane_bytes + (h * nchunks + c) * kBlockBytes, kBlockBytes,
+                                 &full_bar[s]);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            for (long long c = 0; c < nchunks; ++c) {
+                const int sl = (int)(c / kDotSlice), buf = sl & 1;
+                const bool first = (c % kDotSlice) == 0;
+                if (first && sl >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)((sl / 2 - 1) & 1))) {
+                    atomicExch(&fail_sh, 1);
+                    break;
+                }
+                const int s = (int)(c % STAGES);
+                if (!mbar_wait(&full_bar[s], (uint32_t)((c / STAGES) & 1))) { atomicExch(&fail_sh, 1); break; }
+                if (*(volatile int*)&fail_sh) break;
+                tc_fence_after();
+                const uint32_t stg = smem_u32(ring + s * kStageBytes);
+                const uint32_t acc = tmem + (uint32_t)(buf * BN);
+#pragma unroll
+                for (int kk = 0; kk < kTcK / 16; ++kk) {
+#pragma unroll
+                    for (int q = 0; q < NPROD; ++q) {
+                        const uint64_t da = smem_desc(stg + PA[q] * kBlockBytes + kk * 256);
+                        const uint64_t db = smem_desc(stg + (NSPLIT + PB[q] * NB) * kBlockBytes + kk * 256);
+                        tc_mma(acc, da, db, kIdescN, (!first || kk > 0 || q > 0) ? 1u : 0u);
+                    }
+                }
+                tc_commit(&empty_bar[s]);
+                if ((c % kDotSlice) == kDotSlice - 1 || c == nchunks - 1) tc_commit(&acc_full[buf]);
+            }
+            tc_commit(&done_bar);
+        }
+    } else {
+        // epilogue: warps 2.., TMEM lane quadrant warp % 4, 128 columns (warp - 2) / 4
+        const int quad = warp & 3, half = (warp - 2) >> 2;
+        const long long row = tm * kTcM + quad * 32 + lane;
+        const long long n0 = tn_ * BN + half * 128;
+        const int eD = slot_shift_tc(&slots[t.slot_D]);
+        const float sD = pow2f(-eD);
+        // this thread's row of the Dm tile, rescaled, held in registers for every slice
+        // (zero beyond the matrix, so padded rows and columns add nothing)
+        float dm[128];
+        {
+            const float* Dm = static_cast<const float*>(t.Dm) + row * t.N;
+#pragma unroll
+            for (int i = 0; i < 128; ++i) {
+                const long long n = n0 + i;
+                dm[i] = (row < t.M && n < t.N) ? __ldg(Dm + n) * sD : 0.0f;
+            }
+        }
+        for (int sl = 0; sl < nslices; ++sl) {
+            const int buf = sl & 1;
+            if (!mbar_wait(&acc_full[buf], (uint32_t)((sl / 2) & 1))) { atomicExch(&fail_sh, 1); break; }
+            tc_fence_after();
+            const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + half * 128);
+            float s = 0.0f, comp = 0.0f;     // compensated (Neumaier) sum of this slice's products
+#pragma unroll
+            for (int cb = 0; cb < 128; cb += 16) {
+                float v[16];
+                tmem_ld16(lane_addr + (uint32_t)cb, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float x = v[i] * dm[cb + i], tt = s + x;
+                    comp += (fabsf(s) >= fabsf(x)) ? (s - tt) + x : (x - tt) + s;
+                    s = tt;
+                }
+            }
+            dsum += (double)s + (double)comp;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        }
+    }
+    // every MMA issued has completed (bounded), and no copy is left in flight
+    const bool ok = mbar_wait(&done_bar, 0u);
+    if (!ok) atomicExch(&fail_sh, 1);
+    __syncthreads();
+    const bool failed = *(volatile int*)&fail_sh != 0;
+    if (failed) {
+        if (threadIdx.x == 0) atomicExch(status, 1);
+        if (warp == 0 && lane == 0)
+            for (int s = 0; s < STAGES; ++s)
+                if (armed[s] > 0) (void)mbar_wait(&full_bar[s], (uint32_t)((armed[s] - 1) & 1));
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, 2 * BN);
+    if (failed) return;
+    const int eA = slot_shift_tc(&slots[t.slot_A]), eB = slot_shift_tc(&slots[t.slot_B]);
+    const double part = block_reduce(dsum, red, false);
+    if (threadIdx.x == 0) {
+        t.partial[local] = part;
+        __threadfence();
+        const unsigned prev = atomicAdd(&slots[t.slot_C].count, 1u);
+        is_last = (prev == (unsigned)(t.ntiles - 1));
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        double accp = 0.0;
+        for (int k = threadIdx.x; k < t.ntiles; k += blockDim.x) accp += __ldcg(t.partial + k);
+        accp = block_reduce(accp, red, false);
+        if (threadIdx.x == 0) {
+            const int eD = slot_shift_tc(&slots[t.slot_D]);
+            slots[t.slot_C].mant = accp;
+            slots[t.slot_C].X = slots[t.slot_A].X + eA + slots[t.slot_B].X + eB + slots[t.slot_D].X + eD;
         }
     }
 }
@@ -608,9 +814,34 @@ cudaError_t launch_tc_split(const TcSplitTask* tasks, int ntasks, long long nblo
     return cudaGetLastError();
 }
 
-int tc_gemm_bn(int nsplit, long long N, long long Kp) {
+cudaError_t launch_tc_gemm_dot(int nsplit, int bn, const TcGemmTask* tasks, int ntasks, long long nblocks,
+                               Slot* slots, int* status, cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    const int nb = bn / kTcM;
+    const uint32_t stage = (uint32_t)nsplit * (1 + nb) * kBlockBytes;
+    // as many stages as 216 KiB hold, at most 4 (3 for 3 planes x 256)
+    const int stages = (int)std::min<uint32_t>(4, kTcRingBytes / stage);
+    const size_t smem = (size_t)stages * stage + 1024;
+#define TN_TCD_LAUNCH(NS, B)                                                                   \
+    {                                                                                          \
+        auto fn = k_tc_gemm_dot<NS, B, (NS) * (1 + (B) / 128) * 8192 * 4 <= (int)kTcRingBytes ? 4 : 3>; \
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                        \
+        TN_LAUNCH(fn, dim3((unsigned)nblocks), dim3(dot_threads(B)), smem, st, tasks, ntasks, slots, status); \
+        return cudaGetLastError();                                                             \
+    }
+    if (nsplit == 2 && bn == 256) TN_TCD_LAUNCH(2, 256)
+    if (nsplit == 3 && bn == 256) TN_TCD_LAUNCH(3, 256)
+    if (nsplit == 2 && bn == 128) TN_TCD_LAUNCH(2, 128)
+    if (nsplit == 3 && bn == 128) TN_TCD_LAUNCH(3, 128)
+#undef TN_TCD_LAUNCH
+    return cudaErrorInvalidValue;
+}
+
+int tc_gemm_bn(int nsplit, bool dot, long long N, long long Kp) {
+    (void)nsplit; (void)dot;
     if (Kp <= kTcShortK) return 128;
-    return (nsplit == 2 && N > 128) ? 256 : 128;
+    return N > 128 ? 256 : 128;
 }
 
 cudaError_t launch_tc_gemm(int nsplit, bool dot, int bn, const TcGemmTask* tasks, int ntasks, long long nblocks,
@@ -618,7 +849,7 @@ cudaError_t launch_tc_gemm(int nsplit, bool dot, int bn, const TcGemmTask* tasks
     if (nblocks <= 0) return cudaSuccess;
     const int nb = bn / kTcM;
     const uint32_t stage = (uint32_t)nsplit * (1 + nb) * kBlockBytes;
-    const int stages = short_k ? (nsplit == 2 ? 3 : 2) : ((196608u / stage) >= 6 ? 6 : (int)(196608u / stage));
+    const int stages = short_k ? (nsplit == 2 ? 3 : 2) : ((kTcRingBytes / stage) >= 6 ? 6 : (int)(kTcRingBytes / stage));
     const size_t smem = (size_t)stages * stage + 1024;
     if (short_k) {
         // 128-wide tiles, 2 (3 planes) or 3 (2 planes) stages: ~97 KB, two CTAs per SM
@@ -631,8 +862,9 @@ cudaError_t launch_tc_gemm(int nsplit, bool dot, int bn, const TcGemmTask* tasks
             return cudaGetLastError();                                                         \
         }
         if (bn != 128) return cudaErrorInvalidValue;
-        if (nsplit == 2) { if (dot) TN_TCS_LAUNCH(2, true, 3) else TN_TCS_LAUNCH(2, false, 3) }
-        if (dot) TN_TCS_LAUNCH(3, true, 2) else TN_TCS_LAUNCH(3, false, 2)
+        if (dot) return cudaErrorInvalidValue;
+        if (nsplit == 2) TN_TCS_LAUNCH(2, false, 3)
+        TN_TCS_LAUNCH(3, false, 2)
 #undef TN_TCS_LAUNCH
     }
 #define TN_TC_LAUNCH(NS, DT, B)                                                                \
@@ -643,9 +875,12 @@ cudaError_t launch_tc_gemm(int nsplit, bool dot, int bn, const TcGemmTask* tasks
         TN_LAUNCH(fn, dim3((unsigned)nblocks), dim3(128), smem, st, tasks, ntasks, slots, status);                \
         return cudaGetLastError();                                                             \
     }
-    if (nsplit == 2 && bn == 256) { if (dot) TN_TC_LAUNCH(2, true, 256) else TN_TC_LAUNCH(2, false, 256) }
-    if (nsplit == 2) { if (dot) TN_TC_LAUNCH(2, true, 128) else TN_TC_LAUNCH(2, false, 128) }
-    if (dot) TN_TC_LAUNCH(3, true, 128) else TN_TC_LAUNCH(3, false, 128)
+    // products fused with a dot go to launch_tc_gemm_dot; this kernel stores
+    if (dot) return cudaErrorInvalidValue;
+    if (nsplit == 2 && bn == 256) TN_TC_LAUNCH(2, false, 256)
+    if (nsplit == 3 && bn == 256) TN_TC_LAUNCH(3, false, 256)
+    if (nsplit == 2) TN_TC_LAUNCH(2, false, 128)
+    TN_TC_LAUNCH(3, false, 128)
 #undef TN_TC_LAUNCH
 }
 

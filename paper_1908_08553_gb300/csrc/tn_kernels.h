@@ -222,13 +222,19 @@ long long tc_split_tiles(long long Rp, long long Kp);
 cudaError_t launch_tc_split(const TcSplitTask* tasks, int ntasks, long long nblocks, const Slot* slots,
                             cudaStream_t st);
 // status: set to 1 if a bounded wait inside the kernel timed out.
-// Output tile 128 x bn, bn = tc_gemm_bn(nsplit, N, Kp): 256 for 2 planes and
-// N > 128, except short k ranges (Kp <= kTcShortK), which take 128-wide tiles
-// and a shallow stage ring (launch with short_k) so two CTAs share an SM.
+// Output tile 128 x bn, bn = tc_gemm_bn(nsplit, dot, N, Kp): 256 for N > 128
+// (the staged bytes per multiply-add halve against 128-wide tiles), except
+// short k ranges (Kp <= kTcShortK), which take 128-wide tiles and, when
+// stored, a shallow stage ring (launch with short_k) so two CTAs share an SM.
 constexpr long long kTcShortK = 1024;
-int tc_gemm_bn(int nsplit, long long N, long long Kp);
+int tc_gemm_bn(int nsplit, bool dot, long long N, long long Kp);
 cudaError_t launch_tc_gemm(int nsplit, bool dot, int bn, const TcGemmTask* tasks, int ntasks, long long nblocks,
                            Slot* slots, int* status, cudaStream_t st, bool short_k = false);
+// Products fused with a dot (TcGemmTask with ksplit = 1, kchunks = the whole k
+// range): one CTA per 128 x bn tile, 512-term slices pipelined through two
+// TMEM accumulators (see tc_gemm.cu).  bn from tc_gemm_bn.
+cudaError_t launch_tc_gemm_dot(int nsplit, int bn, const TcGemmTask* tasks, int ntasks, long long nblocks,
+                               Slot* slots, int* status, cudaStream_t st);
 // Rows of every split operand are padded to a multiple of this.
 constexpr long long kTcRowPad = 256;
 // Reduction (k) width of one staged block of a split operand.
