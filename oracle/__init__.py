@@ -55,6 +55,8 @@ def lib():
         _lib.or_peps_sz.argtypes = [i32, i32, i32, P, P]
         _lib.or_peps_bond_ops.argtypes = [i32, i32, i32, P, i32, i32, P]
         _lib.or_peps_bond_ops.restype = i32
+        _lib.or_peps_pair.argtypes = [i32, i32, i32, P, i32, i32, i32, i32, P]
+        _lib.or_peps_pair.restype = i32
         for f in (_lib.or_grid_contract, _lib.or_peps_norm, _lib.or_peps_norm_all_cuts,
                   _lib.or_peps_observables, _lib.or_peps_expect_one,
                   _lib.or_ising_enumerate, _lib.or_num_threads, _lib.or_peps_sz):
@@ -197,6 +199,23 @@ def bond_correlators(L: int, W: int, D: int, A: np.ndarray, op_a: str, op_b: str
     code = {"x": 1, "z": 2}
     lib().or_peps_bond_ops(L, W, D, _ptr(A), code[op_a], code[op_b], _ptr(out))
     return out[:nb]
+
+
+def pair(L: int, W: int, D: int, A: np.ndarray, op_a: str, i: int, op_b: str, j: int) -> float:
+    """<A_i B_j> for any distinct sites (row-major), A, B in {'x', 'z', 'y'}, one full
+    contraction per observable.  A real state has <X_i Y_j> = <Z_i Y_j> = 0
+    exactly; <Y_i Y_j> is -<R_i R_j> with the real antisymmetric R, Y = i R."""
+    A = _check_sites(L, W, D, A)
+    ya, yb = op_a == "y", op_b == "y"
+    if ya != yb:
+        if i == j:
+            raise ValueError("sites must differ")
+        return 0.0
+    code = {"x": 1, "z": 2, "y": 4}
+    v = np.zeros(1)
+    if lib().or_peps_pair(L, W, D, _ptr(A), code[op_a], i, code[op_b], j, _ptr(v)) != 0:
+        raise ValueError("bad sites or operators")
+    return -float(v[0]) if ya else float(v[0])
 
 
 def expect_one(L: int, W: int, D: int, A: np.ndarray, op: str, i: int = 0, j: int = 0):

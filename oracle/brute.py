@@ -136,3 +136,30 @@ def ground_energy(L: int, W: int, J: float, h: float) -> float:
     H = hamiltonian(L, W, J, h)
     w = eigsh(H, k=1, which="SA", return_eigenvectors=False, tol=1e-10)
     return float(w[0])
+
+
+def pair_correlator(L: int, W: int, D: int, flat: np.ndarray, op_a: str, i: int, op_b: str, j: int) -> float:
+    """<A_i B_j> = psi^dagger A_i B_j psi / psi^dagger psi for any sites i != j,
+    A, B in {'x', 'y', 'z'} as complex 2 x 2 Pauli matrices on the basis
+    (p = 0 <-> sigma = -1, p = 1 <-> sigma = +1), applied to the state vector."""
+    psi = state_vector(L, W, D, flat).astype(np.complex128)
+    N = L * W
+    idx = np.arange(psi.size)
+    # the Pauli matrices on (sigma = +1, sigma = -1), reordered to (p = 0, p = 1)
+    std = {"x": np.array([[0, 1], [1, 0]], complex), "y": np.array([[0, -1j], [1j, 0]]),
+           "z": np.array([[1, 0], [0, -1]], complex)}
+
+    def op(name):
+        m = std[name]
+        return m[::-1, ::-1]       # index p = 1 - (position in (+1, -1))
+
+    def apply(M, k, v):
+        bit = (idx >> k) & 1
+        flipped = v[idx ^ (1 << k)]
+        # (M v)[s] = M[s_k, s_k] v[s] + M[s_k, 1 - s_k] v[s with k flipped]
+        return M[bit, bit] * v + M[bit, 1 - bit] * flipped
+
+    assert 0 <= i < N and 0 <= j < N and i != j
+    w = apply(op(op_a), i, apply(op(op_b), j, psi))
+    val = np.vdot(psi, w) / np.vdot(psi, psi)
+    return float(val.real) if abs(val.imag) < 1e-12 * max(1.0, abs(val)) else complex(val)

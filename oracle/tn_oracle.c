@@ -205,6 +205,10 @@ static void bottom_boundaries(const grid_t *g, bnd_t *bots) {
 static const double OP_I[4] = {1, 0, 0, 1};
 static const double OP_X[4] = {0, 1, 1, 0};
 static const double OP_Z[4] = {-1, 0, 0, 1};
+/* Y = i R on the basis (p = 0 <-> -1, p = 1 <-> +1): R is real and
+ * antisymmetric, so for real amplitudes <Y_i> = 0, <A_i Y_j> = 0 for A = X, Z,
+ * and <Y_i Y_j> = -<R_i R_j> (the sign convention of R cancels in R R). */
+static const double OP_R[4] = {0, 1, -1, 0};
 
 /*
  * Double-layer (bra x ket) site tensor with operator O on the physical leg:
@@ -515,6 +519,40 @@ int or_peps_bond_ops(int L, int W, int D, const double *A, int op_a, int op_b, d
 }
 
 /* E = -J sum <zz> - h sum <x>; also returns everything or_peps_observables does. */
+/*
+ * <A_i B_j> for any two distinct sites i, j (row-major indices), A and B in
+ * {X (1), Z (2), R (4)}: the network with A at site i and B at site j, swept
+ * row by row, over the norm swept the same way -- one full contraction per
+ * observable, as Sec. 5 counts them.  Returns the ratio in *val.
+ */
+int or_peps_pair(int L, int W, int D, const double *A, int op_a, int i, int op_b, int j, double *val) {
+    if (i == j || i < 0 || j < 0 || i >= L * W || j >= L * W) return -1;
+    const double *oa = op_a == 1 ? OP_X : (op_a == 2 ? OP_Z : (op_a == 4 ? OP_R : NULL));
+    const double *ob = op_b == 1 ? OP_X : (op_b == 2 ? OP_Z : (op_b == 4 ? OP_R : NULL));
+    if (!oa || !ob) return -1;
+    grid_t g = norm_grid(L, W, D, A);
+    size_t *off = site_offsets(L, W, D);
+    int d[4];
+    site_dims(L, W, D, i / W, i % W, d);
+    double *ea = double_layer(A + off[i], d, oa);
+    site_dims(L, W, D, j / W, j % W, d);
+    double *eb = double_layer(A + off[j], d, ob);
+    double **over = (double **)calloc((size_t)W, sizeof(double *));
+    bnd_t n0 = bnd_one(), n1 = bnd_one();
+    for (int r = 0; r < L; ++r) {
+        absorb_row(&g, r, NULL, &n0);
+        over[i % W] = (i / W == r) ? ea : NULL;
+        if (j / W == r) over[j % W] = eb;
+        absorb_row(&g, r, over, &n1);
+        over[i % W] = NULL;
+        over[j % W] = NULL;
+    }
+    *val = ratio(n1.v[0], n1.e, n0.v[0], n0.e);
+    free(n0.v); free(n1.v); free(over); free(ea); free(eb); free(off);
+    grid_free(&g);
+    return 0;
+}
+
 /*
  * One observable alone, keeping only two boundaries (for sampled checks of
  * lattices too large for the cached version).  op: 0 = norm (i, j ignored),
