@@ -83,7 +83,10 @@ typedef enum {
     TN_OP_NORM = 0,        /* <Psi|Psi> (returned as a ratio 1) */
     TN_OP_X = 1,           /* <X_i>, Eq. mx */
     TN_OP_ZZ = 2,          /* <Z_i Z_j> for nearest neighbours i, j, Eq. cij first term */
-    TN_OP_Z = 3            /* <Z_i>, Eq. mz with Pauli Z */
+    TN_OP_Z = 3,           /* <Z_i>, Eq. mz with Pauli Z */
+    TN_OP_Y = 4            /* Pauli Y (two-site correlators only): Y = i R with the real
+                              R = [[0, 1], [-1, 0]] on p = 0, 1, so for the real states
+                              here <A_i Y_j> = 0 (A = X, Z) and <Y_i Y_j> = -<R_i R_j> */
 } tn_op;
 
 /* value = mant * 2^exp2 (the norm of a large lattice leaves the FP64 range). */
@@ -186,12 +189,22 @@ tn_status tn_expectation(tn_lattice *lat, tn_precision prec, int op, int i, int 
 tn_status tn_energy(tn_lattice *lat, double J, double h, tn_precision prec, tn_result *out);
 /* Nearest-neighbour two-site correlators <A_i B_j> (blocking, AUTO schedule):
  * one Pauli operator on each site of every bond, A = op_a on the bond's first
- * site i (left or upper) and B = op_b on j, op_a and op_b each TN_OP_X or
- * TN_OP_Z (the insertion of Sec. 5 with operators other than Z Z; real
- * arithmetic, so Y is not offered).  out: nb = L(W-1) + W(L-1) doubles,
+ * site i (left or upper) and B = op_b on j, op_a and op_b each TN_OP_X,
+ * TN_OP_Y or TN_OP_Z (the insertion of Sec. 5 with operators other than Z Z;
+ * Y as described at TN_OP_Y).  out: nb = L(W-1) + W(L-1) doubles,
  * caller-owned, bonds in the order of tn_result.szsz.  TN_ERR_INVALID for
  * other operators. */
 tn_status tn_bond_correlators(tn_lattice *lat, tn_precision prec, int op_a, int op_b, double *out);
+/* <A_{i[k]} B_{j[k]}> for n arbitrary pairs of distinct sites (row-major
+ * indices; Eq. cij for any i, j), A = op_a, B = op_b in {TN_OP_X, TN_OP_Y,
+ * TN_OP_Z}, exactly (blocking, AUTO schedule).  The contraction program is
+ * built for the call: pairs inside one corner carry the chain from the first
+ * site to the second and meet that corner's environment; pairs in two corners
+ * regrow both and close the ring by one product (adjacent corners) or two
+ * (diagonal corners).  out: n doubles, caller-owned.  TN_ERR_INVALID for bad
+ * sites or operators. */
+tn_status tn_pair_correlators(tn_lattice *lat, tn_precision prec, int op_a, int op_b, int n, const int *i,
+                              const int *j, double *out);
 /* As tn_energy with an explicit schedule. */
 tn_status tn_energy_sched(tn_lattice *lat, double J, double h, tn_precision prec,
                           tn_schedule sched, tn_result *out);

@@ -1,5 +1,6 @@
 // extern "C" entry points of libtn (declared in include/tn.h).  Every function
 // catches exceptions and returns a tn_status; no exception crosses the ABI.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -374,18 +375,87 @@ tn_status tn_expectation(tn_lattice* lat, tn_precision prec, int op, int i, int 
     TN_GUARD_END
 }
 
+namespace {
+// Pauli operator code -> the real operator contracted (Y is i R).
+int pair_phys(int op) {
+    return op == TN_OP_X ? (int)PH_X : (op == TN_OP_Z ? (int)PH_Z : (op == TN_OP_Y ? (int)PH_R : -1));
+}
+}  // namespace
+
 tn_status tn_bond_correlators(tn_lattice* lat, tn_precision prec, int op_a, int op_b, double* out) {
     TN_GUARD_BEGIN
     if (!lat || !out) return TN_ERR_INVALID;
-    auto phys = [](int op) { return op == TN_OP_X ? (int)PH_X : (op == TN_OP_Z ? (int)PH_Z : -1); };
-    const int a = phys(op_a), b = phys(op_b);
-    if (a < 0 || b < 0) { set_error("bond operators must be TN_OP_X or TN_OP_Z"); return TN_ERR_INVALID; }
+    const int a = pair_phys(op_a), b = pair_phys(op_b);
+    if (a < 0 || b < 0) { set_error("bond operators must be TN_OP_X, TN_OP_Y or TN_OP_Z"); return TN_ERR_INVALID; }
     const int L = lat->L, W = lat->W, nb = L * (W - 1) + W * (L - 1);
+    if ((a == PH_R) != (b == PH_R)) {
+        // one Y: <A_i Y_j> = i <A_i R_j> is real only if zero (real amplitudes)
+        if (!lat->ctx || lat->ctx->device < 0) { set_error("context has no device"); return TN_ERR_NO_DEVICE; }
+        std::fill(out, out + nb, 0.0);
+        return TN_OK;
+    }
     std::vector<double> r;
     tn_status s = run_single(lat, prec, TN_SCHED_AUTO, work_bonds(a, b), 1.0, 0.0, &r, nullptr);
     if (s != TN_OK) return s;
-    // result row: header, then the nb correlators (no site observables)
-    std::memcpy(out, r.data() + kResultHeader, sizeof(double) * nb);
+    // result row: header, then the nb correlators (no site observables); <Y Y> = -<R R>
+    const double sign = a == PH_R ? -1.0 : 1.0;
+    for (int k = 0; k < nb; ++k) out[k] = sign * r[kResultHeader + k];
+    return TN_OK;
+    TN_GUARD_END
+}
+
+tn_status tn_pair_correlators(tn_lattice* lat, tn_precision prec, int op_a, int op_b, int n, const int* i,
+                              const int* j, double* out) {
+    TN_GUARD_BEGIN
+    if (!lat || !out || n < 0 || (n > 0 && (!i || !j))) return TN_ERR_INVALID;
+    const int a = pair_phys(op_a), b = pair_phys(op_b);
+    if (a < 0 || b < 0) { set_error("pair operators must be TN_OP_X, TN_OP_Y or TN_OP_Z"); return TN_ERR_INVALID; }
+    const int L = lat->L, W = lat->W, N = L * W;
+    for (int k = 0; k < n; ++k)
+        if (i[k] < 0 || j[k] < 0 || i[k] >= N || j[k] >= N || i[k] == j[k]) {
+            set_error("every pair needs two distinct sites of the lattice");
+            return TN_ERR_INVALID;
+        }
+    if (!lat->ctx || lat->ctx->device < 0) { set_error("context has no device"); return TN_ERR_NO_DEVICE; }
+    if (n == 0) return TN_OK;
+    if ((a == PH_R) != (b == PH_R)) {
+        std::fill(out, out + n, 0.0);
+        return TN_OK;
+    }
+    std::vector<PairSpec> pairs(n);
+    for (int k = 0; k < n; ++k) pairs[k] = PairSpec{i[k], j[k], a, b};
+    const int D = lat->D;
+    auto pg = program_build_plan(plan_choose(L, W, D, TN_SCHED_AUTO, TN_WORK_ENERGY), prec, TN_WORK_ENERGY,
+                                 tuned_knobs(L, W, D, prec, TN_WORK_ENERGY), &pairs);
+    // a program built for one call is checked before it runs (ordering, lifetimes, no aliasing)
+    const std::string why = program_verify(*pg);
+    if (!why.empty()) { set_error(why.c_str()); return TN_ERR_NUMERIC; }
+    BatchOpts opts;
+    opts.program = pg;
+    opts.use_graph = false;     // built for this call only
+    tn_batch* bt = nullptr;
+    tn_status s = batch_create(lat->ctx, 1, &L, &W, &D, prec, TN_SCHED_AUTO, TN_WORK_ENERGY, true, &bt, nullptr, &opts);
+    if (s != TN_OK) return s;
+    std::vector<double> r((size_t)bt->lay.nres);
+    int status = 0;
+    cudaStream_t st = bt->stream;
+    cudaError_t e = cudaMemcpyAsync(bt->buf + bt->lay.in_off, lat->host.data(), lat->host.size() * 8,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) s = batch_run(bt, st);
+    if (e == cudaSuccess && s == TN_OK)
+        e = cudaMemcpyAsync(r.data(), bt->buf + bt->lay.res_off, r.size() * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && s == TN_OK)
+        e = cudaMemcpyAsync(&status, bt->buf + bt->lay.status_off, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    batch_destroy(bt);
+    if (s != TN_OK) return s;
+    if (e != cudaSuccess) return cuda_status(e, "pair correlators");
+    if (status) { set_error("a bounded wait in a kernel timed out"); return TN_ERR_TIMEOUT; }
+    const double sign = a == PH_R ? -1.0 : 1.0;
+    for (int k = 0; k < n; ++k) {
+        out[k] = sign * r[kResultHeader + k];
+        if (!std::isfinite(out[k])) { set_error("non-finite correlator"); return TN_ERR_NUMERIC; }
+    }
     return TN_OK;
     TN_GUARD_END
 }

@@ -1617,7 +1617,7 @@ cudaError_t launch_dot(int dt, const DotTask* tasks, int ntasks, long long nbloc
 // in the corner's frame (h = frame l leg, h' = frame rt leg), where e_A is the
 // frexp exponent of max|A| (so the matrix is O(1) and its slot carries 2 e_A).
 // The two copies are the bra and ket layers of Sec. 5 (real amplitudes, no
-// conjugation); O is I, X or Z = diag(-1, +1).
+// conjugation); O is I, X, Z = diag(-1, +1) or R = [[0, 1], [-1, 0]] (Y = i R).
 // One warp per site matrix (8 per 256-thread block): the max of |A| by warp
 // shuffles, then each lane forms every 32nd entry.
 template <typename T>
@@ -1641,6 +1641,7 @@ k_sitemat(const SiteMatTask* __restrict__ tasks, int ntasks, Slot* __restrict__ 
     double o00, o01, o10, o11;
     if (t.phys == 1) { o00 = 0; o01 = 1; o10 = 1; o11 = 0; }
     else if (t.phys == 2) { o00 = -1; o01 = 0; o10 = 0; o11 = 1; }
+    else if (t.phys == 3) { o00 = 0; o01 = 1; o10 = -1; o11 = 0; }   // R, Y = i R
     else { o00 = 1; o01 = 0; o10 = 0; o11 = 1; }
     T* E = static_cast<T*>(t.E);
     const int K = t.K, N = t.N;

@@ -370,7 +370,8 @@ std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sc
     return program_build_plan(plan_choose(L, W, D, sched, work), prec, work, knobs);
 }
 
-std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision prec, tn_work work, Knobs knobs) {
+std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision prec, tn_work work, Knobs knobs,
+                                                  const std::vector<PairSpec>* pairs) {
     auto pgp = std::make_shared<Program>();
     Program& pg = *pgp;
     pg.plan = plan;
@@ -433,7 +434,7 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
     if (work != TN_WORK_NORM) {
         // energies: every site and the ZZ bonds; bond work kinds: the bonds
         // alone with operators A on each bond's first site and B on its second
-        const bool with_sites = work == TN_WORK_ENERGY;
+        const bool with_sites = work == TN_WORK_ENERGY && !pairs;
         const int bondA = work_is_bonds(work) ? work_bond_a(work) : PH_Z;
         const int bondB = work_is_bonds(work) ? work_bond_b(work) : PH_Z;
         int Env[4] = {-1, -1, -1, -1};
@@ -492,13 +493,18 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
             pg.sx_den[s] = norm_at(w.q, w.t);
         }
         // bonds, output order: horizontal row-major, then vertical row-major
-        std::vector<std::pair<int, int>> bonds;
-        for (int r = 0; r < L; ++r)
-            for (int c = 0; c + 1 < W; ++c) bonds.push_back({r * W + c, r * W + c + 1});
-        for (int r = 0; r + 1 < L; ++r)
-            for (int c = 0; c < W; ++c) bonds.push_back({r * W + c, (r + 1) * W + c});
+        // the correlators to form: every nearest-neighbour bond with (A, B), or the caller's pairs
+        std::vector<PairSpec> bonds;
+        if (pairs) {
+            bonds = *pairs;
+        } else {
+            for (int r = 0; r < L; ++r)
+                for (int c = 0; c + 1 < W; ++c) bonds.push_back({r * W + c, r * W + c + 1, bondA, bondB});
+            for (int r = 0; r + 1 < L; ++r)
+                for (int c = 0; c < W; ++c) bonds.push_back({r * W + c, (r + 1) * W + c, bondA, bondB});
+        }
         int Xl = -1, Xr = -1;
-        int den_cross[4] = {-1, -1, -1, -1};
+        int den_cross[6] = {-1, -1, -1, -1, -1, -1};
         // Chain of corner q over steps t0..t1 from x, operator op0 at step t0
         // and I after; with adj >= 0 the last step is instead an absorb-dot
         // with operator op1 and adj.  Consecutive steps of one frame row run as
@@ -554,8 +560,11 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
             bd.set_floor(0);
         };
         for (size_t bi = 0; bi < bonds.size(); ++bi) {
-            SiteRef a = where[bonds[bi].first], b = where[bonds[bi].second];
-            int opa = bondA, opb = bondB;
+            if (bonds[bi].a == bonds[bi].b || bonds[bi].a < 0 || bonds[bi].b < 0 || bonds[bi].a >= nsite ||
+                bonds[bi].b >= nsite)
+                throw std::invalid_argument("a pair needs two distinct sites of the lattice");
+            SiteRef a = where[bonds[bi].a], b = where[bonds[bi].b];
+            int opa = bonds[bi].op_a, opb = bonds[bi].op_b;
             int v = -1;
             if (a.q == b.q) {
                 if (a.t > b.t) { std::swap(a, b); std::swap(opa, opb); }
@@ -599,8 +608,24 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
                     if (den_cross[3] < 0)
                         den_cross[3] = pg.tensors[bd.gemm(Qt[TR], Qt[BR], vrT, vrB, hbR, 1, vrT, vrB, 1, Xl)].slot;
                     pg.zz_den[bi] = den_cross[3];
+                } else if (qa == TL && qb == BR) {
+                    // diagonal corners: <Za TR^T, BL Zb^T>, two products
+                    const int P1 = bd.gemm(Za, Qt[TR], hbL, hbR, vrT, vrT, 1, 1, vrT);
+                    v = bd.gemm(Qt[BL], Zb, hbL, hbR, vrB, vrB, 1, 1, vrB, P1);
+                    if (!path_norms) den_cross[4] = pg.norm_slot;
+                    if (den_cross[4] < 0)
+                        den_cross[4] = pg.tensors[bd.gemm(Qt[BL], Qt[BR], hbL, hbR, vrB, vrB, 1, 1, vrB, Mtop)].slot;
+                    pg.zz_den[bi] = den_cross[4];
+                } else if (qa == TR && qb == BL) {
+                    // diagonal corners: <TL Za^T, Zb BR^T>, two products
+                    const int P1 = bd.gemm(Qt[TL], Za, hbL, hbR, vrT, vrT, 1, 1, vrT);
+                    v = bd.gemm(Zb, Qt[BR], hbL, hbR, vrB, vrB, 1, 1, vrB, P1);
+                    if (!path_norms) den_cross[5] = pg.norm_slot;
+                    if (den_cross[5] < 0)
+                        den_cross[5] = pg.tensors[bd.gemm(Qt[BL], Qt[BR], hbL, hbR, vrB, vrB, 1, 1, vrB, Mtop)].slot;
+                    pg.zz_den[bi] = den_cross[5];
                 } else {
-                    throw std::logic_error("bond between non-adjacent corners");
+                    throw std::logic_error("pair between unknown corners");
                 }
                 end_chain(v);
             }

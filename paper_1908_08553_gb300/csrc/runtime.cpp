@@ -460,7 +460,11 @@ tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int
     for (int k = 0; k < n; ++k) {
         std::shared_ptr<const Program> pg;
         try {
-            pg = program_cached(L[k], W[k], D[k], sched, prec, work, opts->knobs);
+            pg = opts->program ? opts->program : program_cached(L[k], W[k], D[k], sched, prec, work, opts->knobs);
+            if (pg->plan.L != L[k] || pg->plan.W != W[k] || pg->plan.D != D[k]) {
+                set_error("the given program is for another lattice shape");
+                return TN_ERR_INVALID;
+            }
         } catch (const std::exception& e) {
             set_error(e.what());
             return TN_ERR_INVALID;

@@ -105,6 +105,7 @@ struct BatchOpts {
     bool async_alloc = false;        // cudaMallocAsync / cudaFreeAsync on that stream
     bool use_graph = true;           // capture the launch sequence on the first run
     int knobs = -1;                  // program knobs (Knobs::code); -1: the tuning table's choice
+    std::shared_ptr<const Program> program;   // every member runs this program (its shape must match)
 };
 tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int* D,
                        tn_precision prec, tn_schedule sched, tn_work work, bool alloc,

@@ -84,7 +84,14 @@ enum OpKind {
 };
 
 // Operator insertion on the physical leg.
-enum PhysOp { PH_I = 0, PH_X = 1, PH_Z = 2 };
+// PH_R = [[0, 1], [-1, 0]]: Y = i R on this basis, so a real state's <Y_i Y_j>
+// is -<R_i R_j> (and any single Y averages to zero).
+enum PhysOp { PH_I = 0, PH_X = 1, PH_Z = 2, PH_R = 3 };
+
+// One two-site correlator <A_a B_b> of an explicit pair list (sites row-major).
+struct PairSpec {
+    int a, b, op_a, op_b;
+};
 
 struct Tensor {
     int64_t n = 0;           // entries (0 for a scalar result)
@@ -178,14 +185,17 @@ inline bool work_valid(tn_work w) {
     if (w == TN_WORK_NORM || w == TN_WORK_ENERGY) return true;
     if (!work_is_bonds(w)) return false;
     const int a = work_bond_a(w), b = work_bond_b(w);
-    return (a == PH_X || a == PH_Z) && (b == PH_X || b == PH_Z) && (int)w < 32;
+    return (a == PH_X || a == PH_Z || a == PH_R) && (b == PH_X || b == PH_Z || b == PH_R) && (int)w < 32;
 }
 
 std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sched,
                                              tn_precision prec, tn_work work, Knobs knobs = Knobs());
 // the same for a given plan (any orientation and cut)
+// pairs (work TN_WORK_ENERGY): the correlators of that list instead of the
+// energy's observables (result order = list order)
 std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision prec, tn_work work,
-                                                  Knobs knobs = Knobs());
+                                                  Knobs knobs = Knobs(),
+                                                  const std::vector<PairSpec>* pairs = nullptr);
 // Knobs the tuning table holds for this shape (the defaults if it holds none).
 Knobs tuned_knobs(int L, int W, int D, tn_precision prec, tn_work work);
 // Consistency of a built program ("" if sound): every op runs after the

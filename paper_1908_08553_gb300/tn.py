@@ -20,7 +20,7 @@ TN_ERR_CUDA, TN_ERR_TIMEOUT, TN_ERR_NUMERIC, TN_ERR_NO_DEVICE = -4, -5, -6, -7
 TN_FP64, TN_FP32, TN_BF16X3, TN_BF16X6 = 0, 1, 2, 3
 TN_SCHED_AUTO, TN_SCHED_ROW, TN_SCHED_COL, TN_SCHED_QUADRANT = 0, 1, 2, 3
 TN_WORK_NORM, TN_WORK_ENERGY = 0, 1
-TN_OP_NORM, TN_OP_X, TN_OP_ZZ, TN_OP_Z = 0, 1, 2, 3
+TN_OP_NORM, TN_OP_X, TN_OP_ZZ, TN_OP_Z, TN_OP_Y = 0, 1, 2, 3, 4
 
 PRECISIONS = {"fp64": TN_FP64, "fp32": TN_FP32, "bf16x3": TN_BF16X3, "bf16x6": TN_BF16X6}
 
@@ -93,6 +93,7 @@ SIGNATURES = {
     "tn_ctx_inject_wait_timeout": (c_int, [c_void_p, c_int]),
     "tn_peak_probe": (c_int, [c_void_p, c_int, POINTER(c_double)]),
     "tn_ite_init_product": (c_int, [c_void_p]),
+    "tn_pair_correlators": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "tn_autotune": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_size_t]),
     "tn_autotune_lookup": (c_int, [c_int, c_int, c_int, c_int, c_int, POINTER(c_int), POINTER(c_double),
                                    POINTER(c_double), POINTER(c_int)]),
@@ -402,6 +403,16 @@ def tn_absorb_dot_noalloc(dtype: int, x_in, E, adj, P: int, K: int, N: int, S: i
 
 def tn_ctx_set_profiling(ctx, on: bool):
     check(lib().tn_ctx_set_profiling(ctx, 1 if on else 0), "tn_ctx_set_profiling")
+
+
+def tn_pair_correlators(lat, prec: int, op_a: int, op_b: int, i, j) -> np.ndarray:
+    """<A_i B_j> for arbitrary pairs of distinct sites (row-major), exactly."""
+    i = np.ascontiguousarray(i, dtype=np.int32)
+    j = np.ascontiguousarray(j, dtype=np.int32)
+    out = np.zeros(max(i.size, 1))
+    check(lib().tn_pair_correlators(lat, prec, op_a, op_b, i.size, _ptr(i), _ptr(j), _ptr(out)),
+          "tn_pair_correlators")
+    return out[:i.size]
 
 
 def tn_autotune(ctx, Ls, Ws, Ds, prec: int, work: int = TN_WORK_ENERGY, reps: int = 3, max_bytes: int = 0):

@@ -134,6 +134,20 @@ def test_invalid_arguments(cpu_ctx):
         with pytest.raises(tn.TNError) as e:
             tn.tn_bond_correlators(lat, tn.TN_FP64, tn.TN_OP_X, tn.TN_OP_Z, 3, 3)
         assert e.value.status == tn.TN_ERR_NO_DEVICE
+        # arbitrary pairs: sites and operators are checked before any device work
+        for a, b, i, j in ((tn.TN_OP_Z, tn.TN_OP_Z, 2, 2), (tn.TN_OP_Z, tn.TN_OP_Z, -1, 3),
+                           (tn.TN_OP_Z, tn.TN_OP_Z, 0, 9), (tn.TN_OP_ZZ, tn.TN_OP_Z, 0, 1),
+                           (tn.TN_OP_Y, 5, 0, 1)):
+            with pytest.raises(tn.TNError) as e:
+                tn.tn_pair_correlators(lat, tn.TN_FP64, a, b, [i], [j])
+            assert e.value.status == tn.TN_ERR_INVALID
+        for a, b in ((tn.TN_OP_Y, tn.TN_OP_Y), (tn.TN_OP_X, tn.TN_OP_Y)):
+            with pytest.raises(tn.TNError) as e:
+                tn.tn_pair_correlators(lat, tn.TN_FP64, a, b, [0, 8], [8, 4])
+            assert e.value.status == tn.TN_ERR_NO_DEVICE
+            with pytest.raises(tn.TNError) as e:
+                tn.tn_bond_correlators(lat, tn.TN_FP64, a, b, 3, 3)
+            assert e.value.status == tn.TN_ERR_NO_DEVICE
     finally:
         tn.tn_destroy_lattice(lat)
     with pytest.raises(tn.TNError) as e:
