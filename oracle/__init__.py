@@ -11,6 +11,8 @@ Parts:
   * ``brute.py``     -- 2^N state vector and explicit Hamiltonian (numpy/scipy).
   * ``planner.py``   -- the paper's minimum-bottleneck partition choice (Sec. 4),
                         written independently of the library's planner.
+  * ``complex_peps.py`` -- complex site tensors: the double layer with the bra
+                        conjugated, contracted row by row in complex128.
 """
 from __future__ import annotations
 

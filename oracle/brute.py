@@ -23,10 +23,13 @@ import numpy as np
 def state_vector(L: int, W: int, D: int, flat: np.ndarray) -> np.ndarray:
     """psi[index] with bit k of index = p of site k (row-major)."""
     from paper_1908_08553_gb300.inputs import split_sites  # input layout only
-    sites = split_sites(np.asarray(flat, np.float64), L, W, D)
+    flat = np.asarray(flat)
+    if not np.iscomplexobj(flat):
+        flat = flat.astype(np.float64)
+    sites = split_sites(flat, L, W, D)
     # T axes: [phys bits 0..k-1 (2 each, site 0 first)] + boundary legs
     # boundary before site (r, c): dn_0..dn_{c-1} of row r, h, u_c..u_{W-1}
-    T = np.ones([1] * (W + 1))  # h + W u-legs of row 0, all of dimension 1
+    T = np.ones([1] * (W + 1), dtype=flat.dtype)  # h + W u-legs of row 0, all of dimension 1
     nphys = 0
     for r in range(L):
         for c in range(W):
@@ -138,28 +141,45 @@ def ground_energy(L: int, W: int, J: float, h: float) -> float:
     return float(w[0])
 
 
+def _pauli_p(name: str) -> np.ndarray:
+    """Pauli matrix on the p basis: the standard one on (sigma = +1, sigma = -1)
+    with rows and columns reversed (p = 1 - position)."""
+    std = {"x": np.array([[0, 1], [1, 0]], complex), "y": np.array([[0, -1j], [1j, 0]]),
+           "z": np.array([[1, 0], [0, -1]], complex)}
+    return std[name][::-1, ::-1]
+
+
+def _apply(M: np.ndarray, k: int, v: np.ndarray) -> np.ndarray:
+    """(M acting on site k) v: (M v)[s] = M[s_k, s_k] v[s] + M[s_k, 1 - s_k] v[s with k flipped]."""
+    idx = np.arange(v.size)
+    bit = (idx >> k) & 1
+    return M[bit, bit] * v + M[bit, 1 - bit] * v[idx ^ (1 << k)]
+
+
+def _ratio(psi: np.ndarray, w: np.ndarray):
+    val = np.vdot(psi, w) / np.vdot(psi, psi)
+    return float(val.real) if abs(val.imag) < 1e-12 * max(1.0, abs(val)) else complex(val)
+
+
 def pair_correlator(L: int, W: int, D: int, flat: np.ndarray, op_a: str, i: int, op_b: str, j: int) -> float:
     """<A_i B_j> = psi^dagger A_i B_j psi / psi^dagger psi for any sites i != j,
     A, B in {'x', 'y', 'z'} as complex 2 x 2 Pauli matrices on the basis
-    (p = 0 <-> sigma = -1, p = 1 <-> sigma = +1), applied to the state vector."""
+    (p = 0 <-> sigma = -1, p = 1 <-> sigma = +1), applied to the state vector
+    (real or complex site tensors)."""
     psi = state_vector(L, W, D, flat).astype(np.complex128)
     N = L * W
-    idx = np.arange(psi.size)
-    # the Pauli matrices on (sigma = +1, sigma = -1), reordered to (p = 0, p = 1)
-    std = {"x": np.array([[0, 1], [1, 0]], complex), "y": np.array([[0, -1j], [1j, 0]]),
-           "z": np.array([[1, 0], [0, -1]], complex)}
-
-    def op(name):
-        m = std[name]
-        return m[::-1, ::-1]       # index p = 1 - (position in (+1, -1))
-
-    def apply(M, k, v):
-        bit = (idx >> k) & 1
-        flipped = v[idx ^ (1 << k)]
-        # (M v)[s] = M[s_k, s_k] v[s] + M[s_k, 1 - s_k] v[s with k flipped]
-        return M[bit, bit] * v + M[bit, 1 - bit] * flipped
-
     assert 0 <= i < N and 0 <= j < N and i != j
-    w = apply(op(op_a), i, apply(op(op_b), j, psi))
-    val = np.vdot(psi, w) / np.vdot(psi, psi)
-    return float(val.real) if abs(val.imag) < 1e-12 * max(1.0, abs(val)) else complex(val)
+    return _ratio(psi, _apply(_pauli_p(op_a), i, _apply(_pauli_p(op_b), j, psi)))
+
+
+def site_expectation(L: int, W: int, D: int, flat: np.ndarray, op: str, k: int) -> float:
+    """<O_k> = psi^dagger O_k psi / psi^dagger psi, O in {'x', 'y', 'z'}."""
+    psi = state_vector(L, W, D, flat).astype(np.complex128)
+    return _ratio(psi, _apply(_pauli_p(op), k, psi))
+
+
+def complex_energy(L: int, W: int, D: int, flat: np.ndarray, J: float, h: float) -> float:
+    """psi^dagger H psi / psi^dagger psi with the sparse TFIM Hamiltonian."""
+    psi = state_vector(L, W, D, flat).astype(np.complex128)
+    H = hamiltonian(L, W, J, h)
+    return float((np.vdot(psi, H @ psi) / np.vdot(psi, psi)).real)

@@ -84,6 +84,14 @@ def random_lattice(L: int, W: int, D: int, seed: int) -> np.ndarray:
     return uniform_pm1(seed, n_elems(L, W, D))
 
 
+def random_complex_lattice(L: int, W: int, D: int, seed: int) -> np.ndarray:
+    """Flat complex site tensors: real parts the first n_elems draws of ``seed``,
+    imaginary parts the next n_elems, each uniform[-1, 1)."""
+    n = n_elems(L, W, D)
+    u = uniform_pm1(seed, 2 * n)
+    return u[:n] + 1j * u[n:]
+
+
 def ones_lattice(L: int, W: int, D: int) -> np.ndarray:
     """Every entry 1: the workload of the paper's timing figures (Sec. 6)."""
     return np.ones(n_elems(L, W, D), dtype=np.float64)
