@@ -84,9 +84,11 @@ typedef enum {
     TN_OP_X = 1,           /* <X_i>, Eq. mx */
     TN_OP_ZZ = 2,          /* <Z_i Z_j> for nearest neighbours i, j, Eq. cij first term */
     TN_OP_Z = 3,           /* <Z_i>, Eq. mz with Pauli Z */
-    TN_OP_Y = 4            /* Pauli Y (two-site correlators only): Y = i R with the real
-                              R = [[0, 1], [-1, 0]] on p = 0, 1, so for the real states
-                              here <A_i Y_j> = 0 (A = X, Z) and <Y_i Y_j> = -<R_i R_j> */
+    TN_OP_Y = 4            /* <Y_i>, Pauli Y = [[0, i], [-i, 0]] on p = 0, 1 (sigma_y with
+                              rows and columns in the order sigma = -1, +1).  For real
+                              site tensors Y = i R with the real R = [[0, 1], [-1, 0]],
+                              so <Y_i> = <A_i Y_j> = 0 (A = X, Z) exactly and
+                              <Y_i Y_j> = -<R_i R_j>; complex site tensors contract Y */
 } tn_op;
 
 /* value = mant * 2^exp2 (the norm of a large lattice leaves the FP64 range). */
@@ -137,8 +139,21 @@ tn_status tn_set_site_tensors(tn_lattice *lat, const double *host, size_t n_elem
  * 2014) as a counter-based generator, entry k (fill order above) is
  * 2 * (mix64(seed + (k+1) * 0x9E3779B97F4A7C15) >> 11) * 2^-53 - 1. */
 tn_status tn_fill_random(tn_lattice *lat, uint64_t seed);
-/* Copy the lattice's FP64 tensors back to the host (n_elems entries). */
+/* Copy the lattice's FP64 tensors back to the host (n_elems entries);
+ * TN_ERR_INVALID for a lattice holding complex tensors. */
 tn_status tn_get_site_tensors(const tn_lattice *lat, double *host, size_t n_elems);
+/* Complex site tensors A = re + i im (Eq. Psi with complex amplitudes), each
+ * array n_elems doubles in the layout above.  Every later contraction of the
+ * lattice (norm, expectations, energy, bond and pair correlators, <Y_k>)
+ * uses the double layer sum_{p,q} conj(A_p) O_pq A_q (Sec. 5, bra layer
+ * conjugated), built in a real basis of Hermitian matrices per bond so that
+ * every contraction after the site matrices stays real arithmetic.
+ * tn_set_site_tensors / tn_fill_random return the lattice to real tensors.
+ * Served jobs, batches, the boundary MPS and the imaginary time evolution
+ * take real tensors only. */
+tn_status tn_set_site_tensors_complex(tn_lattice *lat, const double *re, const double *im, size_t n_elems);
+/* 1 if the lattice holds complex site tensors, else 0. */
+int tn_lattice_is_complex(const tn_lattice *lat);
 
 /* ------------------------------------------------------------ planning -- */
 
@@ -180,10 +195,13 @@ tn_status tn_program_info(const tn_lattice *lat, tn_precision prec, tn_schedule 
 
 /* <Psi|Psi> (blocking). */
 tn_status tn_contract_norm(tn_lattice *lat, tn_precision prec, tn_schedule sched, tn_scalar *out);
-/* One expectation value (blocking): op = TN_OP_X or TN_OP_Z with site
- * i = r*W + c, or TN_OP_ZZ with nearest-neighbour sites i < j.  Returns the
- * ratio to the norm. */
+/* One expectation value (blocking): op = TN_OP_X, TN_OP_Y or TN_OP_Z with
+ * site i = r*W + c, or TN_OP_ZZ with nearest-neighbour sites i < j.  Returns
+ * the ratio to the norm. */
 tn_status tn_expectation(tn_lattice *lat, tn_precision prec, int op, int i, int j, double *out);
+/* <O_k> for every site k (row-major), O = TN_OP_X, TN_OP_Y or TN_OP_Z
+ * (Eqs. mx, mz; blocking, AUTO schedule).  out: L*W doubles, caller-owned. */
+tn_status tn_site_expectations(tn_lattice *lat, tn_precision prec, int op, double *out);
 /* Norm, every <X_k>, every <Z_i Z_j>, every <Z_k>, the connected c_ij and E
  * for (J, h) (blocking, AUTO schedule); each array of *out is filled if non-NULL. */
 tn_status tn_energy(tn_lattice *lat, double J, double h, tn_precision prec, tn_result *out);

@@ -99,6 +99,16 @@ namespace {
     catch (const std::exception& e) { set_error(e.what()); return TN_ERR_INVALID; }            \
     catch (...) { set_error("unknown error"); return TN_ERR_INVALID; }
 
+// Switch a lattice between real and complex site tensors: the host buffer
+// takes the programs' input layout and the cached batches are dropped.
+void set_complex(tn_lattice* lat, bool cplx) {
+    if (lat->cplx == cplx) return;
+    for (auto& kv : lat->cache) batch_destroy(kv.second);
+    lat->cache.clear();
+    lat->cplx = cplx;
+    lat->host.assign(lattice_elems(lat->L, lat->W, lat->D) * (cplx ? 2 : 1), 0.0);
+}
+
 // Run one lattice through its cached one-member batch and read the results.
 tn_status run_single(tn_lattice* lat, tn_precision prec, tn_schedule sched, tn_work work, double J,
                      double h, std::vector<double>* res, tn_batch** used) {
@@ -110,7 +120,9 @@ tn_status run_single(tn_lattice* lat, tn_precision prec, tn_schedule sched, tn_w
         b = it->second;
     } else {
         const int L = lat->L, W = lat->W, D = lat->D;
-        tn_status s = batch_create(lat->ctx, 1, &L, &W, &D, prec, sched, work, true, &b, nullptr);
+        BatchOpts opts;
+        opts.complex_sites = lat->cplx;
+        tn_status s = batch_create(lat->ctx, 1, &L, &W, &D, prec, sched, work, true, &b, nullptr, &opts);
         if (s != TN_OK) return s;
         lat->cache[key] = b;
     }
@@ -230,19 +242,51 @@ tn_status tn_destroy_lattice(tn_lattice* lat) {
 }
 
 tn_status tn_set_site_tensors(tn_lattice* lat, const double* host, size_t n) {
-    if (!lat || !host || n != lat->host.size()) { set_error("tensor count mismatch"); return TN_ERR_INVALID; }
+    TN_GUARD_BEGIN
+    if (!lat || !host || n != lattice_elems(lat->L, lat->W, lat->D)) {
+        set_error("tensor count mismatch");
+        return TN_ERR_INVALID;
+    }
+    set_complex(lat, false);
     std::memcpy(lat->host.data(), host, n * sizeof(double));
     return TN_OK;
+    TN_GUARD_END
 }
 
 tn_status tn_get_site_tensors(const tn_lattice* lat, double* host, size_t n) {
-    if (!lat || !host || n != lat->host.size()) return TN_ERR_INVALID;
+    if (!lat || !host || n != lat->host.size() || lat->cplx) return TN_ERR_INVALID;
     std::memcpy(host, lat->host.data(), n * sizeof(double));
     return TN_OK;
 }
 
+tn_status tn_set_site_tensors_complex(tn_lattice* lat, const double* re, const double* im, size_t n) {
+    TN_GUARD_BEGIN
+    if (!lat || !re || !im || n != lattice_elems(lat->L, lat->W, lat->D)) {
+        set_error("tensor count mismatch");
+        return TN_ERR_INVALID;
+    }
+    set_complex(lat, true);
+    // per site: its real parts, then its imaginary parts (the programs' input layout)
+    size_t src = 0, dst = 0;
+    for (int r = 0; r < lat->L; ++r)
+        for (int c = 0; c < lat->W; ++c) {
+            const size_t u = r == 0 ? 1 : lat->D, l = c == 0 ? 1 : lat->D;
+            const size_t dn = r == lat->L - 1 ? 1 : lat->D, rt = c == lat->W - 1 ? 1 : lat->D;
+            const size_t m = 2 * u * l * dn * rt;
+            std::memcpy(lat->host.data() + dst, re + src, m * sizeof(double));
+            std::memcpy(lat->host.data() + dst + m, im + src, m * sizeof(double));
+            src += m;
+            dst += 2 * m;
+        }
+    return TN_OK;
+    TN_GUARD_END
+}
+
+int tn_lattice_is_complex(const tn_lattice* lat) { return lat && lat->cplx ? 1 : 0; }
+
 tn_status tn_fill_random(tn_lattice* lat, uint64_t seed) {
     if (!lat) return TN_ERR_INVALID;
+    set_complex(lat, false);
     fill_uniform(seed, lat->host.data(), lat->host.size());
     return TN_OK;
 }
@@ -253,7 +297,9 @@ tn_status tn_footprint(const tn_lattice* lat, tn_schedule sched, tn_precision pr
     if (!lat || !bytes) return TN_ERR_INVALID;
     tn_batch* b = nullptr;
     const int L = lat->L, W = lat->W, D = lat->D;
-    tn_status s = batch_create(lat->ctx, 1, &L, &W, &D, prec, sched, work, false, &b, bytes);
+    BatchOpts opts;
+    opts.complex_sites = lat->cplx;
+    tn_status s = batch_create(lat->ctx, 1, &L, &W, &D, prec, sched, work, false, &b, bytes, &opts);
     if (b) delete b;
     return s;
     TN_GUARD_END
@@ -269,7 +315,7 @@ tn_status tn_program_info(const tn_lattice* lat, tn_precision prec, tn_schedule 
     if (!lat || !n || prec < TN_FP64 || prec > TN_BF16X6 || sched < TN_SCHED_AUTO || sched > TN_SCHED_QUADRANT ||
         (work != TN_WORK_NORM && work != TN_WORK_ENERGY))
         return TN_ERR_INVALID;
-    const auto pg = program_cached(lat->L, lat->W, lat->D, sched, prec, work);
+    const auto pg = program_cached(lat->L, lat->W, lat->D, sched, prec, work, -1, lat->cplx);
     const std::string why = program_verify(*pg);
     if (!why.empty()) { set_error("inconsistent program: " + why); return TN_ERR_NUMERIC; }
     double absorb_bytes = 0, product_macs = 0;
@@ -284,7 +330,9 @@ tn_status tn_program_info(const tn_lattice* lat, tn_precision prec, tn_schedule 
     size_t footprint = 0;
     tn_batch* b = nullptr;
     const int L = lat->L, W = lat->W, D = lat->D;
-    const tn_status fs = batch_create(lat->ctx, 1, &L, &W, &D, prec, sched, work, false, &b, &footprint);
+    BatchOpts opts;
+    opts.complex_sites = lat->cplx;
+    const tn_status fs = batch_create(lat->ctx, 1, &L, &W, &D, prec, sched, work, false, &b, &footprint, &opts);
     if (b) delete b;
     if (fs != TN_OK) return fs;
     const int64_t w[7] = {(int64_t)pg->ops.size(), (int64_t)pg->n_levels, pg->arena_bytes, (int64_t)footprint,
@@ -351,7 +399,7 @@ tn_status tn_expectation(tn_lattice* lat, tn_precision prec, int op, int i, int 
     if (!lat || !out) return TN_ERR_INVALID;
     const int L = lat->L, W = lat->W, N = L * W;
     if (op == TN_OP_NORM) { *out = 1.0; return TN_OK; }
-    if (op == TN_OP_X || op == TN_OP_Z) {
+    if (op == TN_OP_X || op == TN_OP_Z || op == TN_OP_Y) {
         if (i < 0 || i >= N) return TN_ERR_INVALID;
     } else if (op == TN_OP_ZZ) {
         if (i < 0 || j < 0 || i >= N || j >= N) return TN_ERR_INVALID;
@@ -361,11 +409,19 @@ tn_status tn_expectation(tn_lattice* lat, tn_precision prec, int op, int i, int 
     } else {
         return TN_ERR_INVALID;
     }
+    if (op == TN_OP_Y && !lat->cplx) {
+        // real amplitudes: <Y_k> = i <R_k> is real only if zero
+        if (!lat->ctx || lat->ctx->device < 0) { set_error("context has no device"); return TN_ERR_NO_DEVICE; }
+        *out = 0.0;
+        return TN_OK;
+    }
     std::vector<double> r;
     tn_status s = run_single(lat, prec, TN_SCHED_AUTO, TN_WORK_ENERGY, 1.0, 0.0, &r, nullptr);
     if (s != TN_OK) return s;
+    const int nb = L * (W - 1) + W * (L - 1);
     if (op == TN_OP_X) { *out = r[kResultHeader + i]; return TN_OK; }
-    if (op == TN_OP_Z) { *out = r[kResultHeader + N + L * (W - 1) + W * (L - 1) + i]; return TN_OK; }
+    if (op == TN_OP_Z) { *out = r[kResultHeader + N + nb + i]; return TN_OK; }
+    if (op == TN_OP_Y) { *out = r[kResultHeader + 2 * N + nb + i]; return TN_OK; }
     const int ri = i / W, ci = i % W;
     int bi;
     if (j == i + 1 && ri == j / W) bi = ri * (W - 1) + ci;
@@ -375,17 +431,39 @@ tn_status tn_expectation(tn_lattice* lat, tn_precision prec, int op, int i, int 
     TN_GUARD_END
 }
 
+tn_status tn_site_expectations(tn_lattice* lat, tn_precision prec, int op, double* out) {
+    TN_GUARD_BEGIN
+    if (!lat || !out || !(op == TN_OP_X || op == TN_OP_Y || op == TN_OP_Z)) return TN_ERR_INVALID;
+    const int L = lat->L, W = lat->W, N = L * W, nb = L * (W - 1) + W * (L - 1);
+    if (!lat->ctx || lat->ctx->device < 0) { set_error("context has no device"); return TN_ERR_NO_DEVICE; }
+    if (op == TN_OP_Y && !lat->cplx) {
+        std::fill(out, out + N, 0.0);
+        return TN_OK;
+    }
+    std::vector<double> r;
+    tn_status s = run_single(lat, prec, TN_SCHED_AUTO, TN_WORK_ENERGY, 1.0, 0.0, &r, nullptr);
+    if (s != TN_OK) return s;
+    const double* src = r.data() + kResultHeader + (op == TN_OP_X ? 0 : (op == TN_OP_Z ? N + nb : 2 * N + nb));
+    std::memcpy(out, src, sizeof(double) * N);
+    return TN_OK;
+    TN_GUARD_END
+}
+
 namespace {
-// Pauli operator code -> the real operator contracted (Y is i R).
-int pair_phys(int op) {
-    return op == TN_OP_X ? (int)PH_X : (op == TN_OP_Z ? (int)PH_Z : (op == TN_OP_Y ? (int)PH_R : -1));
+// Pauli operator code -> the operator contracted: for real site tensors Y is
+// i R (R real); complex site tensors take Y itself.
+int pair_phys(int op, bool cplx) {
+    if (op == TN_OP_X) return PH_X;
+    if (op == TN_OP_Z) return PH_Z;
+    if (op == TN_OP_Y) return cplx ? PH_Y : PH_R;
+    return -1;
 }
 }  // namespace
 
 tn_status tn_bond_correlators(tn_lattice* lat, tn_precision prec, int op_a, int op_b, double* out) {
     TN_GUARD_BEGIN
     if (!lat || !out) return TN_ERR_INVALID;
-    const int a = pair_phys(op_a), b = pair_phys(op_b);
+    const int a = pair_phys(op_a, lat->cplx), b = pair_phys(op_b, lat->cplx);
     if (a < 0 || b < 0) { set_error("bond operators must be TN_OP_X, TN_OP_Y or TN_OP_Z"); return TN_ERR_INVALID; }
     const int L = lat->L, W = lat->W, nb = L * (W - 1) + W * (L - 1);
     if ((a == PH_R) != (b == PH_R)) {
@@ -408,7 +486,7 @@ tn_status tn_pair_correlators(tn_lattice* lat, tn_precision prec, int op_a, int 
                               const int* j, double* out) {
     TN_GUARD_BEGIN
     if (!lat || !out || n < 0 || (n > 0 && (!i || !j))) return TN_ERR_INVALID;
-    const int a = pair_phys(op_a), b = pair_phys(op_b);
+    const int a = pair_phys(op_a, lat->cplx), b = pair_phys(op_b, lat->cplx);
     if (a < 0 || b < 0) { set_error("pair operators must be TN_OP_X, TN_OP_Y or TN_OP_Z"); return TN_ERR_INVALID; }
     const int L = lat->L, W = lat->W, N = L * W;
     for (int k = 0; k < n; ++k)
@@ -426,12 +504,13 @@ tn_status tn_pair_correlators(tn_lattice* lat, tn_precision prec, int op_a, int 
     for (int k = 0; k < n; ++k) pairs[k] = PairSpec{i[k], j[k], a, b};
     const int D = lat->D;
     auto pg = program_build_plan(plan_choose(L, W, D, TN_SCHED_AUTO, TN_WORK_ENERGY), prec, TN_WORK_ENERGY,
-                                 tuned_knobs(L, W, D, prec, TN_WORK_ENERGY), &pairs);
+                                 tuned_knobs(L, W, D, prec, TN_WORK_ENERGY), &pairs, lat->cplx);
     // a program built for one call is checked before it runs (ordering, lifetimes, no aliasing)
     const std::string why = program_verify(*pg);
     if (!why.empty()) { set_error(why.c_str()); return TN_ERR_NUMERIC; }
     BatchOpts opts;
     opts.program = pg;
+    opts.complex_sites = lat->cplx;
     opts.use_graph = false;     // built for this call only
     tn_batch* bt = nullptr;
     tn_status s = batch_create(lat->ctx, 1, &L, &W, &D, prec, TN_SCHED_AUTO, TN_WORK_ENERGY, true, &bt, nullptr, &opts);

@@ -16,6 +16,7 @@ namespace {
 tn_status bmps_run(tn_lattice* lat, int chi, std::vector<BmpsTask>& tasks, std::vector<double>* out) {
     tn_ctx* ctx = lat->ctx;
     const int L = lat->L, W = lat->W, D = lat->D;
+    if (lat->cplx) { set_error("the boundary MPS takes real site tensors"); return TN_ERR_INVALID; }
     if (chi < 1 || bmps_bond_max(D, chi) > 512) {
         set_error("chi out of range: max(chi, D^2) * D^2 must not exceed 512");
         return TN_ERR_INVALID;

@@ -58,6 +58,12 @@ extern "C" {
 tn_status tn_ite_init_product(tn_lattice* lat) {
     if (!lat) return TN_ERR_INVALID;
     const int L = lat->L, W = lat->W, D = lat->D;
+    if (lat->cplx) {   // back to real site tensors
+        for (auto& kv : lat->cache) batch_destroy(kv.second);
+        lat->cache.clear();
+        lat->cplx = false;
+        lat->host.assign(lat->host.size() / 2, 0.0);
+    }
     std::fill(lat->host.begin(), lat->host.end(), 0.0);
     size_t off = 0;
     for (int r = 0; r < L; ++r)
@@ -76,6 +82,7 @@ tn_status tn_ite_run(tn_lattice* lat, const tn_ite_params* prm, double* energies
                      double* max_discarded) {
     try {
         if (!lat || !prm) return TN_ERR_INVALID;
+        if (lat->cplx) { set_error("imaginary time evolution takes real site tensors"); return TN_ERR_INVALID; }
         if (!lat->ctx || lat->ctx->device < 0) { set_error("context has no device"); return TN_ERR_NO_DEVICE; }
         const int L = lat->L, W = lat->W, D = lat->D;
         if (prm->chi_max != D || prm->steps < 0 || !(prm->dtau >= 0.0) || !std::isfinite(prm->dtau) ||

@@ -1612,6 +1612,74 @@ cudaError_t launch_dot(int dt, const DotTask* tasks, int ntasks, long long nbloc
 
 // ------------------------------------------------------ site matrices ----
 
+// Complex site tensors.  The double layer
+//   E[(x y)] = sum_{p,q} conj(A_p[x legs]) O_pq A_q[y legs]   (x: bra, y: ket)
+// is complex, but every leg pair (x, y) can be re-expressed in an orthonormal
+// basis of Hermitian D x D matrices H_k, one element per (x, y):
+//   x == y: e_xx;  x < y: (e_xy + e_yx)/sqrt2;  x > y: i (e_yx - e_xy)/sqrt2.
+// With sum_k (H_k)_{ab} conj(H_k)_{a'b'} = delta_aa' delta_bb', a bond's sum
+// over (x, y) equals the sum over k of the two sites' components, the first
+// site (up or left) taking H_k and the second conj(H_k) (= H_k^T).  Each
+// component is <A| O (x) H (x) ... |A>, a Hermitian form, so the transformed
+// site matrix is real and the rest of the contraction is unchanged real
+// arithmetic.  This returns the component for the basis elements (va, vb) on
+// the four lattice legs (u, l, dn, rt): the sum over at most two (bra, ket)
+// index pairs per leg, times i^m for the m antisymmetric legs, real part.
+__device__ double sitemat_complex_entry(const double* __restrict__ Ar, const double* __restrict__ Ai,
+                                        const int* dm, long long stride_p, const int* va, const int* vb, int phys) {
+    const double r2 = 0.70710678118654752440;   // 1/sqrt(2)
+    int nc[4], bra[4][2], ket[4][2];
+    double w[4][2];
+    int m = 0;
+    for (int l = 0; l < 4; ++l) {
+        const int x = va[l], y = vb[l];
+        if (x == y) {
+            nc[l] = 1; bra[l][0] = x; ket[l][0] = x; w[l][0] = 1.0;
+        } else if (x < y) {
+            nc[l] = 2; bra[l][0] = x; ket[l][0] = y; bra[l][1] = y; ket[l][1] = x; w[l][0] = w[l][1] = r2;
+        } else {
+            // i (e_yx - e_xy)/sqrt2 on the dn and rt legs (this site first on the
+            // bond); its conjugate on u and l (this site second)
+            const double s = l >= 2 ? r2 : -r2;
+            nc[l] = 2; bra[l][0] = y; ket[l][0] = x; w[l][0] = s; bra[l][1] = x; ket[l][1] = y; w[l][1] = -s;
+            ++m;
+        }
+    }
+    // O on the physical index: (re, im) of O00, O01, O10, O11
+    double o[4][2] = {{1, 0}, {0, 0}, {0, 0}, {1, 0}};
+    if (phys == 1) { o[0][0] = 0; o[1][0] = 1; o[2][0] = 1; o[3][0] = 0; }
+    else if (phys == 2) { o[0][0] = -1; }
+    else if (phys == 3) { o[0][0] = 0; o[1][0] = 1; o[2][0] = -1; o[3][0] = 0; }
+    else if (phys == 4) { o[0][0] = 0; o[1][1] = 1; o[2][1] = -1; o[3][0] = 0; }
+    double zr = 0.0, zi = 0.0;
+    for (int c0 = 0; c0 < nc[0]; ++c0)
+        for (int c1 = 0; c1 < nc[1]; ++c1)
+            for (int c2 = 0; c2 < nc[2]; ++c2)
+                for (int c3 = 0; c3 < nc[3]; ++c3) {
+                    const double wt = w[0][c0] * w[1][c1] * w[2][c2] * w[3][c3];
+                    const long long ia =
+                        ((long long)(bra[0][c0] * dm[1] + bra[1][c1]) * dm[2] + bra[2][c2]) * dm[3] + bra[3][c3];
+                    const long long ib =
+                        ((long long)(ket[0][c0] * dm[1] + ket[1][c1]) * dm[2] + ket[2][c2]) * dm[3] + ket[3][c3];
+                    const double a0r = Ar[ia], a0i = Ai[ia], a1r = Ar[stride_p + ia], a1i = Ai[stride_p + ia];
+                    const double b0r = Ar[ib], b0i = Ai[ib], b1r = Ar[stride_p + ib], b1i = Ai[stride_p + ib];
+                    // v_p = sum_q O_pq B_q
+                    const double v0r = o[0][0] * b0r - o[0][1] * b0i + o[1][0] * b1r - o[1][1] * b1i;
+                    const double v0i = o[0][0] * b0i + o[0][1] * b0r + o[1][0] * b1i + o[1][1] * b1r;
+                    const double v1r = o[2][0] * b0r - o[2][1] * b0i + o[3][0] * b1r - o[3][1] * b1i;
+                    const double v1i = o[2][0] * b0i + o[2][1] * b0r + o[3][0] * b1i + o[3][1] * b1r;
+                    // conj(A_0) v_0 + conj(A_1) v_1
+                    zr += wt * (a0r * v0r + a0i * v0i + a1r * v1r + a1i * v1i);
+                    zi += wt * (a0r * v0i - a0i * v0r + a1r * v1i - a1i * v1r);
+                }
+    switch (m & 3) {
+        case 0: return zr;
+        case 1: return -zi;
+        case 2: return -zr;
+        default: return zi;
+    }
+}
+
 // E_O[(h_a h_b)(u_a u_b)][(dn_a dn_b)(rt_a rt_b)] =
 //   sum_{p,q} A[p](legs a) O[p][q] A[q](legs b) * 2^(-2 e_A)
 // in the corner's frame (h = frame l leg, h' = frame rt leg), where e_A is the
@@ -1632,6 +1700,8 @@ k_sitemat(const SiteMatTask* __restrict__ tasks, int ntasks, Slot* __restrict__ 
     const int nA = 2 * dm[0] * dm[1] * dm[2] * dm[3];
     double mx = 0.0;
     for (int k = lane; k < nA; k += 32) mx = fmax(mx, fabs(t.A[k]));
+    if (t.Ai)
+        for (int k = lane; k < nA; k += 32) mx = fmax(mx, fabs(t.Ai[k]));
     mx = warp_max(mx);
     int eA = 0;
     if (mx > 0.0) frexp(mx, &eA);
@@ -1678,6 +1748,10 @@ k_sitemat(const SiteMatTask* __restrict__ tasks, int ntasks, Slot* __restrict__ 
         va[t.map[0]] = ua; va[t.map[1]] = la; va[t.map[2]] = da; va[t.map[3]] = ra;
         vb[t.map[0]] = ub; vb[t.map[1]] = lb; vb[t.map[2]] = db; vb[t.map[3]] = rb;
         if (!shape_ok) { E[idx] = T(0); continue; }
+        if (t.Ai) {
+            E[idx] = (T)(sitemat_complex_entry(t.A, t.Ai, dm, stride_p, va, vb, t.phys) * sc);
+            continue;
+        }
         const long long ia = ((long long)(va[0] * dm[1] + va[1]) * dm[2] + va[2]) * dm[3] + va[3];
         const long long ib = ((long long)(vb[0] * dm[1] + vb[1]) * dm[2] + vb[2]) * dm[3] + vb[3];
         const double a0 = t.A[ia], a1 = t.A[stride_p + ia];
@@ -1824,6 +1898,11 @@ __global__ void k_final(const FinalTask* __restrict__ tasks, const Slot* __restr
         const Slot& s = slots[t.sz_slots[k]];
         const Slot& d = slots[t.sx_den[k]];
         v[t.n_sites + t.n_bonds + k] = ldexp(s.mant / d.mant, (int)(s.X - d.X));
+    }
+    for (int k = threadIdx.x; k < t.n_sy; k += blockDim.x) {
+        const Slot& s = slots[t.sy_slots[k]];
+        const Slot& d = slots[t.sx_den[k]];
+        v[2 * t.n_sites + t.n_bonds + k] = ldexp(s.mant / d.mant, (int)(s.X - d.X));
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -366,15 +366,19 @@ int64_t pack_arena(Program& pg) {
 }  // namespace
 
 std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sched,
-                                             tn_precision prec, tn_work work, Knobs knobs) {
-    return program_build_plan(plan_choose(L, W, D, sched, work), prec, work, knobs);
+                                             tn_precision prec, tn_work work, Knobs knobs, bool cplx) {
+    return program_build_plan(plan_choose(L, W, D, sched, work), prec, work, knobs, nullptr, cplx);
 }
 
 std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision prec, tn_work work, Knobs knobs,
-                                                  const std::vector<PairSpec>* pairs) {
+                                                  const std::vector<PairSpec>* pairs, bool cplx) {
     auto pgp = std::make_shared<Program>();
     Program& pg = *pgp;
     pg.plan = plan;
+    pg.cplx = cplx;
+    // the two-pass absorption keeps the double layer as bra x ket factors; the
+    // real basis of complex site matrices mixes the two layers, so it is off
+    if (cplx) knobs.factor_d3 = false;
     pg.knobs = knobs;
     const int L = plan.L, W = plan.W, D = plan.D;
     pg.work = work;
@@ -385,6 +389,7 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
     const int nsite = L * W;
 
     // raw FP64 input layout, [p][u][l][dn][rt] per site, row-major sites
+    // (complex: the site's real parts, then its imaginary parts)
     pg.site_offset.resize(nsite + 1);
     pg.site_dims.resize(4 * nsite);
     pg.site_offset[0] = 0;
@@ -396,7 +401,7 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
             dm[1] = c == 0 ? 1 : D;
             dm[2] = r == L - 1 ? 1 : D;
             dm[3] = c == W - 1 ? 1 : D;
-            pg.site_offset[s + 1] = pg.site_offset[s] + 2LL * dm[0] * dm[1] * dm[2] * dm[3];
+            pg.site_offset[s + 1] = pg.site_offset[s] + (cplx ? 4LL : 2LL) * dm[0] * dm[1] * dm[2] * dm[3];
         }
     pg.input_bytes = pg.site_offset[nsite] * 8;
 
@@ -474,6 +479,7 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
         pg.sx_slot.assign(with_sites ? nsite : 0, -1);
         pg.sz_slot.assign(with_sites ? nsite : 0, -1);
         pg.sx_den.assign(with_sites ? nsite : 0, -1);
+        pg.sy_slot.assign(with_sites && cplx ? nsite : 0, -1);
         for (int s = 0; s < (with_sites ? nsite : 0); ++s) {
             const SiteRef& w = where[s];
             const Step& st = step_of(w.q, w.t);
@@ -490,6 +496,8 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
                 pg.sx_slot[s] = pg.tensors[vx].slot;
                 pg.sz_slot[s] = pg.tensors[vz].slot;
             }
+            if (cplx)
+                pg.sy_slot[s] = pg.tensors[bd.absorb_dot(F[w.q][w.t - 1], E_at(w.q, w.t, PH_Y), G[w.q][w.t], st)].slot;
             pg.sx_den[s] = norm_at(w.q, w.t);
         }
         // bonds, output order: horizontal row-major, then vertical row-major

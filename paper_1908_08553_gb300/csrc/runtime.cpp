@@ -67,7 +67,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         nslots += mb.pg->n_slots;
         mb.res_off = nres;
         mb.res_elems = kResultHeader + (int64_t)mb.pg->sx_slot.size() + (int64_t)mb.pg->zz_slot.size() +
-                       (int64_t)mb.pg->sz_slot.size();
+                       (int64_t)mb.pg->sz_slot.size() + (int64_t)mb.pg->sy_slot.size();
         nres += mb.res_elems;
     }
     lay.nin = nin;
@@ -196,6 +196,8 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
                 t.slot_E = slot_of(r.member, op.out);
                 t.K = op.K; t.N = op.N;
                 t.factored = op.factored ? 1 : 0;
+                // complex: the imaginary parts follow the real parts of the site
+                t.Ai = (pg.cplx && t.A) ? t.A + (pg.site_offset[op.site + 1] - pg.site_offset[op.site]) / 2 : nullptr;
                 off = append(&t, sizeof(t));
                 tile += 1;
             } else if (kind == OP_ABSORB || kind == OP_ABSORB_DOT) {
@@ -366,7 +368,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
     }
     // final tasks and their slot tables
     b->h_final.clear();
-    struct Tbl { size_t sx, zz, sxd, zzd, sz; };
+    struct Tbl { size_t sx, zz, sxd, zzd, sz, sy; };
     std::vector<Tbl> tbl;   // offsets in ints
     for (int mi = 0; mi < (int)b->m.size(); ++mi) {
         const Member& mb = b->m[mi];
@@ -382,6 +384,8 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         for (int s : pg.zz_den) ints.push_back((int)(mb.slot_base + s));
         tb.sz = ints.size();
         for (int s : pg.sz_slot) ints.push_back((int)(mb.slot_base + s));
+        tb.sy = ints.size();
+        for (int s : pg.sy_slot) ints.push_back((int)(mb.slot_base + s));
         tbl.push_back(tb);
     }
     lay.task_bytes = tasks.size();
@@ -398,6 +402,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         f.norm_slot = (int)(mb.slot_base + mb.pg->norm_slot);
         f.n_sites = (int)mb.pg->sx_slot.size();
         f.n_bonds = (int)mb.pg->zz_slot.size();
+        f.n_sy = (int)mb.pg->sy_slot.size();
         if (base) {
             const int* ib = reinterpret_cast<const int*>(base + lay.ints_off);
             f.sx_slots = ib + tbl[mi].sx;
@@ -405,6 +410,7 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
             f.sx_den = ib + tbl[mi].sxd;
             f.zz_den = ib + tbl[mi].zzd;
             f.sz_slots = ib + tbl[mi].sz;
+            f.sy_slots = ib + tbl[mi].sy;
             f.out = reinterpret_cast<double*>(base + lay.res_off) + mb.res_off;
         }
         f.J = 1.0;
@@ -420,18 +426,18 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
 }  // namespace
 
 std::shared_ptr<const Program> program_cached(int L, int W, int D, tn_schedule sched, tn_precision prec,
-                                              tn_work work, int knobs_code) {
+                                              tn_work work, int knobs_code, bool cplx) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, int, int, int>, std::shared_ptr<const Program>> cache;
+    static std::map<std::tuple<int, int, int, int, int, int, int, int>, std::shared_ptr<const Program>> cache;
     // the tuning table's choice for this shape unless the caller names one
     if (knobs_code < 0) knobs_code = tuned_knobs(L, W, D, prec, work).code();
-    const auto key = std::make_tuple(L, W, D, (int)sched, (int)prec, (int)work, knobs_code);
+    const auto key = std::make_tuple(L, W, D, (int)sched, (int)prec, (int)work, knobs_code, (int)cplx);
     {
         std::lock_guard<std::mutex> g(mu);
         auto it = cache.find(key);
         if (it != cache.end()) return it->second;
     }
-    auto pg = program_build(L, W, D, sched, prec, work, Knobs::from_code(knobs_code));
+    auto pg = program_build(L, W, D, sched, prec, work, Knobs::from_code(knobs_code), cplx);
     std::lock_guard<std::mutex> g(mu);
     return cache.emplace(key, pg).first->second;
 }
@@ -460,8 +466,9 @@ tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int
     for (int k = 0; k < n; ++k) {
         std::shared_ptr<const Program> pg;
         try {
-            pg = opts->program ? opts->program : program_cached(L[k], W[k], D[k], sched, prec, work, opts->knobs);
-            if (pg->plan.L != L[k] || pg->plan.W != W[k] || pg->plan.D != D[k]) {
+            pg = opts->program ? opts->program
+                               : program_cached(L[k], W[k], D[k], sched, prec, work, opts->knobs, opts->complex_sites);
+            if (pg->plan.L != L[k] || pg->plan.W != W[k] || pg->plan.D != D[k] || pg->cplx != opts->complex_sites) {
                 set_error("the given program is for another lattice shape");
                 return TN_ERR_INVALID;
             }

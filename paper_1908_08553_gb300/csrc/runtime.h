@@ -95,7 +95,8 @@ struct tn_batch {
 struct tn_lattice {
     tn_ctx* ctx = nullptr;
     int L = 0, W = 0, D = 0;
-    std::vector<double> host;
+    std::vector<double> host;        // input layout of the lattice's programs
+    bool cplx = false;               // complex site tensors (host: per site real parts, then imaginary)
     std::map<std::tuple<int, int, int>, tn_batch*> cache;   // (prec, sched, work) -> 1-member batch
 };
 
@@ -106,12 +107,13 @@ struct BatchOpts {
     bool use_graph = true;           // capture the launch sequence on the first run
     int knobs = -1;                  // program knobs (Knobs::code); -1: the tuning table's choice
     std::shared_ptr<const Program> program;   // every member runs this program (its shape must match)
+    bool complex_sites = false;      // complex site tensors (every member)
 };
 tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int* D,
                        tn_precision prec, tn_schedule sched, tn_work work, bool alloc,
                        tn_batch** out, size_t* bytes, const BatchOpts* opts = nullptr);
 std::shared_ptr<const Program> program_cached(int L, int W, int D, tn_schedule sched, tn_precision prec,
-                                              tn_work work, int knobs_code = -1);
+                                              tn_work work, int knobs_code = -1, bool cplx = false);
 tn_status batch_run(tn_batch* b, cudaStream_t st);
 void batch_destroy(tn_batch* b);
 tn_status cuda_status(cudaError_t e, const char* what);

@@ -85,8 +85,10 @@ enum OpKind {
 
 // Operator insertion on the physical leg.
 // PH_R = [[0, 1], [-1, 0]]: Y = i R on this basis, so a real state's <Y_i Y_j>
-// is -<R_i R_j> (and any single Y averages to zero).
-enum PhysOp { PH_I = 0, PH_X = 1, PH_Z = 2, PH_R = 3 };
+// is -<R_i R_j> (and any single Y averages to zero).  PH_Y = [[0, i], [-i, 0]]
+// itself, for complex site tensors only (their site matrices are built from
+// complex arithmetic, see k_sitemat).
+enum PhysOp { PH_I = 0, PH_X = 1, PH_Z = 2, PH_R = 3, PH_Y = 4 };
 
 // One two-site correlator <A_a B_b> of an explicit pair list (sites row-major).
 struct PairSpec {
@@ -164,6 +166,8 @@ struct Program {
     std::vector<int> sx_slot;     // per site (row-major, original lattice)
     std::vector<int> zz_slot;     // per bond (output order)
     std::vector<int> sz_slot;     // per site: <Z_k> numerator (denominator sx_den)
+    std::vector<int> sy_slot;     // complex site tensors: per site <Y_k> numerator (denominator sx_den)
+    bool cplx = false;            // complex site tensors: per site the real parts, then the imaginary parts
     // denominator of each ratio: <F[q][t], G[q][t]> at the step where the
     // observable meets its environment (the norm along the same rounding path),
     // or norm_slot for bonds across a cut
@@ -176,26 +180,31 @@ struct Program {
 };
 
 // Internal work kinds beyond tn_work: the nearest-neighbour correlators
-// <A_i B_j> alone, A = PhysOp a and B = PhysOp b (X or Z).
-inline tn_work work_bonds(int a, int b) { return (tn_work)(16 + 4 * a + b); }
+// <A_i B_j> alone, A = PhysOp a and B = PhysOp b (X, Z, R or Y).
+inline tn_work work_bonds(int a, int b) { return (tn_work)(16 + 8 * a + b); }
 inline bool work_is_bonds(tn_work w) { return (int)w >= 16; }
-inline int work_bond_a(tn_work w) { return ((int)w - 16) / 4; }
-inline int work_bond_b(tn_work w) { return ((int)w - 16) % 4; }
+inline int work_bond_a(tn_work w) { return ((int)w - 16) / 8; }
+inline int work_bond_b(tn_work w) { return ((int)w - 16) % 8; }
 inline bool work_valid(tn_work w) {
     if (w == TN_WORK_NORM || w == TN_WORK_ENERGY) return true;
-    if (!work_is_bonds(w)) return false;
+    if (!work_is_bonds(w) || (int)w >= 16 + 8 * 8) return false;
     const int a = work_bond_a(w), b = work_bond_b(w);
-    return (a == PH_X || a == PH_Z || a == PH_R) && (b == PH_X || b == PH_Z || b == PH_R) && (int)w < 32;
+    auto ok = [](int o) { return o == PH_X || o == PH_Z || o == PH_R || o == PH_Y; };
+    return ok(a) && ok(b);
 }
 
+// cplx: complex site tensors (the input layout and the site matrices change,
+// nothing downstream of them does)
 std::shared_ptr<const Program> program_build(int L, int W, int D, tn_schedule sched,
-                                             tn_precision prec, tn_work work, Knobs knobs = Knobs());
+                                             tn_precision prec, tn_work work, Knobs knobs = Knobs(),
+                                             bool cplx = false);
 // the same for a given plan (any orientation and cut)
 // pairs (work TN_WORK_ENERGY): the correlators of that list instead of the
 // energy's observables (result order = list order)
 std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision prec, tn_work work,
                                                   Knobs knobs = Knobs(),
-                                                  const std::vector<PairSpec>* pairs = nullptr);
+                                                  const std::vector<PairSpec>* pairs = nullptr,
+                                                  bool cplx = false);
 // Knobs the tuning table holds for this shape (the defaults if it holds none).
 Knobs tuned_knobs(int L, int W, int D, tn_precision prec, tn_work work);
 // Consistency of a built program ("" if sound): every op runs after the

@@ -79,10 +79,11 @@ struct DotTask {
 
 struct SiteMatTask {
     const double* A;      // raw FP64 site tensor [p][u][l][dn][rt]
+    const double* Ai;     // its imaginary parts (complex site tensors), else null
     void* E;              // K x N, compute dtype
     int dims[4];          // original leg dims u, l, dn, rt
     int map[4];           // frame role (u, l, dn, rt) -> original leg
-    int phys;             // 0 I, 1 X, 2 Z
+    int phys;             // 0 I, 1 X, 2 Z, 3 R, 4 Y (complex only)
     int slot_E;
     int K, N;
     int factored;         // 1: the two layer factors of the double-layer matrix (kFactorEntries)
@@ -105,10 +106,11 @@ struct FinalTask {
     const int* sx_den;    // n_sites: slot of each ratio's denominator
     const int* zz_den;    // n_bonds
     const int* sz_slots;  // n_sites: <Z_k> numerators (same denominators as sx)
-    double* out;          // kResultHeader + 2 n_sites + n_bonds: <X_k>, <Z_i Z_j>, <Z_k>
+    const int* sy_slots;  // n_sy (0 or n_sites): <Y_k> numerators (complex site tensors)
+    double* out;          // kResultHeader + 2 n_sites + n_bonds + n_sy: <X_k>, <Z_i Z_j>, <Z_k>, <Y_k>
     double J, h;
     int norm_slot;
-    int n_sites, n_bonds;
+    int n_sites, n_bonds, n_sy;
 };
 
 struct ConstOne {

@@ -94,6 +94,9 @@ SIGNATURES = {
     "tn_peak_probe": (c_int, [c_void_p, c_int, POINTER(c_double)]),
     "tn_ite_init_product": (c_int, [c_void_p]),
     "tn_pair_correlators": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "tn_set_site_tensors_complex": (c_int, [c_void_p, c_void_p, c_void_p, c_size_t]),
+    "tn_lattice_is_complex": (c_int, [c_void_p]),
+    "tn_site_expectations": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "tn_autotune": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_size_t]),
     "tn_autotune_lookup": (c_int, [c_int, c_int, c_int, c_int, c_int, POINTER(c_int), POINTER(c_double),
                                    POINTER(c_double), POINTER(c_int)]),
@@ -403,6 +406,25 @@ def tn_absorb_dot_noalloc(dtype: int, x_in, E, adj, P: int, K: int, N: int, S: i
 
 def tn_ctx_set_profiling(ctx, on: bool):
     check(lib().tn_ctx_set_profiling(ctx, 1 if on else 0), "tn_ctx_set_profiling")
+
+
+def tn_set_site_tensors_complex(lat, A) -> None:
+    """Complex site tensors (one complex array in the real layout)."""
+    A = np.asarray(A, dtype=np.complex128)
+    re = np.ascontiguousarray(A.real)
+    im = np.ascontiguousarray(A.imag)
+    check(lib().tn_set_site_tensors_complex(lat, _ptr(re), _ptr(im), re.size), "tn_set_site_tensors_complex")
+
+
+def tn_lattice_is_complex(lat) -> bool:
+    return bool(lib().tn_lattice_is_complex(lat))
+
+
+def tn_site_expectations(lat, prec: int, op: int, L: int, W: int) -> np.ndarray:
+    """<O_k> for every site, O = TN_OP_X, TN_OP_Y or TN_OP_Z."""
+    out = np.zeros(L * W)
+    check(lib().tn_site_expectations(lat, prec, op, _ptr(out)), "tn_site_expectations")
+    return out
 
 
 def tn_pair_correlators(lat, prec: int, op_a: int, op_b: int, i, j) -> np.ndarray:

@@ -288,3 +288,40 @@ def test_autotune_table_on_the_host(cpu_ctx, tmp_path):
             tn.tn_destroy_lattice(lat)
     finally:
         tn.tn_autotune_clear()
+
+
+def test_complex_lattice_on_the_host(cpu_ctx):
+    L, W, D = 3, 4, 2
+    lat = tn.tn_create_lattice(cpu_ctx, L, W, D)
+    try:
+        n = tn.tn_lattice_elems(L, W, D)
+        A = inputs.random_complex_lattice(L, W, D, 3)
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_set_site_tensors_complex(lat, A[:-1])
+        assert e.value.status == tn.TN_ERR_INVALID
+        fp_real = tn.tn_footprint(lat, tn.TN_SCHED_AUTO, tn.TN_FP32, tn.TN_WORK_ENERGY)
+        info_real = tn.tn_program_info(lat, tn.TN_FP32)
+        tn.tn_set_site_tensors_complex(lat, A)
+        assert tn.tn_lattice_is_complex(lat)
+        # the complex energy program is sound (host check) and holds the <Y_k> terms too
+        info = tn.tn_program_info(lat, tn.TN_FP32)
+        assert info["ops"] > info_real["ops"]
+        assert tn.tn_footprint(lat, tn.TN_SCHED_AUTO, tn.TN_FP32, tn.TN_WORK_ENERGY) > fp_real
+        with pytest.raises(tn.TNError) as e:       # real read-back refused
+            tn.tn_get_site_tensors(lat, n)
+        assert e.value.status == tn.TN_ERR_INVALID
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_bmps_norm(lat, 4)
+        assert e.value.status == tn.TN_ERR_INVALID
+        for op in (tn.TN_OP_X, tn.TN_OP_Y, tn.TN_OP_Z):
+            with pytest.raises(tn.TNError) as e:
+                tn.tn_site_expectations(lat, tn.TN_FP64, op, L, W)
+            assert e.value.status == tn.TN_ERR_NO_DEVICE
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_site_expectations(lat, tn.TN_FP64, tn.TN_OP_ZZ, L, W)
+        assert e.value.status == tn.TN_ERR_INVALID
+        tn.tn_fill_random(lat, 5)                  # back to real
+        assert not tn.tn_lattice_is_complex(lat)
+        assert tn.tn_get_site_tensors(lat, n).size == n
+    finally:
+        tn.tn_destroy_lattice(lat)
