@@ -486,7 +486,7 @@ def run_headline(args):
         line["roofline_absorb_stream"] = absorb_stream_roofline(ctx, stream, hbm, src)
         line["batch_8x8_d2"] = batch_8x8(tn, torch, ctx, stream, args.batch)
         if args.serve_requests > 0:
-            line["serving"] = serve_stream(args.serve_requests, args.calibrate, "fp32", seq_sample=3,
+            line["serving"] = serve_stream(args.serve_requests, args.calibrate, "bf16x6", seq_sample=3,
                                            seq_seconds=30.0)
         line["cpu_baseline"] = cpu_baseline(seeds)
     tn.tn_batch_destroy(b)
@@ -640,7 +640,7 @@ def serve_stream(n: int, calibrate: int, precision: str, seq_sample: int, seq_se
     rate = 0.8 * cap
 
     # Poisson stream with a polling collector
-    pending, done, lock = {}, {}, threading.Lock()
+    pending, done, lock, shapes_of = {}, {}, threading.Lock(), {}
     stop = threading.Event()
     deadline = time.perf_counter() + 900.0
 
@@ -675,10 +675,12 @@ def serve_stream(n: int, calibrate: int, precision: str, seq_sample: int, seq_se
             raise
         with lock:
             pending[t] = (L, W, time.perf_counter())
+            shapes_of[t] = (L, W, D)
     stop.set()
     th.join()
     t_end = max(v[1] for v in done.values())
     lat = np.array([v[1] - v[0] for v in done.values()])
+    lat_d = {d: np.array([v[1] - v[0] for t, v in done.items() if shapes_of[t][2] == d]) for d in (2, 3)}
     served = len(done)
 
     # sequential plain FP64 solves of a sample of the admitted requests (those
@@ -712,6 +714,12 @@ def serve_stream(n: int, calibrate: int, precision: str, seq_sample: int, seq_se
             "offered_rate_jobs_per_s": rate, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
             "throughput_energies_per_s": served / (t_end - t_start),
+            "by_D": {f"D={d}": {"served": int(v.size),
+                                "p50_latency_s": float(np.percentile(v, 50)) if v.size else None,
+                                "p99_latency_s": float(np.percentile(v, 99)) if v.size else None}
+                     for d, v in lat_d.items()},
+            "calibration": {"requests": len(calib), "what": "a burst of admissible requests from the same "
+                            "distribution, submitted at once; capacity = requests / wall time"},
             "sequential_fp64": {"energies_per_s": seq_rate, "sample": n_seq},
             "distribution": "L, W ~ U{4..12}, D ~ U{2,3}, h ~ U[0.5,5], seeded uniform[-1,1) tensors"}
 
@@ -719,7 +727,7 @@ def serve_stream(n: int, calibrate: int, precision: str, seq_sample: int, seq_se
 def run_serve(args):
     import torch
     torch.cuda.set_device(0)
-    line = serve_stream(args.requests, args.calibrate, args.precision or "fp32", args.seq_sample, args.seq_seconds)
+    line = serve_stream(args.requests, args.calibrate, args.precision or "bf16x6", args.seq_sample, args.seq_seconds)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -948,7 +956,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="headline only: skip the other precisions, the 8x8 batch, serving and the CPU baseline")
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end measurement")
-    ap.add_argument("--serve-requests", type=int, default=40, help="headline extras: served stream length")
+    ap.add_argument("--serve-requests", type=int, default=48, help="headline extras: served stream length")
     ap.add_argument("--workload", default="large", choices=["large", "8x8", "serve", "batch", "case"],
                     help="large: 12x12 D=2 + 8x8 D=3 energies (the headline); 8x8: the 8x8 D=2 batch; "
                          "serve: Poisson request stream; batch: 512 mixed lattices; case: --batch copies of "
@@ -963,7 +971,7 @@ def main():
     ap.add_argument("--members", type=int, default=512, help="batch: lattices")
     ap.add_argument("--batch-seed", type=int, default=2, help="batch: tensor seed")
     ap.add_argument("--requests", type=int, default=300, help="serve: requests in the stream")
-    ap.add_argument("--calibrate", type=int, default=20, help="serve: burst size for the capacity")
+    ap.add_argument("--calibrate", type=int, default=24, help="serve: burst size for the capacity")
     ap.add_argument("--seq-sample", type=int, default=30, help="serve: sequential FP64 sample")
     ap.add_argument("--seq-seconds", type=float, default=60.0, help="serve: time cap of the FP64 sample")
     args = ap.parse_args()

@@ -272,7 +272,10 @@ typedef struct {
 
 /* Queue a job.  It is admitted to the GPU when its exact footprint fits the
  * budget left by running jobs; jobs that can never fit return
- * TN_ERR_OVER_BUDGET here.  Admitted jobs run concurrently with earlier ones. */
+ * TN_ERR_OVER_BUDGET here.  Admitted jobs run concurrently with earlier ones:
+ * jobs whose estimated device time (from their contraction program) is at
+ * most 20 ms are batched together on high-priority streams, longer ones run
+ * alone on low-priority streams, so short jobs never queue behind long ones. */
 tn_status tn_submit(tn_ctx *ctx, const tn_job *job, uint64_t *ticket);
 /* TN_NOT_READY until the job is done; then fills *out (sx/szsz if non-NULL)
  * and releases the ticket. */

@@ -1,17 +1,23 @@
 // Request server: tn_submit / tn_poll / tn_wait with continuous batching.
 //
-// A scheduler thread per context keeps a FIFO of submitted jobs.  Whenever a
-// stream slot is free and the HBM budget left by running batches allows, it
-// takes the longest FIFO prefix of jobs with the head's precision whose exact
-// footprints fit, builds one batch from them (one device buffer from the
-// stream-ordered pool, grouped launches), uploads their tensors, runs it on its
-// own stream and queues the read-back of the results.  Batches on different
-// streams overlap on the device; when a batch's completion event fires its
-// results go to the jobs, its memory returns to the budget, and jobs that were
-// waiting for memory are admitted.  A job whose footprint alone exceeds the
-// budget is refused at submit time (TN_ERR_OVER_BUDGET).  Every member's
-// results depend only on its own tasks (shape-fixed tiles, index-ordered
-// reductions), so a job gives the same bits alone and in any mix.
+// A scheduler thread per context keeps a FIFO of submitted jobs.  Each job's
+// device time is estimated at submit from its contraction program (multiply-
+// adds and bytes of every pairwise contraction), which sorts it into one of two
+// classes.  Light jobs are batched: whenever one of the high-priority streams
+// is free and the HBM budget left by running batches allows, the scheduler
+// takes the light jobs in FIFO order with the first one's precision whose
+// exact footprints fit, builds one batch from them (one device buffer from the
+// stream-ordered pool, grouped launches), uploads their tensors, runs it on
+// that stream and queues the read-back of the results.  Heavy jobs (seconds of
+// work, tens of GB) run alone, one per low-priority stream, so a light job
+// never waits for a heavy one to finish: its blocks are scheduled ahead of the
+// heavy job's on the SMs.  When a batch's completion event fires its results
+// go to the jobs, its memory returns to the budget, and jobs that were waiting
+// for memory are admitted.  A job whose footprint alone exceeds the budget is
+// refused at submit time (TN_ERR_OVER_BUDGET).  Every member's results depend
+// only on its own tasks (shape-fixed tiles, index-ordered reductions), so a
+// job gives the same bits alone, in any mix and on either stream class.
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 
@@ -33,6 +39,8 @@ struct SJob {
     double J = 1.0, h = 0.0;
     std::vector<double> tensors;
     size_t footprint = 0;
+    double est_s = 0.0;         // estimated device time
+    bool heavy = false;
     int state = 0;              // 0 pending, 1 running, 2 finished
     tn_status status = TN_OK;
     std::vector<double> result;
@@ -46,8 +54,24 @@ struct SBatch {
     int slot = -1;
 };
 
-constexpr int kStreams = 4;
+constexpr int kLightStreams = 6;              // high priority, batched light jobs
+constexpr int kHeavyStreams = 2;              // low priority, one heavy job each
+constexpr int kStreams = kLightStreams + kHeavyStreams;
 constexpr int kMaxMembers = 256;
+constexpr double kHeavySeconds = 0.02;        // estimated device time that makes a job heavy
+// result doubles of one served member at most: header, <X_k>, <Z_i Z_j>, <Z_k>
+// of a 16 x 16 lattice
+constexpr size_t kMaxResult = kResultHeader + 256 + 2 * 16 * 15 + 256;
+
+// Device time of a job from its program: multiply-adds at a sustained rate of
+// the precision's arithmetic plus bytes at a sustained HBM rate, plus launch
+// latency per wave.  Only orders jobs; nothing depends on its accuracy.
+double estimate_seconds(const Program& pg, tn_precision prec) {
+    double macs = 0.0, bytes = 0.0;
+    for (const Op& op : pg.ops) { macs += (double)op.macs; bytes += (double)op.bytes; }
+    const double rate = prec == TN_FP64 ? 5e11 : (pg.nsplit ? 1e14 : 2e13);
+    return macs / rate + bytes / 3e12 + 5e-6 * pg.n_levels;
+}
 
 }  // namespace
 
@@ -105,23 +129,39 @@ void Server::retire_locked() {
 
 bool Server::admit(std::unique_lock<std::mutex>& lk) {
     if (pending.empty()) return false;
-    int slot = -1;
-    for (int s = 0; s < kStreams; ++s)
-        if (!busy[s]) { slot = s; break; }
-    if (slot < 0) return false;
-    // FIFO prefix with the head's precision that fits the budget left
-    const tn_precision prec = pending.front()->prec;
     const size_t left = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
+    auto free_slot = [&](int s0, int s1) {
+        for (int s = s0; s < s1; ++s)
+            if (!busy[s]) return s;
+        return -1;
+    };
     std::vector<SJob*> take;
-    size_t sum = 0;
-    for (SJob* j : pending) {
-        if (j->prec != prec || (int)take.size() >= kMaxMembers) break;
-        if (sum + j->footprint > left) break;
-        sum += j->footprint;
-        take.push_back(j);
+    int slot = free_slot(0, kLightStreams);
+    if (slot >= 0) {
+        // light jobs in FIFO order with the first one's precision that fit the
+        // budget left (stopping at the first that does not: no overtaking there)
+        int prec = -1;
+        size_t sum = 0;
+        for (SJob* j : pending) {
+            if (j->heavy) continue;
+            if (prec < 0) prec = j->prec;
+            if ((int)j->prec != prec || (int)take.size() >= kMaxMembers || sum + j->footprint > left) break;
+            sum += j->footprint;
+            take.push_back(j);
+        }
     }
-    if (take.empty()) return false;   // the head waits for memory to free up
-    for (size_t k = 0; k < take.size(); ++k) pending.pop_front();
+    if (take.empty()) {
+        // the first heavy job, alone, if a low-priority stream and its memory are free
+        slot = free_slot(kLightStreams, kStreams);
+        if (slot < 0) return false;
+        for (SJob* j : pending)
+            if (j->heavy) {
+                if (j->footprint <= left) take.push_back(j);
+                break;
+            }
+        if (take.empty()) return false;   // it waits for memory to free up
+    }
+    for (SJob* j : take) pending.erase(std::find(pending.begin(), pending.end(), j));
     for (SJob* j : take) j->state = 1;
     busy[slot] = true;
     lk.unlock();
@@ -137,7 +177,7 @@ bool Server::admit(std::unique_lock<std::mutex>& lk) {
     opts.async_alloc = true;
     opts.use_graph = false;
     tn_batch* b = nullptr;
-    tn_status st = batch_create(ctx, (int)take.size(), L.data(), W.data(), D.data(), prec, TN_SCHED_AUTO,
+    tn_status st = batch_create(ctx, (int)take.size(), L.data(), W.data(), D.data(), take[0]->prec, TN_SCHED_AUTO,
                                 TN_WORK_ENERGY, true, &b, nullptr, &opts);
     cudaEvent_t ev = nullptr;
     if (st == TN_OK) {
@@ -149,14 +189,13 @@ bool Server::admit(std::unique_lock<std::mutex>& lk) {
                                          cudaMemcpyHostToDevice, b->stream), "served upload");
         if (st == TN_OK) st = batch_run(b, b->stream);
         // read-back buffer: the results, then one double holding the status word
+        // (allocated once per slot for the largest batch: freeing pinned memory
+        // would synchronise the whole device, stalling the scheduler behind
+        // every running job)
         const size_t need = (size_t)b->lay.nres + 1;
         if (st == TN_OK && pinned_n[slot] < need) {
-            // the slot is idle, so its old buffer is not in use
-            if (pinned[slot]) cudaFreeHost(pinned[slot]);
-            pinned[slot] = nullptr;
-            const size_t n = std::max(need, pinned_n[slot] * 2);
-            st = cuda_status(cudaMallocHost(reinterpret_cast<void**>(&pinned[slot]), n * 8), "pinned buffer");
-            pinned_n[slot] = st == TN_OK ? n : 0;
+            set_error("no pinned read-back buffer for this batch");
+            st = TN_ERR_OOM;
         }
         if (st == TN_OK)
             st = cuda_status(cudaMemcpyAsync(pinned[slot], b->buf + b->lay.res_off, (size_t)b->lay.nres * 8,
@@ -210,12 +249,21 @@ Server* get_server(tn_ctx* ctx, bool create) {
         auto* s = new Server();
         s->ctx = ctx;
         cudaSetDevice(ctx->device);
-        for (int k = 0; k < kStreams; ++k) cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking);
+        // light batches on the highest stream priority, heavy jobs on the lowest
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        for (int k = 0; k < kStreams; ++k)
+            cudaStreamCreateWithPriority(&s->streams[k], cudaStreamNonBlocking, k < kLightStreams ? greatest : least);
         // keep freed batch memory in the pool instead of returning it to the driver
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
             uint64_t thr = ctx->budget;
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        for (int k = 0; k < kStreams; ++k) {
+            const size_t n = (size_t)kMaxMembers * kMaxResult + 1;
+            if (cudaMallocHost(reinterpret_cast<void**>(&s->pinned[k]), n * 8) == cudaSuccess) s->pinned_n[k] = n;
+            else s->pinned[k] = nullptr;
         }
         s->th = std::thread([s] { s->loop(); });
         ctx->server = s;
@@ -273,7 +321,11 @@ tn_status tn_submit(tn_ctx* ctx, const tn_job* job, uint64_t* ticket) {
         tn_batch* probe = nullptr;
         tn_status st = batch_create(ctx, 1, &j->L, &j->W, &j->D, j->prec, TN_SCHED_AUTO, TN_WORK_ENERGY, false,
                                     &probe, &j->footprint);
-        if (probe) delete probe;
+        if (probe) {
+            j->est_s = estimate_seconds(*probe->m[0].pg, j->prec);
+            j->heavy = j->est_s > kHeavySeconds;
+            delete probe;
+        }
         if (st != TN_OK) return st;
         if (j->footprint > ctx->budget) {
             set_error("job footprint " + std::to_string(j->footprint) + " B exceeds the budget");

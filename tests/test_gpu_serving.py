@@ -149,3 +149,33 @@ def test_served_wait_timeout_reaches_the_caller():
             tn.tn_destroy_lattice(lat)
     finally:
         tn.tn_ctx_destroy(ctx)
+
+
+def test_light_jobs_overtake_a_heavy_one():
+    # an 8x9 D=3 FP32 energy (seconds of work, a low-priority stream of its
+    # own) must not hold back 4x4 D=2 jobs submitted after it: they finish
+    # while it is still running, and every result equals its alone value
+    import time
+
+    import torch
+    torch.cuda.init()
+    ctx = tn.tn_ctx_create(0, 0)
+    try:
+        Lh, Wh, Dh = 8, 9, 3
+        Ah = inputs.random_lattice(Lh, Wh, Dh, 899)
+        th = tn.tn_submit(ctx, Lh, Wh, Dh, tn.TN_FP32, 1.0, 3.04, tensors=Ah)
+        time.sleep(0.2)
+        light = []
+        for k in range(6):
+            A = inputs.random_lattice(4, 4, 2, 440 + k)
+            light.append((tn.tn_submit(ctx, 4, 4, 2, tn.TN_FP32, 1.0, 3.04, tensors=A), A))
+        got = [tn.tn_wait(ctx, t, 30.0, 4, 4) for t, _ in light]
+        assert tn.tn_poll(ctx, th, Lh, Wh) is None        # the heavy job is still running
+        r, _, _ = tn.tn_wait(ctx, th, 300.0, Lh, Wh)
+        ra, _, _ = _alone(ctx, Lh, Wh, Dh, Ah, tn.TN_FP32, 3.04)
+        assert r.energy == ra.energy
+        for (r, sx, zz), (_, A) in zip(got, light):
+            ra, sxa, zza = _alone(ctx, 4, 4, 2, A, tn.TN_FP32, 3.04)
+            assert r.energy == ra.energy and np.array_equal(sx, sxa) and np.array_equal(zz, zza)
+    finally:
+        tn.tn_ctx_destroy(ctx)
