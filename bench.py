@@ -866,6 +866,25 @@ def run_batch(args):
         groups.append(cur)
     stream = torch.cuda.Stream()
     ctx = tn.tn_ctx_create(0, int(250e9), stream)
+    # autotune every (L, W, D) bucket whose copies fit the tuning budget (the
+    # largest D = 3 shapes keep the default choices); every batch built after
+    # this takes its programs from the table
+    tune = None
+    if not args.no_autotune:
+        shapes = sorted({(int(Ls[k]), int(Ws[k]), int(Ds[k])) for k in ok})
+        t0 = time.perf_counter()
+        tn.tn_autotune(ctx, [s[0] for s in shapes], [s[1] for s in shapes], [s[2] for s in shapes], prec,
+                       tn.TN_WORK_ENERGY, reps=3, max_bytes=int(4e9))
+        tune_s = time.perf_counter() - t0
+        rows = [(s, tn.tn_autotune_lookup(*s, prec)) for s in shapes]
+        tuned = [(s, r) for s, r in rows if r["tuned"]]
+        changed = [(s, r) for s, r in tuned if r["knobs"] != 15]
+        tune = {"buckets": len(shapes), "tuned": len(tuned), "changed_from_default": len(changed),
+                "seconds": tune_s,
+                "changed": [{"L": s[0], "W": s[1], "D": s[2], "knobs": r["knobs"],
+                             "best_ms": r["best_ms"], "default_ms": r["default_ms"]} for s, r in changed[:12]],
+                "what": "per (L, W, D): every applicable program choice timed on copies of the shape "
+                        "(at most 4 GB); the fastest by >= 2% kept; shapes above 4 GB keep the defaults"}
     total_ms, results, launches = 0.0, {}, 0
     for g in groups:
         b = tn.tn_batch_create(ctx, Ls[g], Ws[g], Ds[g], prec)
@@ -893,7 +912,7 @@ def run_batch(args):
     line = {"metric": "batched exact TFIM-PEPS energy evals/s", "workload": "512 mixed lattices, L, W in 4..10, D in {2,3}",
             "precision": args.precision or "fp32", "members": n, "evaluated": m, "excluded_over_budget": len(excluded),
             "excluded_shapes": sorted({(int(Ls[k]), int(Ws[k]), int(Ds[k])) for k in excluded}),
-            "graphs": len(groups), "kernel_launches": launches, "ms": total_ms,
+            "graphs": len(groups), "kernel_launches": launches, "ms": total_ms, "autotune": tune,
             "evals_per_s": m / (total_ms / 1e3), "energies_per_s": m / (total_ms / 1e3),
             "budget_gb": budget / 1e9,
             "distribution": "L, W ~ U{4..10}, D ~ U{2,3}, h ~ U[0.5,5], seeded uniform[-1,1) tensors"}
@@ -970,6 +989,7 @@ def main():
     ap.add_argument("--clock-log", default=None, help="CSV file for the nvidia-smi clock samples")
     ap.add_argument("--members", type=int, default=512, help="batch: lattices")
     ap.add_argument("--batch-seed", type=int, default=2, help="batch: tensor seed")
+    ap.add_argument("--no-autotune", action="store_true", help="batch: keep the default program choices")
     ap.add_argument("--requests", type=int, default=300, help="serve: requests in the stream")
     ap.add_argument("--calibrate", type=int, default=24, help="serve: burst size for the capacity")
     ap.add_argument("--seq-sample", type=int, default=30, help="serve: sequential FP64 sample")

@@ -382,9 +382,13 @@ tn_status tn_ite_run(tn_lattice *lat, const tn_ite_params *params, double *energ
  * reformulation -- only speed differs:
  *   bit 0  FP32 D = 2: two steps of a frame row fused in one pass
  *   bit 1  FP32 D <= 2: <X_k>, <Z_k> and the local norm in one absorb-dot
- *   bit 2  FP32 / FP64 D = 3 interior steps: ket pass then bra pass
- *   bit 3  BF16x3 / BF16x6: ring products on the tensor cores (else FP32 SIMT)
- * 15 (all set) is the fixed default.  tn_autotune times every combination that
+ *   bit 2  D = 3 interior steps: ket pass then bra pass on FP32 / FP64 ALUs
+ *          (cleared: the double-layer site matrix, absorbed on the tensor
+ *          cores in BF16x3 / BF16x6)
+ *   bit 3  BF16x3 / BF16x6: products of at least 2^26 multiply-adds on the
+ *          tensor cores (else FP32 SIMT)
+ *   bit 4  BF16x3 / BF16x6: smaller products on the tensor cores too
+ * 15 (bits 0-3 set) is the fixed default; codes run from 0 to 31.  tn_autotune times every combination that
  * changes the program of each distinct (L[k], W[k], D[k]) on a batch of
  * copies of it (as many as fit max_bytes, 0 = 4 GiB, at most 64; shapes whose
  * single footprint exceeds max_bytes are skipped), `reps` timed runs after one

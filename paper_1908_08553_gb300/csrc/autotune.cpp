@@ -31,15 +31,19 @@ std::vector<int> candidates(int D, tn_precision prec, tn_work work) {
     std::vector<int> bits;   // knob bits that apply
     const bool fp32_store = prec != TN_FP64;
     const bool tc = prec == TN_BF16X3 || prec == TN_BF16X6;
-    if (D == 3 && !tc) bits.push_back(4);                                  // factor_d3
+    if (D == 3) bits.push_back(4);              // factor_d3 (off: tensor-core D = 3 absorption when tc)
     if (fp32_store && D <= 2 && work != TN_WORK_NORM) bits.push_back(2);   // site_triple
     if (fp32_store && D == 2 && work != TN_WORK_NORM) bits.push_back(1);   // fuse_pairs
     if (tc) bits.push_back(8);                                             // tc_products
+    if (tc) bits.push_back(16);                                            // tc_small
+    // every combination of the applicable bits flipped from the default
+    // (tc_small only matters with tc_products)
     std::vector<int> out{kDefaultKnobs};
     for (int mask = 1; mask < (1 << bits.size()); ++mask) {
         int code = kDefaultKnobs;
         for (size_t b = 0; b < bits.size(); ++b)
-            if (mask & (1 << b)) code &= ~bits[b];
+            if (mask & (1 << b)) code ^= bits[b];
+        if ((code & 16) && !(code & 8)) continue;
         out.push_back(code);
     }
     return out;
@@ -147,7 +151,7 @@ tn_status tn_autotune_lookup(int L, int W, int D, tn_precision prec, tn_work wor
 }
 
 tn_status tn_autotune_set(int L, int W, int D, tn_precision prec, tn_work work, int knobs) {
-    if (knobs < 0 || knobs > kDefaultKnobs || L < 1 || W < 1 || D < 1) return TN_ERR_INVALID;
+    if (knobs < 0 || knobs > kMaxKnobs || L < 1 || W < 1 || D < 1) return TN_ERR_INVALID;
     std::lock_guard<std::mutex> g(g_tune_mu);
     TuneEntry& e = g_tune[std::make_tuple(L, W, D, (int)prec, (int)work)];
     e.knobs = knobs;
@@ -187,7 +191,7 @@ tn_status tn_autotune_load(const char* path) {
         int l, w, d, p, wk, kn, cp, cd;
         double bm, dm;
         if (std::sscanf(line, "%d %d %d %d %d %d %lf %lf %d %d", &l, &w, &d, &p, &wk, &kn, &bm, &dm, &cp, &cd) != 10 ||
-            kn < 0 || kn > kDefaultKnobs) {
+            kn < 0 || kn > kMaxKnobs) {
             std::fclose(f);
             set_error("malformed tuning file");
             return TN_ERR_INVALID;

@@ -76,9 +76,11 @@ public:
         auto key = std::make_pair(site, phys);
         auto it = E_.find(key);
         if (it != E_.end()) return it->second;
-        // interior D = 3 steps off the tensor cores: keep the two layer factors
-        // (Sec. 5, bra and ket layers) and absorb them one after the other
-        const bool factored = pg_.nsplit == 0 && s.K == 81 && s.N == 81 && pg_.knobs.factor_d3;
+        // interior D = 3 steps: keep the two layer factors (Sec. 5, bra and
+        // ket layers) and absorb them one after the other; without that choice
+        // the double-layer matrix is formed (and, in the split-BF16 precisions,
+        // the step runs on the tensor cores)
+        const bool factored = s.K == 81 && s.N == 81 && pg_.knobs.factor_d3;
         const int e = tensor(factored ? (int64_t)kFactorEntries : (int64_t)s.K * s.N, 0);
         pg_.tensors[e].factored = factored;
         Op op;
@@ -119,9 +121,10 @@ public:
         op.K = trans ? s.N : s.K;
         op.N = trans ? s.K : s.N;
         op.transE = trans;
-        // wide double-layer steps (D = 3 interior, K = N = 81) go to the tensor cores
-        if (pg_.nsplit && op.K == 81 && op.N == 81) op.nsplit = pg_.nsplit;
         op.factored = pg_.tensors[E].factored;
+        // wide double-layer steps (D = 3 interior, K = N = 81) not in the
+        // factored form go to the tensor cores
+        if (pg_.nsplit && op.K == 81 && op.N == 81 && !op.factored) op.nsplit = pg_.nsplit;
         op.bytes = (double)(s.n_in + s.n_out) * pg_.esize;
         // the factored form does 2 x 2 x 9^3 multiply-adds per outer position instead of 81^2
         op.macs = op.factored ? (double)s.P * s.S * 2916.0 : (double)s.mac;
@@ -139,8 +142,8 @@ public:
         op.level = level;
         op.in = in; op.E = E; op.adj = adj; op.out = out;
         op.P = s.P; op.S = s.S; op.K = s.K; op.N = s.N;
-        if (pg_.nsplit && op.K == 81 && op.N == 81) op.nsplit = pg_.nsplit;
         op.factored = pg_.tensors[E].factored;
+        if (pg_.nsplit && op.K == 81 && op.N == 81 && !op.factored) op.nsplit = pg_.nsplit;
         op.bytes = (double)(s.n_in + s.n_out) * pg_.esize;
         op.macs = (op.factored ? (double)s.P * s.S * 2916.0 : (double)s.mac) + (double)s.n_out;
         use(in, level); use(E, level); use(adj, level);
@@ -240,7 +243,12 @@ public:
     // C[m][n] = sum_k A(m,k) B(k,n); dot partner Cd -> scalar.
     int gemm(int A, int B, int64_t M, int64_t N, int64_t K, int64_t sam, int64_t sak,
              int64_t sbk, int64_t sbn, int Cd = -1) {
-        if (pg_.nsplit && pg_.knobs.tc_products && M >= 128 && N >= 128 && K >= 64) {
+        // tensor cores for products of at least 2^26 multiply-adds: below that
+        // (e.g. the 256^3 ring of an 8 x 8 D = 2 lattice: 14.2 against 12.0 ms
+        // per batch of 256 lattices in BF16x6) splitting the operands and the
+        // per-tile set-up cost more than the FP32 SIMT product
+        if (pg_.nsplit && pg_.knobs.tc_products && M >= 128 && N >= 128 && K >= 64 &&
+            (M * N * K >= (1LL << 26) || pg_.knobs.tc_small)) {
             // tensor cores: C = A' B'^T with A'[m][k] = A(m,k) and B'[n][k] = B(k,n)
             const int Ap = tc_split(A, M, K, sam, sak);
             const int Bp = tc_split(B, N, K, sbn, sbk);

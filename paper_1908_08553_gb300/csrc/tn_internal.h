@@ -140,16 +140,23 @@ struct Op {
 struct Knobs {
     bool fuse_pairs = true;     // FP32 D = 2: two steps of a frame row in one pass (OP_ABSORB2)
     bool site_triple = true;    // FP32 D <= 2: <X_k>, <Z_k> and the local norm in one absorb-dot
-    bool factor_d3 = true;      // FP32 / FP64 D = 3 interior steps: ket pass then bra pass
-    bool tc_products = true;    // BF16x3 / BF16x6: ring products on the tensor cores (else FP32 SIMT)
-    int code() const { return (fuse_pairs ? 1 : 0) | (site_triple ? 2 : 0) | (factor_d3 ? 4 : 0) | (tc_products ? 8 : 0); }
+    bool factor_d3 = true;      // D = 3 interior steps: ket pass then bra pass (off: the double-layer
+                                // matrix, on the tensor cores in the split-BF16 precisions)
+    bool tc_products = true;    // BF16x3 / BF16x6: products of >= 2^26 multiply-adds on the tensor cores
+    bool tc_small = false;      // ... and the smaller ones too (else FP32 SIMT)
+    int code() const {
+        return (fuse_pairs ? 1 : 0) | (site_triple ? 2 : 0) | (factor_d3 ? 4 : 0) | (tc_products ? 8 : 0) |
+               (tc_small ? 16 : 0);
+    }
     static Knobs from_code(int c) {
         Knobs k;
         k.fuse_pairs = c & 1; k.site_triple = c & 2; k.factor_d3 = c & 4; k.tc_products = c & 8;
+        k.tc_small = c & 16;
         return k;
     }
 };
 constexpr int kDefaultKnobs = 15;
+constexpr int kMaxKnobs = 31;
 
 // Result addressing inside one program: which scalar slots hold what.
 struct Program {

@@ -274,7 +274,7 @@ def test_autotune_table_on_the_host(cpu_ctx, tmp_path):
         tn.tn_autotune_load(path)
         assert tn.tn_autotune_lookup(8, 8, 2, tn.TN_FP32) ["knobs"] == 14
         with pytest.raises(tn.TNError):
-            tn.tn_autotune_set(8, 8, 2, tn.TN_FP32, tn.TN_WORK_ENERGY, 16)
+            tn.tn_autotune_set(8, 8, 2, tn.TN_FP32, tn.TN_WORK_ENERGY, 32)
         with pytest.raises(tn.TNError) as e:
             tn.tn_autotune(cpu_ctx, [4], [4], [2], tn.TN_FP32)
         assert e.value.status == tn.TN_ERR_NO_DEVICE

@@ -11,9 +11,11 @@ from paper_1908_08553_gb300 import inputs, tn
 pytestmark = pytest.mark.gpu
 
 TOL_OBS = {tn.TN_FP64: 1e-10, tn.TN_FP32: 1e-6, tn.TN_BF16X6: 1e-6, tn.TN_BF16X3: 1e-5}
-# knob combinations that change each shape's program (bits: 1 pairs, 2 triple dot, 4 D=3 factors, 8 tensor cores)
+# knob combinations that change each shape's program (bits: 1 pairs, 2 triple dot, 4 D=3 factors,
+# 8 tensor-core products of >= 2^26 multiply-adds, 16 smaller ones too)
 CASES = [((6, 6, 2), tn.TN_FP32, [15, 14, 13, 12]), ((4, 4, 3), tn.TN_FP32, [15, 11]),
-         ((4, 4, 3), tn.TN_FP64, [15, 11]), ((6, 6, 2), tn.TN_BF16X6, [15, 7, 6])]
+         ((4, 4, 3), tn.TN_FP64, [15, 11]), ((8, 8, 2), tn.TN_BF16X6, [15, 31, 30, 29]),
+         ((5, 5, 3), tn.TN_BF16X6, [15, 11, 7, 3]), ((5, 5, 3), tn.TN_BF16X3, [15, 11])]
 
 
 @pytest.fixture(scope="module")

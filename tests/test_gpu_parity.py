@@ -253,22 +253,30 @@ def test_tn_absorb_dot_matches_reference(K, N, P, S, dtype):
 
 @pytest.mark.parametrize("prec", [tn.TN_BF16X3, tn.TN_BF16X6])
 def test_c2_8x8_d2_tensor_core_precisions(ctx, prec):
-    """256-wide ring products on tcgen05 (split BF16, FP32 accumulation)."""
+    """256-wide ring products on tcgen05 (split BF16, FP32 accumulation).  By
+    default products this small run on FP32 SIMT (the same bits as FP32);
+    program choice 31 puts them on the tensor cores."""
     L, W, D = 8, 8, 2
     A = inputs.random_lattice(L, W, D, 88)
     ref = oracle.observables(L, W, D, A)
-    lat = tn.tn_create_lattice(ctx, L, W, D)
+    r32, _, _ = _energy(ctx, L, W, D, A, tn.TN_FP32, tn.TN_SCHED_AUTO)
+    r16, _, _ = _energy(ctx, L, W, D, A, prec, tn.TN_SCHED_AUTO)
+    assert r32.energy == r16.energy
+    tn.tn_autotune_set(L, W, D, prec, tn.TN_WORK_ENERGY, 31)
     try:
-        tn.tn_set_site_tensors(lat, A)
-        for h in (2.0, 3.04, 4.0):
-            r, sx, zz = tn.tn_energy(lat, 1.0, h, prec, tn.TN_SCHED_AUTO, L, W)
-            _check(r, sx, zz, ref, prec, 1.0, h)
-        # the tensor-core result is not the FP32 SIMT result bit for bit
-        r32, _, _ = tn.tn_energy(lat, 1.0, 3.04, tn.TN_FP32, tn.TN_SCHED_AUTO, L, W)
-        r16, _, _ = tn.tn_energy(lat, 1.0, 3.04, prec, tn.TN_SCHED_AUTO, L, W)
-        assert r32.energy != r16.energy
+        lat = tn.tn_create_lattice(ctx, L, W, D)
+        try:
+            tn.tn_set_site_tensors(lat, A)
+            for h in (2.0, 3.04, 4.0):
+                r, sx, zz = tn.tn_energy(lat, 1.0, h, prec, tn.TN_SCHED_AUTO, L, W)
+                _check(r, sx, zz, ref, prec, 1.0, h)
+            # the tensor-core result is not the FP32 SIMT result bit for bit
+            rt, _, _ = tn.tn_energy(lat, 1.0, 3.04, prec, tn.TN_SCHED_AUTO, L, W)
+            assert r32.energy != rt.energy
+        finally:
+            tn.tn_destroy_lattice(lat)
     finally:
-        tn.tn_destroy_lattice(lat)
+        tn.tn_autotune_clear()
 
 
 def test_tensor_core_d3_5x5(ctx):

@@ -124,7 +124,7 @@ def test_served_wait_timeout_reaches_the_caller():
     torch.cuda.init()
     ctx = tn.tn_ctx_create(0, 0)
     try:
-        L, W, D = 5, 5, 3          # D = 3 interior steps: tensor-core absorption in BF16x3
+        L, W, D = 5, 5, 3          # 729-wide ring products on the tensor cores in BF16x3
         A = inputs.random_lattice(L, W, D, 77)
         tn.tn_ctx_inject_wait_timeout(ctx, 1)
         t = tn.tn_submit(ctx, L, W, D, tn.TN_BF16X3, 1.0, 3.04, tensors=A)
