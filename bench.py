@@ -486,8 +486,7 @@ def run_headline(args):
         line["roofline_absorb_stream"] = absorb_stream_roofline(ctx, stream, hbm, src)
         line["batch_8x8_d2"] = batch_8x8(tn, torch, ctx, stream, args.batch)
         if args.serve_requests > 0:
-            line["serving"] = serve_stream(args.serve_requests, args.calibrate, "bf16x6", seq_sample=3,
-                                           seq_seconds=30.0)
+            line["serving"] = serve_stream(args.serve_requests, args.calibrate, "bf16x6", seq_seconds=20.0)
         line["cpu_baseline"] = cpu_baseline(seeds)
     tn.tn_batch_destroy(b)
     tn.tn_ctx_destroy(ctx)
@@ -604,11 +603,11 @@ def batch_8x8(tn, torch, ctx, stream, B: int):
 
 # ------------------------------------------------------------------ serving --
 
-def serve_stream(n: int, calibrate: int, precision: str, seq_sample: int, seq_seconds: float) -> dict:
+def serve_stream(n: int, calibrate: int, precision: str, seq_seconds: float) -> dict:
     """Serving: a Poisson stream of requests (L, W ~ U{4..12}, D ~ U{2,3},
     h ~ U[0.5, 5], seeded tensors) at 80% of the measured capacity, admitted by
     exact footprint against a 160 GB budget; p50/p99 latency and throughput,
-    beside sequential FP64 solves of a sample of the same requests."""
+    beside sequential FP64 solves of the same requests (the lighter ones)."""
     import threading
 
     import numpy as np
@@ -640,7 +639,7 @@ def serve_stream(n: int, calibrate: int, precision: str, seq_sample: int, seq_se
     rate = 0.8 * cap
 
     # Poisson stream with a polling collector
-    pending, done, lock, shapes_of = {}, {}, threading.Lock(), {}
+    pending, done, lock, shapes_of, ticket_of = {}, {}, threading.Lock(), {}, {}
     stop = threading.Event()
     deadline = time.perf_counter() + 900.0
 
@@ -676,6 +675,7 @@ def serve_stream(n: int, calibrate: int, precision: str, seq_sample: int, seq_se
         with lock:
             pending[t] = (L, W, time.perf_counter())
             shapes_of[t] = (L, W, D)
+        ticket_of[(L, W, D, h, sd)] = t
     stop.set()
     th.join()
     t_end = max(v[1] for v in done.values())
@@ -683,28 +683,43 @@ def serve_stream(n: int, calibrate: int, precision: str, seq_sample: int, seq_se
     lat_d = {d: np.array([v[1] - v[0] for t, v in done.items() if shapes_of[t][2] == d]) for d in (2, 3)}
     served = len(done)
 
-    # sequential plain FP64 solves of a sample of the admitted requests (those
-    # whose FP64 footprint also fits the budget)
+    # sequential plain FP64 solves of the served requests in stream order, one
+    # at a time, skipping those whose FP64 products exceed 5e12 multiply-adds
+    # (minutes each at the GB300's FP64 rate), until seq_seconds have passed;
+    # compared with the served latencies of the same requests
     probe2 = tn.tn_ctx_create(-1)
 
-    def fits64(L, W, D):
+    def fp64_macs(L, W, D):
         lat_ = tn.tn_create_lattice(probe2, L, W, D)
-        ok = tn.tn_footprint(lat_, tn.TN_SCHED_AUTO, tn.TN_FP64, tn.TN_WORK_ENERGY) <= budget
+        info = tn.tn_program_info(lat_, tn.TN_FP64)
         tn.tn_destroy_lattice(lat_)
-        return ok
+        return info["product_macs"], info["footprint_bytes"]
 
-    sample = [r for r, f in stream_reqs if f and fits64(*r[:3])][:seq_sample]
+    seq_times, seq_tickets, skipped = [], [], 0
     t0 = time.perf_counter()
-    n_seq = 0
-    for (L, W, D, h, sd) in sample:
+    for r, f in stream_reqs:
+        t = ticket_of.get(r)
+        if not f or t is None or t not in done:
+            continue
+        L, W, D, h, sd = r
+        macs, fp64_bytes = fp64_macs(L, W, D)
+        if macs > 5e12 or fp64_bytes > budget:
+            skipped += 1
+            continue
         l_ = tn.tn_create_lattice(ctx, L, W, D)
         tn.tn_fill_random(l_, sd)
+        torch.cuda.synchronize()
+        ts_ = time.perf_counter()
         tn.tn_energy(l_, 1.0, h, tn.TN_FP64, tn.TN_SCHED_AUTO, L, W)
+        seq_times.append(time.perf_counter() - ts_)
         tn.tn_destroy_lattice(l_)
-        n_seq += 1
+        seq_tickets.append(t)
         if time.perf_counter() - t0 > seq_seconds:
             break
-    seq_rate = n_seq / (time.perf_counter() - t0)
+    seq_times = np.array(seq_times)
+    same = np.array([done[t][1] - done[t][0] for t in seq_tickets])
+    n_seq = int(seq_times.size)
+    seq_rate = n_seq / seq_times.sum() if n_seq else None
     tn.tn_ctx_destroy(probe)
     tn.tn_ctx_destroy(probe2)
     tn.tn_ctx_destroy(ctx)
@@ -720,14 +735,21 @@ def serve_stream(n: int, calibrate: int, precision: str, seq_sample: int, seq_se
                      for d, v in lat_d.items()},
             "calibration": {"requests": len(calib), "what": "a burst of admissible requests from the same "
                             "distribution, submitted at once; capacity = requests / wall time"},
-            "sequential_fp64": {"energies_per_s": seq_rate, "sample": n_seq},
+            "sequential_fp64": {"energies_per_s": seq_rate, "requests": n_seq, "skipped_heavy": skipped,
+                                "p50_solve_s": float(np.percentile(seq_times, 50)) if n_seq else None,
+                                "p99_solve_s": float(np.percentile(seq_times, 99)) if n_seq else None,
+                                "served_p50_latency_s_same_requests": float(np.percentile(same, 50)) if n_seq else None,
+                                "served_p99_latency_s_same_requests": float(np.percentile(same, 99)) if n_seq else None,
+                                "what": "the served requests in stream order, one FP64 energy at a time (those "
+                                        "with more than 5e12 FP64 product multiply-adds skipped), until the time "
+                                        "cap; beside the served latencies of the same requests"},
             "distribution": "L, W ~ U{4..12}, D ~ U{2,3}, h ~ U[0.5,5], seeded uniform[-1,1) tensors"}
 
 
 def run_serve(args):
     import torch
     torch.cuda.set_device(0)
-    line = serve_stream(args.requests, args.calibrate, args.precision or "bf16x6", args.seq_sample, args.seq_seconds)
+    line = serve_stream(args.requests, args.calibrate, args.precision or "bf16x6", args.seq_seconds)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -992,7 +1014,6 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="batch: keep the default program choices")
     ap.add_argument("--requests", type=int, default=300, help="serve: requests in the stream")
     ap.add_argument("--calibrate", type=int, default=24, help="serve: burst size for the capacity")
-    ap.add_argument("--seq-sample", type=int, default=30, help="serve: sequential FP64 sample")
     ap.add_argument("--seq-seconds", type=float, default=60.0, help="serve: time cap of the FP64 sample")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -33,8 +33,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(ROOT, "include", "tn.h"),
-                                                               os.path.abspath(__file__)]
+    return (_sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+            [os.path.join(ROOT, "include", "tn.h"), os.path.abspath(__file__)])
 
 
 def up_to_date() -> bool:

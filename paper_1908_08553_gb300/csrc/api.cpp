@@ -186,6 +186,9 @@ tn_status tn_ctx_create(int device, size_t budget, void* stream, tn_ctx** out) {
         }
         cudaError_t e = cudaSetDevice(device);
         if (e != cudaSuccess) return cuda_status(e, "cudaSetDevice");
+        // every kernel loaded now, not on its first launch (which may
+        // synchronise the context while other streams are busy)
+        preload_kernels(device);
         size_t fr = 0, tot = 0;
         e = cudaMemGetInfo(&fr, &tot);
         if (e != cudaSuccess) return cuda_status(e, "cudaMemGetInfo");

@@ -303,6 +303,9 @@ __global__ void __launch_bounds__(kBmpsThreads) k_bmps(const BmpsTask* __restric
     }
 }
 
+// One kernel of this translation unit, for loading its module up front (preload.cpp).
+const void* bmps_module_anchor() { return reinterpret_cast<const void*>(&k_bmps); }
+
 cudaError_t launch_bmps(const BmpsTask* tasks, int ntasks, cudaStream_t st) {
     if (ntasks <= 0) return cudaSuccess;
     k_bmps<<<ntasks, kBmpsThreads, 0, st>>>(tasks);

@@ -185,6 +185,9 @@ k_ite_bond(double* __restrict__ A, const IteBondTask* __restrict__ tasks, int nt
     }
 }
 
+// One kernel of this translation unit, for loading its module up front (preload.cpp).
+const void* ite_module_anchor() { return reinterpret_cast<const void*>(&k_ite_scale); }
+
 cudaError_t launch_ite_one_body(double* A, const long long* site_off, int nsites, const double g[4],
                                 cudaStream_t st) {
     if (nsites <= 0) return cudaSuccess;

@@ -1921,6 +1921,9 @@ __global__ void k_final(const FinalTask* __restrict__ tasks, const Slot* __restr
     }
 }
 
+// One kernel of this translation unit, for loading its module up front (preload.cpp).
+const void* kernels_module_anchor() { return reinterpret_cast<const void*>(&k_final); }
+
 cudaError_t launch_final(const FinalTask* tasks, int ntasks, const Slot* slots, cudaStream_t st) {
     if (ntasks <= 0) return cudaSuccess;
     TN_LAUNCH(k_final, dim3(ntasks), dim3(128), 0, st, tasks, slots);

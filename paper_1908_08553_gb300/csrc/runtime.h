@@ -117,5 +117,6 @@ std::shared_ptr<const Program> program_cached(int L, int W, int D, tn_schedule s
 tn_status batch_run(tn_batch* b, cudaStream_t st);
 void batch_destroy(tn_batch* b);
 tn_status cuda_status(cudaError_t e, const char* what);
+void preload_kernels(int device);
 void server_stop(tn_ctx* ctx);
 }  // namespace tn

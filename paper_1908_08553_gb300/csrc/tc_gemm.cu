@@ -807,6 +807,9 @@ cudaError_t launch_tc_absorb(int nsplit, bool dot, const AbsorbTask* tasks, int 
 
 long long tc_split_tiles(long long Rp, long long Kp) { return (Rp * (Kp / 8) + 255) / 256; }
 
+// One kernel of this translation unit, for loading its module up front (preload.cpp).
+const void* tc_module_anchor() { return reinterpret_cast<const void*>(&k_tc_split); }
+
 cudaError_t launch_tc_split(const TcSplitTask* tasks, int ntasks, long long nblocks, const Slot* slots,
                             cudaStream_t st) {
     if (nblocks <= 0) return cudaSuccess;
