@@ -272,6 +272,22 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
     const long long tile = blockIdx.x;
     const AbsorbTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
     const long long local = tile - t.tile0;
+    const long long S = t.S;
+    const long long ngroups = ALONG_P ? t.P / 4 : t.P * (S / 4);
+    const long long g = local * kV2Threads + threadIdx.x;
+    // along s: this thread's K input loads go out first -- they depend on
+    // neither the site matrix nor the scales, so their latency overlaps the
+    // loads of the prologue below instead of following it
+    float4 raw[ALONG_P ? 1 : K];
+    long long p4 = 0, s4 = 0;
+    if (!ALONG_P && g < ngroups) {
+        const long long sq = S / 4;
+        p4 = g / sq;
+        s4 = (g - p4 * sq) * 4;
+        const float* in = static_cast<const float*>(t.in);
+#pragma unroll
+        for (int k = 0; k < K; ++k) raw[k] = __ldg(reinterpret_cast<const float4*>(in + (p4 * K + k) * S + s4));
+    }
     const float* E = static_cast<const float*>(t.E);
     for (int idx = threadIdx.x; idx < K * N; idx += blockDim.x) {
         const int k = idx / N, n = idx - k * N;
@@ -297,21 +313,16 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
         sc_adj = pow2<float>(-e_adj);
     }
     __syncthreads();
-    const long long S = t.S;
-    const long long ngroups = ALONG_P ? t.P / 4 : t.P * (S / 4);
-    const long long g = local * kV2Threads + threadIdx.x;
     float lmax = 0.0f;
     double ldot = 0.0, ldot2 = 0.0, ldot3 = 0.0;
     if (g < ngroups && !ALONG_P) {
         // ---- 4 consecutive s of one p, two-lane FMAs over position pairs
-        const long long sq = S / 4, p = g / sq, s = (g - p * sq) * 4;
-        const float* in = static_cast<const float*>(t.in);
+        const long long p = p4, s = s4;
         unsigned long long xv[K][2];     // (x_0, x_1), (x_2, x_3) per k, rescaled
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(in + (p * K + k) * S + s));
-            xv[k][0] = f2_pack(v.x * sc_in, v.y * sc_in);
-            xv[k][1] = f2_pack(v.z * sc_in, v.w * sc_in);
+            xv[k][0] = f2_pack(raw[k].x * sc_in, raw[k].y * sc_in);
+            xv[k][1] = f2_pack(raw[k].z * sc_in, raw[k].w * sc_in);
         }
         if (MODE >= 4) {
             // dual / triple dot: 4 outputs n at a time for every site matrix
@@ -822,6 +833,18 @@ k_absorb2(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
     const long long tile = blockIdx.x;
     const AbsorbTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
     const long long local = tile - t.tile0;
+    const long long S2 = t.S;
+    const long long pos = local * kA2Threads + threadIdx.x;
+    // this thread's inputs go out first, overlapping the prologue's loads
+    float x[K1][U];
+    if (pos < t.P * S2) {
+        const long long p = pos / S2, s2 = pos - p * S2;
+        const float* in = static_cast<const float*>(t.in) + p * K1 * U * S2 + s2;
+#pragma unroll
+        for (int k = 0; k < K1; ++k)
+#pragma unroll
+            for (int u = 0; u < U; ++u) x[k][u] = __ldg(in + (k * U + u) * S2);
+    }
     for (int i = threadIdx.x; i < K1 * DN * H; i += blockDim.x) {
         const float e = static_cast<const float*>(t.E)[i];
         E1s[i] = e;
@@ -837,18 +860,14 @@ k_absorb2(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
         sc_adj = pow2<float>(-e_adj);
     }
     __syncthreads();
-    const long long S2 = t.S;
-    const long long pos = local * kA2Threads + threadIdx.x;
     float lmax = 0.0f;
     CSum<float> acc;
     if (pos < t.P * S2) {
         const long long p = pos / S2, s2 = pos - p * S2;
-        const float* in = static_cast<const float*>(t.in) + p * K1 * U * S2 + s2;
-        float x[K1][U];
 #pragma unroll
         for (int k = 0; k < K1; ++k)
 #pragma unroll
-            for (int u = 0; u < U; ++u) x[k][u] = __ldg(in + (k * U + u) * S2) * sc_in;
+            for (int u = 0; u < U; ++u) x[k][u] *= sc_in;
         if (PAIRED) {
             // the same contraction order with two lanes per FMA: step 1 pairs
             // adjacent u (E1 entries duplicated in shared memory), step 2 pairs
