@@ -258,7 +258,7 @@ k_absorb_one(const __grid_constant__ AbsorbTask t) {
 constexpr int kV2Threads = 128;
 
 template <int K, int N, int MODE, bool ALONG_P>
-__global__ void __launch_bounds__(kV2Threads, MODE >= 4 ? 3 : 4)
+__global__ void __launch_bounds__(kV2Threads, MODE >= 4 ? 4 : 5)
 k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
     pdl_enter();
     constexpr int NE = MODE == 5 ? 3 : (MODE == 4 ? 2 : 1);     // site matrices
@@ -376,7 +376,7 @@ k_absorb4(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ s
             if (NE >= 2) ldot2 = (double)acc[NE >= 2 ? 1 : 0].value();
             if (NE == 3) ldot3 = (double)acc[NE - 1].value();
         } else {
-            constexpr int NC = N >= 8 ? 8 : N;      // output columns per pass
+            constexpr int NC = N >= 4 ? 4 : N;      // output columns per pass
             CSum<float> acc;
 #pragma unroll
             for (int h = 0; h < N / NC; ++h) {
@@ -821,7 +821,7 @@ cudaError_t launch_2pass_t(const AbsorbTask* tasks, int ntasks, long long nblock
 constexpr int kA2Threads = 128;
 
 template <int K1, int N2, int MODE>
-__global__ void __launch_bounds__(kA2Threads, MODE == 2 ? 3 : 4)
+__global__ void __launch_bounds__(kA2Threads, MODE == 2 ? 4 : 5)
 k_absorb2(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots, const int* __restrict__ tmap) {
     pdl_enter();
     constexpr int DN = 4, H = 4, U = 4;
