@@ -849,10 +849,11 @@ def run_8x8(args):
 
 
 def run_batch(args):
-    """512 independent lattices, L, W ~ U{4..10}, D ~ U{2,3}, h ~ U[0.5,5]: as few
-    graph-captured batches as the HBM budget allows (members run together,
-    every wave of all members one grouped launch); members whose footprint
-    alone exceeds the budget are reported, not run."""
+    """512 independent lattices, L, W ~ U{4..10}, D ~ U{2,3}, h ~ U[0.5,5], in one
+    batch group: passes of at most the pass budget (members of a pass run
+    together, every wave of all members one grouped launch) sharing one arena,
+    all captured into one CUDA graph, so a run is one graph launch; members
+    whose footprint alone exceeds the budget are reported, not run."""
     import numpy as np
     import torch
 
@@ -860,7 +861,7 @@ def run_batch(args):
 
     torch.cuda.set_device(0)
     prec = tn.PRECISIONS[args.precision or "fp32"]
-    budget = int(200e9)
+    budget = int(225e9)              # per pass; the passes share one arena
     rng = np.random.default_rng(2)
     n = args.members
     Ls = rng.integers(4, 11, size=n)
@@ -876,18 +877,8 @@ def run_batch(args):
     tn.tn_ctx_destroy(probe)
     ok = [k for k in range(n) if fp[k] <= budget]
     excluded = [k for k in range(n) if fp[k] > budget]
-    # pack members in order into sub-batches of at most the budget
-    groups, cur, used = [], [], 0
-    for k in ok:
-        if cur and used + fp[k] > budget:
-            groups.append(cur)
-            cur, used = [], 0
-        cur.append(k)
-        used += fp[k]
-    if cur:
-        groups.append(cur)
     stream = torch.cuda.Stream()
-    ctx = tn.tn_ctx_create(0, int(250e9), stream)
+    ctx = tn.tn_ctx_create(0, 0, stream)          # budget: 90% of the free device memory
     # autotune every (L, W, D) bucket whose copies fit the tuning budget (the
     # largest D = 3 shapes keep the default choices); every batch built after
     # this takes its programs from the table
@@ -907,34 +898,32 @@ def run_batch(args):
                              "best_ms": r["best_ms"], "default_ms": r["default_ms"]} for s, r in changed[:12]],
                 "what": "per (L, W, D): every applicable program choice timed on copies of the shape "
                         "(at most 4 GB); the fastest by >= 2% kept; shapes above 4 GB keep the defaults"}
-    total_ms, results, launches = 0.0, {}, 0
-    for g in groups:
-        b = tn.tn_batch_create(ctx, Ls[g], Ws[g], Ds[g], prec)
-        tn.tn_batch_fill_random(b, args.batch_seed)      # member seeds from the batch seed
-        hh = hs[g].copy()
-        tn.tn_batch_run(b, 1.0, hh)                      # capture + first run
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        tn.tn_batch_run(b, 1.0, hh)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        launches += tn.tn_batch_launch_count(b)
-        r = tn.tn_batch_results_host(b)
-        off = 0
-        for k in g:
-            L, W = int(Ls[k]), int(Ws[k])
-            nres = 6 + 2 * L * W + L * (W - 1) + W * (L - 1)
-            results[k] = r[off:off + nres]
-            off += nres
-        tn.tn_batch_destroy(b)
+    # every admissible member in one batch group: passes of at most the budget
+    # sharing one arena, all captured into one CUDA graph
+    okk = np.array(ok)
+    g = tn.tn_batch_group_create(ctx, Ls[okk], Ws[okk], Ds[okk], prec, budget)
+    info = tn.tn_batch_group_info(g)
+    tn.tn_batch_group_fill_random(g, args.batch_seed)      # member seeds from the batch seed
+    hh = hs[okk].copy()
+    # one timed run (minutes of device work: the graph and every kernel are
+    # already loaded, so there is nothing to warm up)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tn.tn_batch_group_run(g, 1.0, hh)                      # one graph launch
+    e1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    r = tn.tn_batch_group_results_host(g)
+    assert np.all(np.isfinite(r))
+    tn.tn_batch_group_destroy(g)
     tn.tn_ctx_destroy(ctx)
     m = len(ok)
     line = {"metric": "batched exact TFIM-PEPS energy evals/s", "workload": "512 mixed lattices, L, W in 4..10, D in {2,3}",
             "precision": args.precision or "fp32", "members": n, "evaluated": m, "excluded_over_budget": len(excluded),
             "excluded_shapes": sorted({(int(Ls[k]), int(Ws[k]), int(Ds[k])) for k in excluded}),
-            "graphs": len(groups), "kernel_launches": launches, "ms": total_ms, "autotune": tune,
+            "graph_launches": 1, "passes": info["passes"], "kernel_launches": info["launches"],
+            "shared_arena_gb": info["arena_bytes"] / 1e9, "ms": total_ms, "autotune": tune,
             "evals_per_s": m / (total_ms / 1e3), "energies_per_s": m / (total_ms / 1e3),
             "budget_gb": budget / 1e9,
             "distribution": "L, W ~ U{4..10}, D ~ U{2,3}, h ~ U[0.5,5], seeded uniform[-1,1) tensors"}

@@ -113,6 +113,7 @@ typedef struct {
 typedef struct tn_ctx tn_ctx;
 typedef struct tn_lattice tn_lattice;
 typedef struct tn_batch tn_batch;
+typedef struct tn_batch_group tn_batch_group;
 
 /* ----------------------------------------------------------- context ---- */
 
@@ -259,6 +260,31 @@ tn_status tn_batch_results_host(tn_batch *b, double *host, size_t cap);
 tn_status tn_batch_results_device(tn_batch *b, const double **dev);
 /* Number of kernel launches one tn_batch_run issues. */
 tn_status tn_batch_launch_count(const tn_batch *b, int64_t *n);
+
+/* Batch groups (no counterpart in the paper; the batched form of the
+ * spec workload): n lattices whose summed footprint may exceed the
+ * device.  Members are split, in order, into passes of at most pass_budget
+ * bytes each; the passes run one after another and share one arena (the
+ * largest pass's), each keeping its small regions (inputs, slots, results,
+ * tables); the launches of all passes are captured into ONE CUDA graph, so a
+ * run of the whole group is one graph launch.  TN_ERR_OVER_BUDGET when a
+ * member alone exceeds pass_budget or the arena the remaining budget;
+ * TN_ERR_NO_DEVICE without a device.  Inputs and results are concatenated in
+ * member order with the layouts of tn_batch_*; member k of the generator
+ * takes the seed member k of one batch would. */
+tn_status tn_batch_group_create(tn_ctx *ctx, int n, const int *L, const int *W, const int *D,
+                                tn_precision prec, tn_schedule sched, tn_work work, size_t pass_budget,
+                                tn_batch_group **out);
+tn_status tn_batch_group_destroy(tn_batch_group *g);
+/* Passes, shared arena bytes, total input entries, total result doubles and
+ * kernel launches per run (any pointer may be NULL). */
+tn_status tn_batch_group_info(const tn_batch_group *g, int *passes, size_t *arena_bytes, size_t *n_elems,
+                              size_t *n_results, int64_t *launches);
+tn_status tn_batch_group_set_tensors(tn_batch_group *g, const double *host, size_t n_elems);
+tn_status tn_batch_group_fill_random(tn_batch_group *g, uint64_t batch_seed);
+/* One graph launch for every member (asynchronous on the ctx stream). */
+tn_status tn_batch_group_run(tn_batch_group *g, double J, const double *h);
+tn_status tn_batch_group_results_host(tn_batch_group *g, double *host, size_t cap);
 
 /* ------------------------------------------------------------- serving --- */
 

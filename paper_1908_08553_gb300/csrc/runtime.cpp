@@ -103,8 +103,9 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
     }
     // --- device pointers of the fixed regions
     lay.in_off = 0;
+    b->arena_bytes = arena;
     lay.arena_off = up(lay.in_off + (size_t)nin * 8);
-    lay.slots_off = up(lay.arena_off + arena);
+    lay.slots_off = b->arena_external ? lay.arena_off : up(lay.arena_off + arena);
     auto ptr = [&](size_t off) -> char* { return base ? base + off : nullptr; };
     Slot* slots_base = reinterpret_cast<Slot*>(ptr(lay.slots_off));
     (void)slots_base;
@@ -117,7 +118,8 @@ void materialize(tn_batch* b, char* base, std::vector<char>* tasks_out, std::vec
         const Member& mb = b->m[mi];
         const Tensor& t = mb.pg->tensors[tid];
         if (!base) return nullptr;
-        return base + lay.arena_off + mb.arena_off + t.offset;
+        char* arena_base = b->arena_external ? b->ext_arena : base + lay.arena_off;
+        return arena_base + mb.arena_off + t.offset;
     };
     auto slot_of = [&](int mi, int tid) -> int {
         return (int)(b->m[mi].slot_base + b->m[mi].pg->tensors[tid].slot);
@@ -481,7 +483,13 @@ tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int
         mb.L = L[k]; mb.W = W[k]; mb.D = D[k];
         b->m.push_back(mb);
     }
+    b->arena_external = opts->arena_external;
     materialize(b.get(), nullptr, nullptr, nullptr, nullptr);
+    if (alloc && b->arena_external && (!opts->ext_arena || opts->ext_arena_bytes < b->arena_bytes)) {
+        set_error("the shared arena is smaller than the batch's tensors");
+        return TN_ERR_INVALID;
+    }
+    b->ext_arena = opts->ext_arena;
     if (bytes) *bytes = b->lay.total;
     if (!alloc) { *out = b.release(); return TN_OK; }
     if (!ctx || ctx->device < 0) { set_error("context has no device"); return TN_ERR_NO_DEVICE; }
@@ -668,5 +676,7 @@ tn_status batch_run_plain(tn_batch* b, cudaStream_t st) {
     }
     return cuda_status(cudaGraphLaunch(b->gexec, st), "graph launch");
 }
+
+cudaError_t batch_issue(tn_batch* b, cudaStream_t st) { return issue(b, st, nullptr); }
 
 }  // namespace tn

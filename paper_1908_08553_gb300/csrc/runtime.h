@@ -90,6 +90,9 @@ struct tn_batch {
     std::vector<char> h_tasks;        // host copies of the uploaded tables
     std::vector<int> h_ints;
     std::vector<tn::ConstOne> h_ones;
+    bool arena_external = false;      // the arena lives outside buf (shared by the passes of a group)
+    char* ext_arena = nullptr;
+    size_t arena_bytes = 0;           // the members' arena, wherever it lives
 };
 
 struct tn_lattice {
@@ -108,6 +111,9 @@ struct BatchOpts {
     int knobs = -1;                  // program knobs (Knobs::code); -1: the tuning table's choice
     std::shared_ptr<const Program> program;   // every member runs this program (its shape must match)
     bool complex_sites = false;      // complex site tensors (every member)
+    bool arena_external = false;     // no arena in the batch buffer: the tensors live in ext_arena
+    char* ext_arena = nullptr;       // (null when only sizes are computed)
+    size_t ext_arena_bytes = 0;
 };
 tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int* D,
                        tn_precision prec, tn_schedule sched, tn_work work, bool alloc,
@@ -115,6 +121,8 @@ tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int
 std::shared_ptr<const Program> program_cached(int L, int W, int D, tn_schedule sched, tn_precision prec,
                                               tn_work work, int knobs_code = -1, bool cplx = false);
 tn_status batch_run(tn_batch* b, cudaStream_t st);
+// The kernel launches of one run (no table upload): what a graph captures.
+cudaError_t batch_issue(tn_batch* b, cudaStream_t st);
 void batch_destroy(tn_batch* b);
 tn_status cuda_status(cudaError_t e, const char* what);
 void preload_kernels(int device);

@@ -95,6 +95,14 @@ SIGNATURES = {
     "tn_ite_init_product": (c_int, [c_void_p]),
     "tn_pair_correlators": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "tn_set_site_tensors_complex": (c_int, [c_void_p, c_void_p, c_void_p, c_size_t]),
+    "tn_batch_group_create": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_size_t,
+                                      POINTER(c_void_p)]),
+    "tn_batch_group_destroy": (c_int, [c_void_p]),
+    "tn_batch_group_info": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "tn_batch_group_set_tensors": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "tn_batch_group_fill_random": (c_int, [c_void_p, c_uint64]),
+    "tn_batch_group_run": (c_int, [c_void_p, c_double, c_void_p]),
+    "tn_batch_group_results_host": (c_int, [c_void_p, c_void_p, c_size_t]),
     "tn_lattice_is_complex": (c_int, [c_void_p]),
     "tn_site_expectations": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "tn_autotune": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_size_t]),
@@ -406,6 +414,48 @@ def tn_absorb_dot_noalloc(dtype: int, x_in, E, adj, P: int, K: int, N: int, S: i
 
 def tn_ctx_set_profiling(ctx, on: bool):
     check(lib().tn_ctx_set_profiling(ctx, 1 if on else 0), "tn_ctx_set_profiling")
+
+
+def tn_batch_group_create(ctx, Ls, Ws, Ds, prec: int, pass_budget: int, sched: int = TN_SCHED_AUTO,
+                          work: int = TN_WORK_ENERGY):
+    """Lattices of any number and sizes, split into passes of at most pass_budget
+    bytes sharing one arena, run as one CUDA graph."""
+    Ls, Ws, Ds = (np.ascontiguousarray(v, dtype=np.int32) for v in (Ls, Ws, Ds))
+    g = c_void_p()
+    check(lib().tn_batch_group_create(ctx, Ls.size, _ptr(Ls), _ptr(Ws), _ptr(Ds), prec, sched, work,
+                                      c_size_t(int(pass_budget)), byref(g)), "tn_batch_group_create")
+    return g
+
+
+def tn_batch_group_destroy(g):
+    check(lib().tn_batch_group_destroy(g), "tn_batch_group_destroy")
+
+
+def tn_batch_group_info(g) -> dict:
+    p, a, ne, nr, nl = c_int(), c_size_t(), c_size_t(), c_size_t(), c_int64()
+    check(lib().tn_batch_group_info(g, byref(p), byref(a), byref(ne), byref(nr), byref(nl)), "tn_batch_group_info")
+    return {"passes": p.value, "arena_bytes": a.value, "n_elems": ne.value, "n_results": nr.value,
+            "launches": nl.value}
+
+
+def tn_batch_group_set_tensors(g, A):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    check(lib().tn_batch_group_set_tensors(g, _ptr(A), A.size), "tn_batch_group_set_tensors")
+
+
+def tn_batch_group_fill_random(g, seed: int):
+    check(lib().tn_batch_group_fill_random(g, c_uint64(seed)), "tn_batch_group_fill_random")
+
+
+def tn_batch_group_run(g, J: float, hs):
+    hs = np.ascontiguousarray(hs, dtype=np.float64)
+    check(lib().tn_batch_group_run(g, J, _ptr(hs)), "tn_batch_group_run")
+
+
+def tn_batch_group_results_host(g) -> np.ndarray:
+    out = np.zeros(tn_batch_group_info(g)["n_results"])
+    check(lib().tn_batch_group_results_host(g, _ptr(out), out.size), "tn_batch_group_results_host")
+    return out
 
 
 def tn_set_site_tensors_complex(lat, A) -> None:

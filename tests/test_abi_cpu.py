@@ -325,3 +325,15 @@ def test_complex_lattice_on_the_host(cpu_ctx):
         assert tn.tn_get_site_tensors(lat, n).size == n
     finally:
         tn.tn_destroy_lattice(lat)
+
+
+def test_batch_group_arguments(cpu_ctx):
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_batch_group_create(cpu_ctx, [4], [4], [2], tn.TN_FP32, 1 << 30)
+    assert e.value.status == tn.TN_ERR_NO_DEVICE
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_batch_group_create(cpu_ctx, [4], [4], [2], tn.TN_FP32, 0)
+    assert e.value.status == tn.TN_ERR_INVALID
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_batch_group_create(cpu_ctx, [], [], [], tn.TN_FP32, 1 << 30)
+    assert e.value.status == tn.TN_ERR_INVALID
