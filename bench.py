@@ -48,7 +48,7 @@ WORKLOAD_8X8 = "8x8 open-boundary TFIM PEPS, D=2, E at h in {2.0, 3.04, 4.0}"
 FAMILIES = ["absorb", "absorb_dot", "gemm_simt", "gemm_tc", "other", "absorb_pair"]
 # DRAM bytes per algorithmic byte of one interior k_absorb4<16,16,1,0> launch (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum, `bench.py --workload case --batch 64 --precision fp32`, 8x8 D=2 lattices)
-ABSORB_DRAM_PER_BYTE = 89.35 / 134.22
+ABSORB_DRAM_PER_BYTE = 86.88 / 134.22
 # DRAM bytes per multiply-add of one k_gemm3<1,0,1> launch (640 products of 256^3, the same capture command)
 GEMM_DRAM_PER_MAC = 373.1e6 / (640 * 256.0 ** 3)
 
