@@ -487,7 +487,9 @@ def run_headline(args):
         line["batch_8x8_d2"] = batch_8x8(tn, torch, ctx, stream, args.batch)
         if args.serve_requests > 0:
             line["serving"] = serve_stream(args.serve_requests, args.calibrate, "bf16x6", seq_seconds=20.0)
+        line["next_rows"] = next_rows(tn, torch, ctx)
         line["cpu_baseline"] = cpu_baseline(seeds)
+        line["cpu_baseline"]["next_rows_oracle"] = next_rows_oracle()
     tn.tn_batch_destroy(b)
     tn.tn_ctx_destroy(ctx)
     if rank == 0:
@@ -599,6 +601,138 @@ def batch_8x8(tn, torch, ctx, stream, B: int):
             entry["vs_fp64_gpu"] = worst([energy_errors(m, r, 1.0, hs[k]) for k, (m, r) in enumerate(zip(mem, ref))])
         out[name] = entry
     return out
+
+
+# ---------------------------------------------------------------- next rows --
+
+def next_rows(tn, torch, ctx) -> dict:
+    """The ranked next rows on the GPU: every pair correlator of an 8x8 D=2
+    lattice in one call, a complex 8x8 D=2 energy with every <Y_k>, the
+    boundary-MPS energy at chi_b = 16 against the exact one, and imaginary time
+    evolution of a 6x6 lattice.  Errors are against the FP64 GPU results (the
+    oracle parity of these paths is in the tests); the oracle's times on the
+    same jobs are in the CPU-baseline leg (next_rows_oracle)."""
+    import numpy as np
+
+    from paper_1908_08553_gb300 import inputs
+
+    def wall(f, reps=1):
+        f()                                  # warm-up (programs, caches)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = f()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps, r
+
+    out = {}
+    L, W, D = 8, 8, 2
+    N, nb = L * W, L * (W - 1) + W * (L - 1)
+    lat = tn.tn_create_lattice(ctx, L, W, D)
+    try:
+        # f2: all 2016 pairs <Z_i Z_j>, one program built and run per call
+        tn.tn_set_site_tensors(lat, inputs.random_lattice(L, W, D, 8801))
+        ij = np.array([(i, j) for i in range(N) for j in range(i + 1, N)], dtype=np.int32)
+        pairs, ref = {"pairs": int(ij.shape[0])}, None
+        for name in ("fp64", "fp32"):
+            prec = tn.PRECISIONS[name]
+            dt, v = wall(lambda: tn.tn_pair_correlators(lat, prec, tn.TN_OP_Z, tn.TN_OP_Z, ij[:, 0], ij[:, 1]))
+            pairs[name] = {"s_per_call": dt, "pairs_per_s": ij.shape[0] / dt}
+            if ref is None:
+                ref = v
+            else:
+                pairs[name]["max_abs_diff_vs_fp64"] = float(np.abs(v - ref).max())
+        out["f2_pairs_8x8_d2"] = pairs
+        # f2: complex PEPS energy with every <X>, <Y>, <Z>, <ZZ>
+        tn.tn_set_site_tensors_complex(lat, inputs.random_complex_lattice(L, W, D, 8802))
+        cplx, ref = {}, None
+        for name in ("fp64", "bf16x6"):
+            prec = tn.PRECISIONS[name]
+
+            def run():
+                r, sx, zz, sz, _ = tn.tn_energy_full(lat, 1.0, 3.04, prec, tn.TN_SCHED_AUTO, L, W)
+                sy = tn.tn_site_expectations(lat, prec, tn.TN_OP_Y, L, W)
+                return np.concatenate([sx, sy, sz, zz])
+            dt, v = wall(run)
+            cplx[name] = {"s_per_eval": dt, "evals_per_s": 1.0 / dt}
+            if ref is None:
+                ref = v
+            else:
+                cplx[name]["max_abs_diff_vs_fp64"] = float(np.abs(v - ref).max())
+        out["f2_complex_8x8_d2"] = cplx
+        # f3: boundary MPS at chi_b = 16 against the exact FP64 energy
+        tn.tn_set_site_tensors(lat, inputs.random_lattice(L, W, D, 8801))
+        exact = tn.tn_energy(lat, 1.0, 3.04, tn.TN_FP64)
+        bmps = {"networks": N + nb + 1}
+        for name in ("fp64", "fp32"):
+            dt, (r, _, _) = wall(lambda: tn.tn_bmps_energy(lat, 16, 1.0, 3.04, L, W, tn.PRECISIONS[name]))
+            bmps[name] = {"s_per_energy": dt,
+                          "rel_energy_err_vs_exact": abs(r.energy - exact.energy) / abs(exact.energy)}
+        out["f3_bmps_8x8_d2_chi16"] = bmps
+    finally:
+        tn.tn_destroy_lattice(lat)
+    # f4: ITE, 6x6, chi_max = 2, Gamma = 3.04, dtau = 0.05, 20 steps, energy every 10
+    Li, Wi, chi, steps = 6, 6, 2, 20
+    lat = tn.tn_create_lattice(ctx, Li, Wi, chi)
+    try:
+        def ite_run():
+            tn.tn_ite_init_product(lat)
+            return tn.tn_ite_run(lat, Li, Wi, 1.0, 3.04, 0.05, steps, chi, 1e-3, energy_every=10)
+        dt, (en, dims, disc) = wall(ite_run)
+    finally:
+        tn.tn_destroy_lattice(lat)
+    out["f4_ite_6x6_chi2"] = {"steps": steps, "s_per_step": dt / steps, "energy_per_site": float(en[-1]) / (Li * Wi)}
+    return out
+
+
+def next_rows_oracle() -> dict:
+    """The oracle, as it stands, on the next rows' jobs (CPU-baseline leg):
+    bounded samples scaled to each job, the sample stated."""
+    import oracle
+    import oracle.bmps as bm
+    import oracle.complex_peps as cp
+    import oracle.ite as ite
+    from paper_1908_08553_gb300 import inputs
+
+    L, W, D = 8, 8, 2
+    N, nb = L * W, L * (W - 1) + W * (L - 1)
+    A = inputs.random_lattice(L, W, D, 8801)
+    t0 = time.perf_counter()
+    for i, j in ((0, 63), (7, 56), (27, 36)):
+        oracle.pair(L, W, D, A, "z", i, "z", j)
+    per_pair = (time.perf_counter() - t0) / 3
+    Ac = inputs.random_complex_lattice(L, W, D, 8802)
+    t0 = time.perf_counter()
+    cp.value(L, W, D, Ac)
+    per_contraction = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bm.norm(L, W, D, A, 16)
+    per_network = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ite.evolve(6, 6, 1.0, 3.04, 0.05, 20, 2, 1e-3, energy_every=10)
+    ite_s = time.perf_counter() - t0
+    return {"f2_pairs_8x8_d2": {"pairs_per_s": 1.0 / per_pair, "sample": "3 pairs, one row sweep each"},
+            "f2_complex_8x8_d2": {"s_per_eval": per_contraction * (3 * N + nb + 1),
+                                  "sample": "one complex128 contraction x the 3N + nb + 1 contractions"},
+            "f3_bmps_8x8_d2_chi16": {"s_per_energy": per_network * (N + nb + 1),
+                                     "sample": "one numpy boundary-MPS network x the N + nb + 1 networks"},
+            "f4_ite_6x6_chi2": {"s_per_step": ite_s / 20, "sample": "the same 20 steps (numpy)"},
+            "cores": os.cpu_count()}
+
+
+def run_next(args):
+    import torch
+
+    from paper_1908_08553_gb300 import tn
+    torch.cuda.set_device(0)
+    ctx = tn.tn_ctx_create(0, 0)
+    line = {"metric": "next rows: pair correlators, complex PEPS, boundary MPS, ITE", "unit": "s",
+            "higher_is_better": False, "data": "synthetic: seeded uniform[-1,1) site tensors",
+            "results": next_rows(tn, torch, ctx)}
+    tn.tn_ctx_destroy(ctx)
+    line["cpu_baseline"] = {"kind": "oracle", "next_rows_oracle": next_rows_oracle()}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 # ------------------------------------------------------------------ serving --
@@ -987,7 +1121,7 @@ def main():
                     help="headline only: skip the other precisions, the 8x8 batch, serving and the CPU baseline")
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end measurement")
     ap.add_argument("--serve-requests", type=int, default=48, help="headline extras: served stream length")
-    ap.add_argument("--workload", default="large", choices=["large", "8x8", "serve", "batch", "case"],
+    ap.add_argument("--workload", default="large", choices=["large", "8x8", "serve", "batch", "case", "next"],
                     help="large: 12x12 D=2 + 8x8 D=3 energies (the headline); 8x8: the 8x8 D=2 batch; "
                          "serve: Poisson request stream; batch: 512 mixed lattices; case: --batch copies of "
                          "one L x W lattice")
@@ -1008,7 +1142,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     return {"large": run_headline, "8x8": run_8x8, "serve": run_serve, "batch": run_batch,
-            "case": run_case}[args.workload](args)
+            "case": run_case, "next": run_next}[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -445,22 +445,27 @@ tn_status tn_autotune_load(const char *path);
  * state whose physical legs are the rows' down legs; each further row is
  * applied as a matrix product operator and the result compressed back to bond
  * chi (right-orthonormalised right to left, then cut by SVD left to right,
- * keeping the chi largest singular values; FP64 one-sided Jacobi SVDs).  With
+ * keeping the chi largest singular values; one-sided Jacobi SVDs).  With
  * chi >= (D^2)^floor(W/2) nothing is dropped and the result is exact.
+ * prec: TN_FP64, or TN_FP32 (every tensor and SVD in FP32: the truncation
+ * error of an approximate contraction is far above FP32 rounding, and the
+ * GB300 runs FP32 at 64 times its FP64 rate; singular values below 3e-6 of the
+ * largest are dropped as zero); other precisions return TN_ERR_INVALID.
  * chi must satisfy max(chi, D^2) * D^2 <= 512.  Every network is contracted by
  * one block of one launch, its workspace (about (2W + 2) B^2 D^2 + B^2 + D^8
  * doubles, B = max(chi, D^2) D^2) taken from the context's budget for the call.
  * tn_bmps_norm: <Psi|Psi>. */
-tn_status tn_bmps_norm(tn_lattice *lat, int chi, tn_scalar *out);
+tn_status tn_bmps_norm(tn_lattice *lat, int chi, tn_precision prec, tn_scalar *out);
 /* <A_i> (op_j = 0) or <A_i B_j> (i != j) for A, B in {TN_OP_X, TN_OP_Z}, any
  * sites: the network with the operators inserted over the norm, both by the
  * boundary MPS (two networks, one launch). */
-tn_status tn_bmps_expectation(tn_lattice *lat, int chi, int op_i, int i, int op_j, int j, double *out);
+tn_status tn_bmps_expectation(tn_lattice *lat, int chi, tn_precision prec, int op_i, int i, int op_j, int j,
+                               double *out);
 /* The norm, every <X_k> and every nearest-neighbour <Z_i Z_j> (1 + N + nb
  * networks in one launch, Sec. 5's one contraction per observable, each by the
  * boundary MPS), and E = -J sum <ZZ> - h sum <X>; out->sx / out->szsz filled if
  * non-NULL; out->sz and out->czz untouched. */
-tn_status tn_bmps_energy(tn_lattice *lat, int chi, double J, double h, tn_result *out);
+tn_status tn_bmps_energy(tn_lattice *lat, int chi, tn_precision prec, double J, double h, tn_result *out);
 
 /* ------------------------------------------------------------ misc -------- */
 

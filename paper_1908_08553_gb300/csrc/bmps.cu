@@ -12,8 +12,10 @@
 // The last row closes the state into a scalar.  Every tensor is rescaled to
 // max |entry| in [1/2, 1) by an exact power of two after each row, the powers
 // summed in an integer exponent.  One block contracts one network (the norm,
-// or the norm with one or two Pauli operators inserted), FP64 throughout; its
-// tensors live in a global-memory workspace of its own.
+// or the norm with one or two Pauli operators inserted), in FP64 or FP32
+// throughout (an approximation whose truncation error is far above FP32
+// rounding; GB300 runs FP32 at 64 times its FP64 rate); its tensors live in a
+// global-memory workspace of its own.
 #include <cstdint>
 
 #include "jacobi.cuh"
@@ -26,28 +28,30 @@ namespace {
 constexpr int kBmpsThreads = 256;
 constexpr int kBmpsMaxBond = 512;     // columns of any SVD (host-checked)
 
-__device__ __forceinline__ double bmps_block_max(double v, double* red) {
+template <typename T>
+__device__ __forceinline__ T bmps_block_max(T v, T* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
     if (l == 0) red[w] = v;
     __syncthreads();
-    double r = 0.0;
+    T r = 0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r = fmax(r, red[k]);
     __syncthreads();
     return r;
 }
 
 // Scale x[0..n) by 2^-e with e the frexp exponent of max |x|; returns e.
-__device__ int bmps_rescale(double* x, long long n, double* red) {
-    double m = 0.0;
+template <typename T>
+__device__ int bmps_rescale(T* x, long long n, T* red) {
+    T m = 0;
     for (long long k = threadIdx.x; k < n; k += blockDim.x) m = fmax(m, fabs(x[k]));
     m = bmps_block_max(m, red);
-    if (!(m > 0.0) || !isfinite(m)) return 0;
+    if (!(m > T(0)) || !isfinite(m)) return 0;
     int e;
     frexp(m, &e);
-    const double f = ldexp(1.0, -e);
+    const T f = (T)ldexp(1.0, -e);
     for (long long k = threadIdx.x; k < n; k += blockDim.x) x[k] *= f;
     __syncthreads();
     return e;
@@ -55,17 +59,20 @@ __device__ int bmps_rescale(double* x, long long n, double* red) {
 
 // Singular values (column norms) of the n columns of S after block_jacobi,
 // ordered: sel[0..k) = the columns with the k largest norms (ties: lower
-// index), k = min(kmax, numerical rank: sigma > 1e-14 sigma_max).  Returns k.
-__device__ int bmps_select(const double* S, int m, int n, long long lds, int kmax, double* sig, int* sel,
-                           double* red) {
+// index), k = min(kmax, numerical rank: sigma > 1e-14 sigma_max in FP64,
+// 3e-6 sigma_max in FP32).  Returns k.
+template <typename T>
+__device__ int bmps_select(const T* S, int m, int n, long long lds, int kmax, T* sig, int* sel, T* red) {
+    // FP32 keeps values above a few units of its rounding of the largest
+    const T floor_rel = sizeof(T) == 8 ? T(1e-14) : T(3e-6);
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        double s2 = 0.0;
-        const double* cc = S + c * lds;
+        T s2 = 0;
+        const T* cc = S + c * lds;
         for (int r = 0; r < m; ++r) s2 += cc[r] * cc[r];
         sig[c] = sqrt(s2);
     }
     __syncthreads();
-    double mx = 0.0;
+    T mx = 0;
     for (int c = threadIdx.x; c < n; c += blockDim.x) mx = fmax(mx, sig[c]);
     mx = bmps_block_max(mx, red);
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
@@ -76,13 +83,14 @@ __device__ int bmps_select(const double* S, int m, int n, long long lds, int kma
     __syncthreads();
     int k = 0;
     for (int r = 0; r < n && r < kmax; ++r)
-        if (sig[sel[r]] > 1e-14 * mx) ++k;
+        if (sig[sel[r]] > floor_rel * mx) ++k;
     return k > 0 ? k : 1;     // a zero tensor keeps one (zero) column
 }
 
 // Double-layer tensor of site (r, c): T[(u u')(l l')(dn dn')(rt rt')] =
 // sum_{p,q} A[p,u,l,dn,rt] O[p][q] A[q,u',l',dn',rt'] (O = I, X or Z).
-__device__ void bmps_site(const double* A, const int* d5, int op, double* T) {
+template <typename T>
+__device__ void bmps_site(const double* A, const int* d5, int op, T* Tout) {
     const int u = d5[1], l = d5[2], dn = d5[3], rt = d5[4];
     const long long half = (long long)u * l * dn * rt;
     const int U = u * u, Lg = l * l, Dn = dn * dn, R = rt * rt;
@@ -101,7 +109,7 @@ __device__ void bmps_site(const double* A, const int* d5, int op, double* T) {
         const long long ia = (((long long)ua * l + la) * dn + da) * rt + ra;
         const long long ib = (((long long)ub * l + lb) * dn + db) * rt + rb;
         const double a0 = A[ia], a1 = A[half + ia], b0 = A[ib], b1 = A[half + ib];
-        T[idx] = a0 * (o00 * b0 + o01 * b1) + a1 * (o10 * b0 + o11 * b1);
+        Tout[idx] = (T)(a0 * (o00 * b0 + o01 * b1) + a1 * (o10 * b0 + o11 * b1));
     }
     __syncthreads();
 }
@@ -114,26 +122,27 @@ long long bmps_workspace(int W, int D, int chi) {
     return (2LL * W + 2) * slot + B * B + d * d * d * d;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kBmpsThreads) k_bmps(const BmpsTask* __restrict__ tasks) {
     const BmpsTask& t = tasks[blockIdx.x];
     __shared__ int a[17];                     // a[c] = bond left of tensor c; a[0] = a[W] = 1
     __shared__ int ph[16];                    // physical (down-leg) dimension of tensor c
     __shared__ int d5[5];
     __shared__ long long soff[257];
-    __shared__ double red[kBmpsThreads / 32];
-    __shared__ double sig[kBmpsMaxBond];
+    __shared__ T red[kBmpsThreads / 32];
+    __shared__ T sig[kBmpsMaxBond];
     __shared__ int sel[kBmpsMaxBond];
     __shared__ int flag;
     const int L = t.L, W = t.W, D = t.D, chi = t.chi;
     const int d = D * D;
     const long long B = bmps_bond_max(D, chi);
     const long long slot = B * d * B;
-    double* bufA = t.ws;
-    double* bufB = bufA + (long long)W * slot;
-    double* S = bufB + (long long)W * slot;
-    double* Tm = S + slot;
-    double* V = Tm + slot;
-    double* Ts = V + B * B;
+    T* bufA = reinterpret_cast<T*>(t.ws);
+    T* bufB = bufA + (long long)W * slot;
+    T* S = bufB + (long long)W * slot;
+    T* Tm = S + slot;
+    T* V = Tm + slot;
+    T* Ts = V + B * B;
     long long ex = 0;                         // power-of-two exponent of the value
     if (threadIdx.x == 0) {
         soff[0] = 0;
@@ -182,8 +191,8 @@ __global__ void __launch_bounds__(kBmpsThreads) k_bmps(const BmpsTask* __restric
             site(r, c);
             const int lu = d5[1] * d5[1], ll = d5[2] * d5[2], ld = d5[3] * d5[3], lr = d5[4] * d5[4];
             const int ac = a[c], bc = a[c + 1];
-            const double* M = bufA + c * slot;
-            double* N = bufB + c * slot;
+            const T* M = bufA + c * slot;
+            T* N = bufB + c * slot;
             const long long n = (long long)ac * ll * ld * bc * lr;
             for (long long idx = threadIdx.x; idx < n; idx += blockDim.x) {
                 long long k = idx;
@@ -192,7 +201,7 @@ __global__ void __launch_bounds__(kBmpsThreads) k_bmps(const BmpsTask* __restric
                 const int dn = (int)(k % ld); k /= ld;
                 const int l = (int)(k % ll); k /= ll;
                 const int aa = (int)k;
-                double v = 0.0;
+                T v = 0;
                 for (int u = 0; u < lu; ++u)
                     v += M[((long long)aa * lu + u) * bc + bb] * Ts[(((long long)u * ll + l) * ld + dn) * lr + x];
                 N[idx] = v;
@@ -206,13 +215,13 @@ __global__ void __launch_bounds__(kBmpsThreads) k_bmps(const BmpsTask* __restric
         if (threadIdx.x == 0)
             for (int c = 1; c < W; ++c) a[c] *= d;
         __syncthreads();
-        { double* tmp = bufA; bufA = bufB; bufB = tmp; }
+        { T* tmp = bufA; bufA = bufB; bufB = tmp; }
 
         if (r < L - 1) {
             // ---- right to left: right-orthonormalise
             for (int c = W - 1; c >= 1; --c) {
                 const int ac = a[c], p = ph[c], bc = a[c + 1];
-                double* M = bufA + c * slot;
+                T* M = bufA + c * slot;
                 const int m = p * bc;
                 // M row-major [a][p b] is its transpose column-major: columns = the a rows
                 block_jacobi(M, m, ac, m, V, ac, &flag);
@@ -220,17 +229,17 @@ __global__ void __launch_bounds__(kBmpsThreads) k_bmps(const BmpsTask* __restric
                 // new tensor c: row j = column sel[j] / sigma
                 for (long long idx = threadIdx.x; idx < (long long)k * m; idx += blockDim.x) {
                     const int j = (int)(idx / m), i = (int)(idx - (long long)j * m);
-                    const double sg = sig[sel[j]];
-                    Tm[idx] = sg > 0.0 ? M[(long long)sel[j] * m + i] / sg : 0.0;
+                    const T sg = sig[sel[j]];
+                    Tm[idx] = sg > T(0) ? M[(long long)sel[j] * m + i] / sg : T(0);
                 }
                 __syncthreads();
                 // tensor c - 1 times V Sigma: [x][p'][a] -> [x][p'][j]
                 const int ap = a[c - 1] * ph[c - 1];
-                double* Mp = bufA + (c - 1) * slot;
+                T* Mp = bufA + (c - 1) * slot;
                 for (long long idx = threadIdx.x; idx < (long long)ap * k; idx += blockDim.x) {
                     const int xp = (int)(idx / k), j = (int)(idx - (long long)xp * k);
                     const int cj = sel[j];
-                    double v = 0.0;
+                    T v = 0;
                     for (int aa = 0; aa < ac; ++aa) v += Mp[(long long)xp * ac + aa] * V[(long long)cj * ac + aa];
                     S[idx] = v * sig[cj];
                 }
@@ -244,7 +253,7 @@ __global__ void __launch_bounds__(kBmpsThreads) k_bmps(const BmpsTask* __restric
             // ---- left to right: truncate every bond to chi
             for (int c = 0; c < W - 1; ++c) {
                 const int ac = a[c], p = ph[c], bc = a[c + 1];
-                double* M = bufA + c * slot;
+                T* M = bufA + c * slot;
                 const int m = ac * p;
                 for (long long idx = threadIdx.x; idx < (long long)m * bc; idx += blockDim.x) {
                     const int i = (int)(idx / bc), j = (int)(idx - (long long)i * bc);
@@ -255,16 +264,16 @@ __global__ void __launch_bounds__(kBmpsThreads) k_bmps(const BmpsTask* __restric
                 const int k = bmps_select(S, m, bc, m, chi, sig, sel, red);
                 for (long long idx = threadIdx.x; idx < (long long)m * k; idx += blockDim.x) {
                     const int i = (int)(idx / k), j = (int)(idx - (long long)i * k);
-                    const double sg = sig[sel[j]];
-                    M[idx] = sg > 0.0 ? S[(long long)sel[j] * m + i] / sg : 0.0;
+                    const T sg = sig[sel[j]];
+                    M[idx] = sg > T(0) ? S[(long long)sel[j] * m + i] / sg : T(0);
                 }
                 // tensor c + 1 := Sigma V^T (k x b) times [b][q]
                 const int q = ph[c + 1] * a[c + 2];
-                double* Mn = bufA + (c + 1) * slot;
+                T* Mn = bufA + (c + 1) * slot;
                 for (long long idx = threadIdx.x; idx < (long long)k * q; idx += blockDim.x) {
                     const int j = (int)(idx / q), qq = (int)(idx - (long long)j * q);
                     const int cj = sel[j];
-                    double v = 0.0;
+                    T v = 0;
                     for (int bb = 0; bb < bc; ++bb) v += V[(long long)cj * bc + bb] * Mn[(long long)bb * q + qq];
                     Tm[idx] = sig[cj] * v;
                 }
@@ -279,36 +288,37 @@ __global__ void __launch_bounds__(kBmpsThreads) k_bmps(const BmpsTask* __restric
     }
 
     // ---- close: every physical leg has dimension 1 now; v := v M_c
-    double* v = S;
-    double* w = Tm;
-    if (threadIdx.x == 0) v[0] = 1.0;
+    T* v = S;
+    T* w = Tm;
+    if (threadIdx.x == 0) v[0] = T(1);
     __syncthreads();
     for (int c = 0; c < W; ++c) {
         const int ac = a[c], bc = a[c + 1];
-        const double* M = bufA + c * slot;   // [a][1][b]
+        const T* M = bufA + c * slot;   // [a][1][b]
         for (int j = threadIdx.x; j < bc; j += blockDim.x) {
-            double s = 0.0;
+            T s = 0;
             for (int aa = 0; aa < ac; ++aa) s += v[aa] * M[(long long)aa * bc + j];
             w[j] = s;
         }
         __syncthreads();
         ex += bmps_rescale(w, bc, red);
-        double* tmp = v; v = w; w = tmp;
+        T* tmp = v; v = w; w = tmp;
     }
     if (threadIdx.x == 0) {
         int e = 0;
-        const double m = frexp(v[0], &e);
+        const double m = frexp((double)v[0], &e);
         t.out[0] = m;
         t.out[1] = (double)(ex + e);
     }
 }
 
 // One kernel of this translation unit, for loading its module up front (preload.cpp).
-const void* bmps_module_anchor() { return reinterpret_cast<const void*>(&k_bmps); }
+const void* bmps_module_anchor() { return reinterpret_cast<const void*>(&k_bmps<double>); }
 
-cudaError_t launch_bmps(const BmpsTask* tasks, int ntasks, cudaStream_t st) {
+cudaError_t launch_bmps(int dt, const BmpsTask* tasks, int ntasks, cudaStream_t st) {
     if (ntasks <= 0) return cudaSuccess;
-    k_bmps<<<ntasks, kBmpsThreads, 0, st>>>(tasks);
+    if (dt == 0) k_bmps<double><<<ntasks, kBmpsThreads, 0, st>>>(tasks);
+    else k_bmps<float><<<ntasks, kBmpsThreads, 0, st>>>(tasks);
     return cudaGetLastError();
 }
 

@@ -13,10 +13,12 @@ tn_status result_from_array(const double* r, int L, int W, tn_precision prec, co
 namespace {
 
 // Contract the given networks; out receives (mantissa, exponent) per network.
-tn_status bmps_run(tn_lattice* lat, int chi, std::vector<BmpsTask>& tasks, std::vector<double>* out) {
+tn_status bmps_run(tn_lattice* lat, int chi, tn_precision prec, std::vector<BmpsTask>& tasks,
+                   std::vector<double>* out) {
     tn_ctx* ctx = lat->ctx;
     const int L = lat->L, W = lat->W, D = lat->D;
     if (lat->cplx) { set_error("the boundary MPS takes real site tensors"); return TN_ERR_INVALID; }
+    if (prec != TN_FP64 && prec != TN_FP32) { set_error("the boundary MPS runs in FP64 or FP32"); return TN_ERR_INVALID; }
     if (chi < 1 || bmps_bond_max(D, chi) > 512) {
         set_error("chi out of range: max(chi, D^2) * D^2 must not exceed 512");
         return TN_ERR_INVALID;
@@ -47,7 +49,7 @@ tn_status bmps_run(tn_lattice* lat, int chi, std::vector<BmpsTask>& tasks, std::
     e = cudaMemcpyAsync(buf, lat->host.data(), nel * 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(buf + off_tasks, tasks.data(), n * sizeof(BmpsTask), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_bmps(reinterpret_cast<const BmpsTask*>(buf + off_tasks), (int)n, st);
+    if (e == cudaSuccess) e = launch_bmps(prec == TN_FP64 ? 0 : 1, reinterpret_cast<const BmpsTask*>(buf + off_tasks), (int)n, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out->data(), buf + off_out, 2 * n * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(buf);
@@ -72,12 +74,12 @@ using namespace tn;
 
 extern "C" {
 
-tn_status tn_bmps_norm(tn_lattice* lat, int chi, tn_scalar* out) {
+tn_status tn_bmps_norm(tn_lattice* lat, int chi, tn_precision prec, tn_scalar* out) {
     try {
         if (!lat || !out) return TN_ERR_INVALID;
         std::vector<BmpsTask> tasks{plain_task()};
         std::vector<double> o;
-        const tn_status s = bmps_run(lat, chi, tasks, &o);
+        const tn_status s = bmps_run(lat, chi, prec, tasks, &o);
         if (s != TN_OK) return s;
         out->mant = o[0];
         out->exp2 = (int64_t)o[1];
@@ -89,7 +91,8 @@ tn_status tn_bmps_norm(tn_lattice* lat, int chi, tn_scalar* out) {
     }
 }
 
-tn_status tn_bmps_expectation(tn_lattice* lat, int chi, int op_i, int i, int op_j, int j, double* out) {
+tn_status tn_bmps_expectation(tn_lattice* lat, int chi, tn_precision prec, int op_i, int i, int op_j, int j,
+                               double* out) {
     try {
         if (!lat || !out) return TN_ERR_INVALID;
         const int N = lat->L * lat->W;
@@ -106,7 +109,7 @@ tn_status tn_bmps_expectation(tn_lattice* lat, int chi, int op_i, int i, int op_
             tasks[1].op_code[1] = op_j == TN_OP_X ? 1 : 2;
         }
         std::vector<double> o;
-        const tn_status s = bmps_run(lat, chi, tasks, &o);
+        const tn_status s = bmps_run(lat, chi, prec, tasks, &o);
         if (s != TN_OK) return s;
         *out = ratio(o, 1);
         return std::isfinite(*out) ? TN_OK : TN_ERR_NUMERIC;
@@ -116,7 +119,7 @@ tn_status tn_bmps_expectation(tn_lattice* lat, int chi, int op_i, int i, int op_
     }
 }
 
-tn_status tn_bmps_energy(tn_lattice* lat, int chi, double J, double h, tn_result* out) {
+tn_status tn_bmps_energy(tn_lattice* lat, int chi, tn_precision prec, double J, double h, tn_result* out) {
     try {
         if (!lat || !out) return TN_ERR_INVALID;
         const int L = lat->L, W = lat->W, N = L * W;
@@ -139,7 +142,7 @@ tn_status tn_bmps_energy(tn_lattice* lat, int chi, double J, double h, tn_result
             tasks.push_back(t);
         }
         std::vector<double> o;
-        const tn_status s = bmps_run(lat, chi, tasks, &o);
+        const tn_status s = bmps_run(lat, chi, prec, tasks, &o);
         if (s != TN_OK) return s;
         double sx = 0.0, szz = 0.0;
         for (int k = 0; k < N; ++k) {
@@ -156,7 +159,7 @@ tn_status tn_bmps_energy(tn_lattice* lat, int chi, double J, double h, tn_result
         out->energy_per_site = out->energy / N;
         out->norm.mant = o[0];
         out->norm.exp2 = (int64_t)o[1];
-        out->precision = TN_FP64;
+        out->precision = prec;
         out->err_bound_est = 0.0;
         out->schedule_o = out->schedule_i = out->schedule_j = -1;
         if (!std::isfinite(out->energy)) { set_error("non-finite energy"); return TN_ERR_NUMERIC; }

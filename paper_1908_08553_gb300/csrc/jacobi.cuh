@@ -1,5 +1,5 @@
 // Block-wide one-sided Jacobi SVD (Hestenes 1958; Demmel & Veselic 1992) on a
-// matrix in global memory, FP64.  The n columns of A (column-major, leading
+// matrix in global memory, FP64 or FP32.  The n columns of A (column-major, leading
 // dimension lda, m rows) are rotated pairwise until mutually orthogonal; the
 // same rotations applied to V (n x n, column-major, leading dimension ldv,
 // reset to the identity here) give A_in = A_out V^T with A_out = U Sigma, so
@@ -15,19 +15,24 @@ namespace tn {
 
 constexpr int kJacobiMaxSweeps = 60;
 
-__device__ __forceinline__ double jacobi_warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T jacobi_warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// `flag` is one int of shared memory owned by the caller.
-__device__ inline void block_jacobi(double* A, int m, int n, long long lda, double* V, long long ldv, int* flag) {
+// `flag` is one int of shared memory owned by the caller.  T is double or
+// float; a pair counts as orthogonal when |a.b| <= tol |a| |b|, tol = 1e-15
+// (double) or 1e-6 (float, a few units of its rounding).
+template <typename T>
+__device__ inline void block_jacobi(T* A, int m, int n, long long lda, T* V, long long ldv, int* flag) {
+    const T tol = sizeof(T) == 8 ? T(1e-15) : T(1e-6);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int n2 = n + (n & 1);
     for (long long idx = threadIdx.x; idx < (long long)n * n; idx += blockDim.x) {
         const int c = (int)(idx / n), r = (int)(idx - (long long)c * n);
-        V[c * ldv + r] = r == c ? 1.0 : 0.0;
+        V[c * ldv + r] = r == c ? T(1) : T(0);
     }
     __syncthreads();
     for (int sweep = 0; sweep < kJacobiMaxSweeps && n > 1; ++sweep) {
@@ -40,29 +45,29 @@ __device__ inline void block_jacobi(double* A, int m, int n, long long lda, doub
                 else { a = (round + k) % (n2 - 1); b = (round - k + n2 - 1) % (n2 - 1); }
                 if (a > b) { const int t = a; a = b; b = t; }
                 if (b >= n) continue;              // the padding column is zero
-                double* ca = A + a * lda;
-                double* cb = A + b * lda;
-                double al = 0.0, be = 0.0, ga = 0.0;
+                T* ca = A + a * lda;
+                T* cb = A + b * lda;
+                T al = 0, be = 0, ga = 0;
                 for (int r = lane; r < m; r += 32) {
-                    const double x = ca[r], y = cb[r];
+                    const T x = ca[r], y = cb[r];
                     al += x * x; be += y * y; ga += x * y;
                 }
                 al = jacobi_warp_sum(al); be = jacobi_warp_sum(be); ga = jacobi_warp_sum(ga);
-                if (ga == 0.0 || al == 0.0 || be == 0.0) continue;
-                if (fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+                if (ga == T(0) || al == T(0) || be == T(0)) continue;
+                if (fabs(ga) <= tol * sqrt(al * be)) continue;
                 if (lane == 0) *flag = 0;
-                const double zeta = (be - al) / (2.0 * ga);
-                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                const T zeta = (be - al) / (T(2) * ga);
+                const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                const T c = T(1) / sqrt(T(1) + t * t), s = c * t;
                 for (int r = lane; r < m; r += 32) {
-                    const double x = ca[r], y = cb[r];
+                    const T x = ca[r], y = cb[r];
                     ca[r] = c * x - s * y;
                     cb[r] = s * x + c * y;
                 }
-                double* va = V + a * ldv;
-                double* vb = V + b * ldv;
+                T* va = V + a * ldv;
+                T* vb = V + b * ldv;
                 for (int r = lane; r < n; r += 32) {
-                    const double x = va[r], y = vb[r];
+                    const T x = va[r], y = vb[r];
                     va[r] = c * x - s * y;
                     vb[r] = s * x + c * y;
                 }

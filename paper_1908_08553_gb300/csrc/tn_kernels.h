@@ -176,7 +176,7 @@ __host__ __device__ inline int bmps_bond_max(int D, int chi) {
     const int d = D * D;
     return (chi > d ? chi : d) * d;
 }
-cudaError_t launch_bmps(const BmpsTask* tasks, int ntasks, cudaStream_t st);
+cudaError_t launch_bmps(int dt, const BmpsTask* tasks, int ntasks, cudaStream_t st);   // dt 0: FP64, 1: FP32
 
 // ----------------------------------------------------------- launchers ---
 // Each returns cudaSuccess or the launch error.  dt: 0 FP64, 1 FP32.

@@ -112,9 +112,9 @@ SIGNATURES = {
     "tn_autotune_clear": (c_int, []),
     "tn_autotune_save": (c_int, [c_char_p]),
     "tn_autotune_load": (c_int, [c_char_p]),
-    "tn_bmps_norm": (c_int, [c_void_p, c_int, POINTER(tn_scalar)]),
-    "tn_bmps_expectation": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, POINTER(c_double)]),
-    "tn_bmps_energy": (c_int, [c_void_p, c_int, c_double, c_double, POINTER(tn_result)]),
+    "tn_bmps_norm": (c_int, [c_void_p, c_int, c_int, POINTER(tn_scalar)]),
+    "tn_bmps_expectation": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, POINTER(c_double)]),
+    "tn_bmps_energy": (c_int, [c_void_p, c_int, c_int, c_double, c_double, POINTER(tn_result)]),
     "tn_ite_run": (c_int, [c_void_p, POINTER(tn_ite_params), c_void_p, c_void_p, POINTER(c_double)]),
     "tn_ctx_kernel_stats": (c_int, [c_void_p, c_int, POINTER(c_int64), POINTER(c_double), POINTER(c_double),
                                     POINTER(c_double)]),
@@ -517,23 +517,23 @@ def tn_autotune_load(path: str):
     check(lib().tn_autotune_load(path.encode()), "tn_autotune_load")
 
 
-def tn_bmps_norm(lat, chi: int):
+def tn_bmps_norm(lat, chi: int, prec: int = TN_FP64):
     """<Psi|Psi> by the boundary MPS of bond chi: (mantissa, exponent)."""
     out = tn_scalar()
-    check(lib().tn_bmps_norm(lat, chi, byref(out)), "tn_bmps_norm")
+    check(lib().tn_bmps_norm(lat, chi, prec, byref(out)), "tn_bmps_norm")
     return out.mant, out.exp2
 
 
-def tn_bmps_expectation(lat, chi: int, op_i: int, i: int, op_j: int = 0, j: int = -1) -> float:
+def tn_bmps_expectation(lat, chi: int, op_i: int, i: int, op_j: int = 0, j: int = -1, prec: int = TN_FP64) -> float:
     v = c_double()
-    check(lib().tn_bmps_expectation(lat, chi, op_i, i, op_j, j, byref(v)), "tn_bmps_expectation")
+    check(lib().tn_bmps_expectation(lat, chi, prec, op_i, i, op_j, j, byref(v)), "tn_bmps_expectation")
     return v.value
 
 
-def tn_bmps_energy(lat, chi: int, J: float, h: float, L: int, W: int):
+def tn_bmps_energy(lat, chi: int, J: float, h: float, L: int, W: int, prec: int = TN_FP64):
     """(tn_result, sx, szsz) by the boundary MPS of bond chi."""
     r, sx, zz, nb = _result_arrays(L, W)
-    check(lib().tn_bmps_energy(lat, chi, J, h, byref(r)), "tn_bmps_energy")
+    check(lib().tn_bmps_energy(lat, chi, prec, J, h, byref(r)), "tn_bmps_energy")
     return r, sx, zz[:nb]
 
 

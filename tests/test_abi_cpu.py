@@ -243,6 +243,14 @@ def test_bmps_arguments(cpu_ctx):
         with pytest.raises(tn.TNError) as e:
             tn.tn_bmps_norm(lat, 8)
         assert e.value.status == tn.TN_ERR_NO_DEVICE
+        for prec in (tn.TN_FP32, tn.TN_FP64):
+            with pytest.raises(tn.TNError) as e:
+                tn.tn_bmps_norm(lat, 8, prec)
+            assert e.value.status == tn.TN_ERR_NO_DEVICE
+        for prec in (tn.TN_BF16X3, tn.TN_BF16X6, 7):
+            with pytest.raises(tn.TNError) as e:
+                tn.tn_bmps_norm(lat, 8, prec)
+            assert e.value.status == tn.TN_ERR_INVALID
         with pytest.raises(tn.TNError) as e:
             tn.tn_bmps_expectation(lat, 8, tn.TN_OP_ZZ, 0)
         assert e.value.status == tn.TN_ERR_INVALID

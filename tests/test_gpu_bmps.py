@@ -6,6 +6,8 @@
   numpy QR and SVD) to rounding: the same compression keeps the same singular
   values, whatever the factorisation's gauge.
 * The Ising PEPS norm is the enumerated partition function at the exact rank.
+* FP32 (every tensor and SVD): the same results within 1e-5 relative (norm) and
+  1e-4 absolute (observables), the truncation decisions unchanged.
 """
 import math
 
@@ -102,3 +104,22 @@ def test_ising_peps_partition_function(ctx):
         tn.tn_destroy_lattice(lat)
     logz, _, _ = oracle.ising_enumerate(L, W, K)
     assert abs(_log2(m, e) * math.log(2) - logz) < 1e-11 * logz
+
+
+@pytest.mark.parametrize("L,W,D,chi", [(4, 4, 2, 16), (4, 3, 3, 9), (6, 6, 2, 8), (5, 7, 2, 6)])
+def test_fp32_follows_fp64(ctx, L, W, D, chi):
+    A = inputs.random_lattice(L, W, D, 3200 + L + W + chi)
+    lat = _lat(ctx, L, W, D, A)
+    try:
+        m, e = tn.tn_bmps_norm(lat, chi, tn.TN_FP32)
+        mr, er = bm.norm(L, W, D, A, chi)
+        assert abs(_log2(m, e) - _log2(mr, er)) < 1e-5 * max(1.0, abs(_log2(mr, er)))
+        r32, sx32, zz32 = tn.tn_bmps_energy(lat, chi, 1.0, 3.04, L, W, tn.TN_FP32)
+        r64, sx64, zz64 = tn.tn_bmps_energy(lat, chi, 1.0, 3.04, L, W, tn.TN_FP64)
+        np.testing.assert_allclose(sx32, sx64, rtol=0, atol=1e-4)
+        np.testing.assert_allclose(zz32, zz64, rtol=0, atol=1e-4)
+        assert r32.precision == tn.TN_FP32
+        v = tn.tn_bmps_expectation(lat, chi, tn.TN_OP_Z, 0, tn.TN_OP_Z, L * W - 1, tn.TN_FP32)
+        assert abs(v - bm.expectation(L, W, D, A, chi, {0: Z, L * W - 1: Z})) < 1e-4
+    finally:
+        tn.tn_destroy_lattice(lat)
