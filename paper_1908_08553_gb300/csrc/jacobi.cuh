@@ -24,16 +24,33 @@ __device__ __forceinline__ T jacobi_warp_sum(T v) {
 
 // `flag` is one int of shared memory owned by the caller.  T is double or
 // float; a pair counts as orthogonal when |a.b| <= tol |a| |b|, tol = 1e-15
-// (double) or 1e-6 (float, a few units of its rounding).
+// (double) or 1e-6 (float, a few units of its rounding).  A column whose norm
+// is at most tol |A|_F is numerically zero (the matrices here are often rank-
+// deficient, e.g. a two-site product through a bond of dimension chi): its
+// pairs are not rotated, so rounding noise in such columns cannot keep the
+// sweeps from converging.
 template <typename T>
 __device__ inline void block_jacobi(T* A, int m, int n, long long lda, T* V, long long ldv, int* flag) {
     const T tol = sizeof(T) == 8 ? T(1e-15) : T(1e-6);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int n2 = n + (n & 1);
+    __shared__ T fro_part[32];
+    T f2 = 0;
+    for (long long idx = threadIdx.x; idx < (long long)n * m; idx += blockDim.x) {
+        const int c = (int)(idx / m), r = (int)(idx - (long long)c * m);
+        const T x = A[c * lda + r];
+        f2 += x * x;
+    }
+    f2 = jacobi_warp_sum(f2);
+    if (lane == 0) fro_part[warp] = f2;
     for (long long idx = threadIdx.x; idx < (long long)n * n; idx += blockDim.x) {
         const int c = (int)(idx / n), r = (int)(idx - (long long)c * n);
         V[c * ldv + r] = r == c ? T(1) : T(0);
     }
+    __syncthreads();
+    T fro2 = 0;
+    for (int w = 0; w < nwarps; ++w) fro2 += fro_part[w];
+    const T negligible = tol * tol * fro2;
     __syncthreads();
     for (int sweep = 0; sweep < kJacobiMaxSweeps && n > 1; ++sweep) {
         if (threadIdx.x == 0) *flag = 1;
@@ -53,7 +70,7 @@ __device__ inline void block_jacobi(T* A, int m, int n, long long lda, T* V, lon
                     al += x * x; be += y * y; ga += x * y;
                 }
                 al = jacobi_warp_sum(al); be = jacobi_warp_sum(be); ga = jacobi_warp_sum(ga);
-                if (ga == T(0) || al == T(0) || be == T(0)) continue;
+                if (ga == T(0) || al <= negligible || be <= negligible) continue;
                 if (fabs(ga) <= tol * sqrt(al * be)) continue;
                 if (lane == 0) *flag = 0;
                 const T zeta = (be - al) / (T(2) * ga);
