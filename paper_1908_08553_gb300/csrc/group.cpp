@@ -11,6 +11,7 @@
 // on its shape, so it gives the same bits in a group as alone.
 #include <algorithm>
 #include <cstring>
+#include <memory>
 
 #include "runtime.h"
 
@@ -78,7 +79,9 @@ tn_status tn_batch_group_create(tn_ctx* ctx, int n, const int* L, const int* W, 
                 return TN_ERR_OVER_BUDGET;
             }
         }
-        auto g = new tn_batch_group();
+        // freed with everything it holds on every early return or exception
+        std::unique_ptr<tn_batch_group, void (*)(tn_batch_group*)> owner(new tn_batch_group(), group_free);
+        tn_batch_group* g = owner.get();
         g->ctx = ctx;
         g->stream = ctx->stream;
         g->n = n;
@@ -103,7 +106,7 @@ tn_status tn_batch_group_create(tn_ctx* ctx, int n, const int* L, const int* W, 
             tn_batch* probe = nullptr;
             const tn_status st = batch_create(ctx, (int)mem.size(), l.data(), w.data(), d.data(), prec, sched, work,
                                               false, &probe, nullptr, &sizing);
-            if (st != TN_OK) { if (probe) delete probe; group_free(g); return st; }
+            if (st != TN_OK) { if (probe) delete probe; return st; }
             g->arena_bytes = std::max(g->arena_bytes, probe->arena_bytes);
             delete probe;
         }
@@ -112,7 +115,6 @@ tn_status tn_batch_group_create(tn_ctx* ctx, int n, const int* L, const int* W, 
         do {
             if (cur_used + g->arena_bytes > ctx->budget) {
                 g->arena_bytes = 0;
-                group_free(g);
                 set_error("the shared arena exceeds the remaining budget");
                 return TN_ERR_OVER_BUDGET;
             }
@@ -122,7 +124,7 @@ tn_status tn_batch_group_create(tn_ctx* ctx, int n, const int* L, const int* W, 
         if (e != cudaSuccess) {
             ctx->used -= g->arena_bytes;
             g->arena = nullptr;
-            group_free(g);
+            g->arena_bytes = 0;
             return cuda_status(e, "shared arena");
         }
         BatchOpts opts;
@@ -138,7 +140,7 @@ tn_status tn_batch_group_create(tn_ctx* ctx, int n, const int* L, const int* W, 
             tn_batch* b = nullptr;
             const tn_status st = batch_create(ctx, (int)mem.size(), l.data(), w.data(), d.data(), prec, sched, work,
                                               true, &b, nullptr, &opts);
-            if (st != TN_OK) { group_free(g); return st; }
+            if (st != TN_OK) return st;
             g->passes.push_back(b);
         }
         // member order in the concatenated inputs and results
@@ -165,8 +167,8 @@ tn_status tn_batch_group_create(tn_ctx* ctx, int n, const int* L, const int* W, 
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&g->gexec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
-        if (e != cudaSuccess) { g->gexec = nullptr; group_free(g); return cuda_status(e, "group graph"); }
-        *out = g;
+        if (e != cudaSuccess) { g->gexec = nullptr; return cuda_status(e, "group graph"); }
+        *out = owner.release();
         return TN_OK;
     } catch (const std::exception& ex) {
         set_error(ex.what());
