@@ -987,7 +987,9 @@ def run_batch(args):
     batch group: passes of at most the pass budget (members of a pass run
     together, every wave of all members one grouped launch) sharing one arena,
     all captured into one CUDA graph, so a run is one graph launch; members
-    whose footprint alone exceeds the budget are reported, not run."""
+    whose footprint alone exceeds the budget are reported, not run (with
+    --recompute: members whose cached-state program exceeds it run in the
+    recompute form where that fits)."""
     import numpy as np
     import torch
 
@@ -1004,11 +1006,20 @@ def run_batch(args):
     hs = rng.uniform(0.5, 5.0, size=n)
     probe = tn.tn_ctx_create(-1)
     fp = []
-    for L, W, D in zip(Ls, Ws, Ds):
+    recomputed = []
+    for k, (L, W, D) in enumerate(zip(Ls, Ws, Ds)):
         lat = tn.tn_create_lattice(probe, int(L), int(W), int(D))
         fp.append(tn.tn_footprint(lat, tn.TN_SCHED_AUTO, prec, tn.TN_WORK_ENERGY))
+        if args.recompute and fp[-1] > budget:
+            # the batch group falls back to the recompute form for such a member
+            tn.tn_autotune_set(int(L), int(W), int(D), prec, tn.TN_WORK_ENERGY, 15 | 32)
+            fp[-1] = tn.tn_footprint(lat, tn.TN_SCHED_AUTO, prec, tn.TN_WORK_ENERGY)
+            tn.tn_autotune_set(int(L), int(W), int(D), prec, tn.TN_WORK_ENERGY, 15)
+            if fp[-1] <= budget:
+                recomputed.append(k)
         tn.tn_destroy_lattice(lat)
     tn.tn_ctx_destroy(probe)
+    tn.tn_autotune_clear()
     ok = [k for k in range(n) if fp[k] <= budget]
     excluded = [k for k in range(n) if fp[k] > budget]
     stream = torch.cuda.Stream()
@@ -1055,6 +1066,7 @@ def run_batch(args):
     m = len(ok)
     line = {"metric": "batched exact TFIM-PEPS energy evals/s", "workload": "512 mixed lattices, L, W in 4..10, D in {2,3}",
             "precision": args.precision or "fp32", "members": n, "evaluated": m, "excluded_over_budget": len(excluded),
+            "recompute_form_members": len(recomputed),
             "excluded_shapes": sorted({(int(Ls[k]), int(Ws[k]), int(Ds[k])) for k in excluded}),
             "graph_launches": 1, "passes": info["passes"], "kernel_launches": info["launches"],
             "shared_arena_gb": info["arena_bytes"] / 1e9, "ms": total_ms, "autotune": tune,
@@ -1082,6 +1094,9 @@ def run_case(args):
     work = tn.TN_WORK_ENERGY if args.work == "energy" else tn.TN_WORK_NORM
     prec = tn.PRECISIONS[args.precision or "fp32"]
     L, W, D = args.L, args.W, args.D
+    if args.recompute:
+        # the recompute form of the energy program (program choice bit 32)
+        tn.tn_autotune_set(L, W, D, prec, work, tn.tn_autotune_lookup(L, W, D, prec, work)["knobs"] | 32)
     b = tn.tn_batch_create(ctx, [L] * args.batch, [W] * args.batch, [D] * args.batch, prec, sched, work)
     A = np.concatenate([inputs.random_lattice(L, W, D, inputs.lattice_seed(args.seed, k))
                         for k in range(args.batch)])
@@ -1099,7 +1114,7 @@ def run_case(args):
     ms = e0.elapsed_time(e1) / max(1, args.steps)
     r = tn.tn_batch_results_host(b)
     line = {"workload": f"{args.batch} x {L}x{W} D={D}", "precision": args.precision or "fp32",
-            "schedule": args.schedule, "work": args.work, "ms_per_run": ms,
+            "schedule": args.schedule, "work": args.work, "recompute": bool(args.recompute), "ms_per_run": ms,
             "launches_per_run": tn.tn_batch_launch_count(b),
             "log2_norm": float(r[1]), "energy_per_site": float(r[0]) / (L * W)}
     tn.tn_batch_destroy(b)
@@ -1131,6 +1146,9 @@ def main():
     ap.add_argument("--seed", type=int, default=7, help="case: tensor seed")
     ap.add_argument("--schedule", default="auto", choices=["auto", "row", "col", "quadrant"])
     ap.add_argument("--work", default="energy", choices=["energy", "norm"], help="case: work kind")
+    ap.add_argument("--recompute", action="store_true",
+                    help="case: the recompute form of the energy program (chain states recomputed, not cached); "
+                         "batch: members whose cached form exceeds the pass budget run in the recompute form")
     ap.add_argument("--clock-log", default=None, help="CSV file for the nvidia-smi clock samples")
     ap.add_argument("--members", type=int, default=512, help="batch: lattices")
     ap.add_argument("--batch-seed", type=int, default=2, help="batch: tensor seed")

@@ -159,7 +159,9 @@ int tn_lattice_is_complex(const tn_lattice *lat);
 /* ------------------------------------------------------------ planning -- */
 
 /* Exact device bytes the library allocates to run `work` on this lattice with
- * this schedule and precision (the arena admission control checks). */
+ * this schedule and precision (the arena admission control checks), for the
+ * program choices the tuning table holds for the shape (see tn_autotune):
+ * with bit 5 set, the recompute form's bytes. */
 tn_status tn_footprint(const tn_lattice *lat, tn_schedule sched, tn_precision prec,
                        tn_work work, size_t *peak_bytes);
 /* The contraction schedule chosen by the heuristic of Sec. 4 as int64 words:
@@ -204,7 +206,13 @@ tn_status tn_expectation(tn_lattice *lat, tn_precision prec, int op, int i, int 
  * (Eqs. mx, mz; blocking, AUTO schedule).  out: L*W doubles, caller-owned. */
 tn_status tn_site_expectations(tn_lattice *lat, tn_precision prec, int op, double *out);
 /* Norm, every <X_k>, every <Z_i Z_j>, every <Z_k>, the connected c_ij and E
- * for (J, h) (blocking, AUTO schedule); each array of *out is filled if non-NULL. */
+ * for (J, h) (blocking, AUTO schedule); each array of *out is filled if non-NULL.
+ * When the program with every chain state cached does not fit the context's
+ * budget left, this call and every other observable call on the lattice
+ * (tn_expectation, tn_site_expectations, tn_bond_correlators,
+ * tn_pair_correlators) take the recompute form (program choice bit 5: the
+ * same values, bit for bit, in less memory); TN_ERR_OVER_BUDGET if that does
+ * not fit either.  Served jobs do not fall back (tn_submit). */
 tn_status tn_energy(tn_lattice *lat, double J, double h, tn_precision prec, tn_result *out);
 /* Nearest-neighbour two-site correlators <A_i B_j> (blocking, AUTO schedule):
  * one Pauli operator on each site of every bond, A = op_a on the bond's first
@@ -261,14 +269,16 @@ tn_status tn_batch_results_device(tn_batch *b, const double **dev);
 /* Number of kernel launches one tn_batch_run issues. */
 tn_status tn_batch_launch_count(const tn_batch *b, int64_t *n);
 
-/* Batch groups (no counterpart in the paper; the batched form of the
- * spec workload): n lattices whose summed footprint may exceed the
+/* Batch groups (no counterpart in the paper; many lattices of uneven sizes
+ * in one launch): n lattices whose summed footprint may exceed the
  * device.  Members are split, in order, into passes of at most pass_budget
  * bytes each; the passes run one after another and share one arena (the
  * largest pass's), each keeping its small regions (inputs, slots, results,
  * tables); the launches of all passes are captured into ONE CUDA graph, so a
- * run of the whole group is one graph launch.  TN_ERR_OVER_BUDGET when a
- * member alone exceeds pass_budget or the arena the remaining budget;
+ * run of the whole group is one graph launch.  A member whose energy program
+ * alone exceeds pass_budget with its chain states cached takes the recompute
+ * form (program choice bit 5) when that fits.  TN_ERR_OVER_BUDGET when a
+ * member alone still exceeds pass_budget or the arena the remaining budget;
  * TN_ERR_NO_DEVICE without a device.  Inputs and results are concatenated in
  * member order with the layouts of tn_batch_*; member k of the generator
  * takes the seed member k of one batch would. */
@@ -298,7 +308,11 @@ typedef struct {
 
 /* Queue a job.  It is admitted to the GPU when its exact footprint fits the
  * budget left by running jobs; jobs that can never fit return
- * TN_ERR_OVER_BUDGET here.  Admitted jobs run concurrently with earlier ones:
+ * TN_ERR_OVER_BUDGET here.  Jobs take the tuning table's program choices and
+ * do not fall back to the recompute form: a job whose cached-state program
+ * exceeds the budget would hold the device for seconds to minutes, which a
+ * latency-bound stream refuses instead (set bit 5 for the shape by hand to
+ * serve it).  Admitted jobs run concurrently with earlier ones:
  * jobs whose estimated device time (from their contraction program) is at
  * most 20 ms are batched together on high-priority streams, longer ones run
  * alone on low-priority streams, so short jobs never queue behind long ones. */
@@ -414,7 +428,16 @@ tn_status tn_ite_run(tn_lattice *lat, const tn_ite_params *params, double *energ
  *   bit 3  BF16x3 / BF16x6: products of at least 2^26 multiply-adds on the
  *          tensor cores (else FP32 SIMT)
  *   bit 4  BF16x3 / BF16x6: smaller products on the tensor cores too
- * 15 (bits 0-3 set) is the fixed default; codes run from 0 to 31.  tn_autotune times every combination that
+ *   bit 5  energies and correlators: the recompute form -- the corner chains
+ *          keep only the states that start a frame row (and the finished
+ *          corners); each observable absorbs the states it needs again from
+ *          the checkpoint before them, and the environment sweep of Sec. 5
+ *          holds one state at a time, corner after corner.  The same
+ *          contractions on the same inputs, so the same bits, in a fraction of
+ *          the memory (10 x 10, D = 3, FP32: 155 GB instead of 692 GB) for
+ *          more absorptions; never chosen by tn_autotune, set by hand or taken
+ *          as the fallback described at tn_energy
+ * 15 (bits 0-3 set) is the fixed default; codes run from 0 to 63.  tn_autotune times every combination that
  * changes the program of each distinct (L[k], W[k], D[k]) on a batch of
  * copies of it (as many as fit max_bytes, 0 = 4 GiB, at most 64; shapes whose
  * single footprint exceeds max_bytes are skipped), `reps` timed runs after one

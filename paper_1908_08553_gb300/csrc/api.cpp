@@ -123,6 +123,13 @@ tn_status run_single(tn_lattice* lat, tn_precision prec, tn_schedule sched, tn_w
         BatchOpts opts;
         opts.complex_sites = lat->cplx;
         tn_status s = batch_create(lat->ctx, 1, &L, &W, &D, prec, sched, work, true, &b, nullptr, &opts);
+        // an energy whose cached chain states do not fit the budget left falls
+        // back to the recompute form (the same values, fewer bytes, more passes)
+        const int knobs = tuned_knobs(L, W, D, prec, work).code();
+        if (s == TN_ERR_OVER_BUDGET && work != TN_WORK_NORM && !(knobs & kRecomputeKnob)) {
+            opts.knobs = knobs | kRecomputeKnob;
+            s = batch_create(lat->ctx, 1, &L, &W, &D, prec, sched, work, true, &b, nullptr, &opts);
+        }
         if (s != TN_OK) return s;
         lat->cache[key] = b;
     }
@@ -506,17 +513,24 @@ tn_status tn_pair_correlators(tn_lattice* lat, tn_precision prec, int op_a, int 
     std::vector<PairSpec> pairs(n);
     for (int k = 0; k < n; ++k) pairs[k] = PairSpec{i[k], j[k], a, b};
     const int D = lat->D;
-    auto pg = program_build_plan(plan_choose(L, W, D, TN_SCHED_AUTO, TN_WORK_ENERGY), prec, TN_WORK_ENERGY,
-                                 tuned_knobs(L, W, D, prec, TN_WORK_ENERGY), &pairs, lat->cplx);
-    // a program built for one call is checked before it runs (ordering, lifetimes, no aliasing)
-    const std::string why = program_verify(*pg);
-    if (!why.empty()) { set_error(why.c_str()); return TN_ERR_NUMERIC; }
-    BatchOpts opts;
-    opts.program = pg;
-    opts.complex_sites = lat->cplx;
-    opts.use_graph = false;     // built for this call only
+    const Plan plan = plan_choose(L, W, D, TN_SCHED_AUTO, TN_WORK_ENERGY);
+    Knobs knobs = tuned_knobs(L, W, D, prec, TN_WORK_ENERGY);
     tn_batch* bt = nullptr;
-    tn_status s = batch_create(lat->ctx, 1, &L, &W, &D, prec, TN_SCHED_AUTO, TN_WORK_ENERGY, true, &bt, nullptr, &opts);
+    tn_status s = TN_OK;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        auto pg = program_build_plan(plan, prec, TN_WORK_ENERGY, knobs, &pairs, lat->cplx);
+        // a program built for one call is checked before it runs (ordering, lifetimes, no aliasing)
+        const std::string why = program_verify(*pg);
+        if (!why.empty()) { set_error(why.c_str()); return TN_ERR_NUMERIC; }
+        BatchOpts opts;
+        opts.program = pg;
+        opts.complex_sites = lat->cplx;
+        opts.use_graph = false;     // built for this call only
+        s = batch_create(lat->ctx, 1, &L, &W, &D, prec, TN_SCHED_AUTO, TN_WORK_ENERGY, true, &bt, nullptr, &opts);
+        // cached chain states over the budget left: the recompute form
+        if (s != TN_ERR_OVER_BUDGET || knobs.recompute) break;
+        knobs.recompute = true;
+    }
     if (s != TN_OK) return s;
     std::vector<double> r((size_t)bt->lay.nres);
     int status = 0;

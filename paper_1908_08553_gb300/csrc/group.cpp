@@ -66,13 +66,27 @@ tn_status tn_batch_group_create(tn_ctx* ctx, int n, const int* L, const int* W, 
         if (!ctx || !out || n <= 0 || !L || !W || !D || pass_budget == 0) return TN_ERR_INVALID;
         *out = nullptr;
         if (ctx->device < 0) { set_error("context has no device"); return TN_ERR_NO_DEVICE; }
-        // each member's footprint alone, for the split into passes
+        // each member's footprint alone, for the split into passes; an energy
+        // whose cached chain states exceed the pass budget takes the recompute
+        // form (the same values, fewer bytes)
         std::vector<size_t> fp(n);
+        std::vector<int> kn(n, -1);
         for (int k = 0; k < n; ++k) {
             tn_batch* probe = nullptr;
-            const tn_status st = batch_create(ctx, 1, &L[k], &W[k], &D[k], prec, sched, work, false, &probe, &fp[k]);
+            tn_status st = batch_create(ctx, 1, &L[k], &W[k], &D[k], prec, sched, work, false, &probe, &fp[k]);
             if (probe) delete probe;
             if (st != TN_OK) return st;
+            const int code = tuned_knobs(L[k], W[k], D[k], prec, work).code();
+            if (fp[k] > pass_budget && work != TN_WORK_NORM && !(code & kRecomputeKnob)) {
+                BatchOpts o;
+                o.knobs = code | kRecomputeKnob;
+                size_t f2 = 0;
+                probe = nullptr;
+                st = batch_create(ctx, 1, &L[k], &W[k], &D[k], prec, sched, work, false, &probe, &f2, &o);
+                if (probe) delete probe;
+                if (st != TN_OK) return st;
+                if (f2 <= pass_budget) { fp[k] = f2; kn[k] = o.knobs; }
+            }
             if (fp[k] > pass_budget) {
                 set_error("member " + std::to_string(k) + " alone needs " + std::to_string(fp[k]) +
                           " B, more than the pass budget");
@@ -102,7 +116,11 @@ tn_status tn_batch_group_create(tn_ctx* ctx, int n, const int* L, const int* W, 
         sizing.arena_external = true;
         for (const auto& mem : g->members) {
             std::vector<int> l, w, d;
-            for (int k : mem) { l.push_back(L[k]); w.push_back(W[k]); d.push_back(D[k]); }
+            sizing.member_knobs.clear();
+            for (int k : mem) {
+                l.push_back(L[k]); w.push_back(W[k]); d.push_back(D[k]);
+                sizing.member_knobs.push_back(kn[k]);
+            }
             tn_batch* probe = nullptr;
             const tn_status st = batch_create(ctx, (int)mem.size(), l.data(), w.data(), d.data(), prec, sched, work,
                                               false, &probe, nullptr, &sizing);
@@ -136,7 +154,11 @@ tn_status tn_batch_group_create(tn_ctx* ctx, int n, const int* L, const int* W, 
         g->res_off.assign(n, 0); g->res_elems.assign(n, 0);
         for (const auto& mem : g->members) {
             std::vector<int> l, w, d;
-            for (int k : mem) { l.push_back(L[k]); w.push_back(W[k]); d.push_back(D[k]); }
+            opts.member_knobs.clear();
+            for (int k : mem) {
+                l.push_back(L[k]); w.push_back(W[k]); d.push_back(D[k]);
+                opts.member_knobs.push_back(kn[k]);
+            }
             tn_batch* b = nullptr;
             const tn_status st = batch_create(ctx, (int)mem.size(), l.data(), w.data(), d.data(), prec, sched, work,
                                               true, &b, nullptr, &opts);

@@ -26,6 +26,7 @@
 // one arena.
 #include <algorithm>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <stdexcept>
 
@@ -67,9 +68,16 @@ public:
     int level_of(int tid) const { return pg_.tensors[tid].level; }
 
     int add(Op op) {
+        max_level_ = std::max(max_level_, op.level);
         pg_.ops.push_back(op);
         return (int)pg_.ops.size() - 1;
     }
+    // the last wave any op so far runs in
+    int max_level() const { return max_level_; }
+    // Every op created while a global floor is set starts after that wave
+    // (the recompute form's stages: each stage starts when the previous one
+    // has finished, so the arena reuses the previous stage's memory).
+    void set_gfloor(int f) { gfloor_ = f; }
 
     // Site matrix of `site` with physical operator `phys` in its corner's frame.
     int sitemat(int site, int phys, const CornerPlan& cp, const Step& s) {
@@ -110,7 +118,7 @@ public:
     void set_floor(int f) { floor_ = f; }
 
     int absorb(int in, int E, const Step& s, bool trans) {
-        const int level = std::max({level_of(in), level_of(E), floor_}) + 1;
+        const int level = std::max({level_of(in), level_of(E), floor_, gfloor_}) + 1;
         const int64_t nout = trans ? s.n_in : s.n_out;
         const int out = tensor(nout, level);
         Op op;
@@ -135,7 +143,7 @@ public:
 
     // scalar = <absorb(in, E), adj> with the shape of step s.
     int absorb_dot(int in, int E, int adj, const Step& s) {
-        const int level = std::max({level_of(in), level_of(E), level_of(adj)}) + 1;
+        const int level = std::max({level_of(in), level_of(E), level_of(adj), gfloor_}) + 1;
         const int out = scalar(level);
         Op op;
         op.kind = OP_ABSORB_DOT;
@@ -163,7 +171,7 @@ public:
 
     // absorb(absorb(in, E1), E2) for the consecutive steps a, b (pair_ok).
     int absorb2(int in, int E1, int E2, const Step& a, const Step& b) {
-        const int level = std::max({level_of(in), level_of(E1), level_of(E2), floor_}) + 1;
+        const int level = std::max({level_of(in), level_of(E1), level_of(E2), floor_, gfloor_}) + 1;
         const int out = tensor(b.n_out, level);
         Op op;
         op.kind = OP_ABSORB2;
@@ -179,7 +187,8 @@ public:
 
     // <absorb(absorb(in, E1), E2), adj> for the consecutive steps a, b (pair_ok).
     int absorb2_dot(int in, int E1, int E2, int adj, const Step& a, const Step& b) {
-        const int level = std::max({level_of(in), level_of(E1), level_of(E2), level_of(adj), floor_}) + 1;
+        const int level =
+            std::max({level_of(in), level_of(E1), level_of(E2), level_of(adj), floor_, gfloor_}) + 1;
         const int out = scalar(level);
         Op op;
         op.kind = OP_ABSORB2_DOT;
@@ -203,7 +212,8 @@ public:
     // (<absorb(in, E), adj>, <absorb(in, E2), adj>, <absorb(in, E3), adj>) in
     // one pass over in and adj.
     std::tuple<int, int, int> absorb_dot3(int in, int E, int E2, int E3, int adj, const Step& s) {
-        const int level = std::max({level_of(in), level_of(E), level_of(E2), level_of(E3), level_of(adj)}) + 1;
+        const int level =
+            std::max({level_of(in), level_of(E), level_of(E2), level_of(E3), level_of(adj), gfloor_}) + 1;
         const int out = scalar(level), out2 = scalar(level), out3 = scalar(level);
         Op op;
         op.kind = OP_ABSORB_DOT;
@@ -220,11 +230,12 @@ public:
 
     // Tiled BF16 planes of the operand X[r][k] = src[r*sr + k*sk] (one per view).
     int tc_split(int src, int64_t R, int64_t Kd, int64_t sr, int64_t sk) {
+        // the recompute form splits per product, so no plane set outlives its product
         auto key = std::make_tuple(src, R, Kd, sr, sk);
         auto it = split_.find(key);
-        if (it != split_.end()) return it->second;
+        if (it != split_.end() && !pg_.knobs.recompute) return it->second;
         const int64_t Rp = (R + kTcRowPad - 1) / kTcRowPad * kTcRowPad, Kp = (Kd + 63) / 64 * 64;
-        const int level = level_of(src) + 1;
+        const int level = std::max(level_of(src), gfloor_) + 1;
         // BF16 planes counted in 4-byte units of the FP32 arena
         const int out = tensor((int64_t)pg_.nsplit * Rp * Kp / 2, level);
         Op op;
@@ -252,7 +263,7 @@ public:
             // tensor cores: C = A' B'^T with A'[m][k] = A(m,k) and B'[n][k] = B(k,n)
             const int Ap = tc_split(A, M, K, sam, sak);
             const int Bp = tc_split(B, N, K, sbn, sbk);
-            int lv = std::max(level_of(Ap), level_of(Bp)) + 1;
+            int lv = std::max({level_of(Ap), level_of(Bp), gfloor_}) + 1;
             if (Cd >= 0) lv = std::max(lv, level_of(Cd) + 1);
             const int o = Cd >= 0 ? scalar(lv) : tensor(M * N, lv);
             Op op;
@@ -271,7 +282,7 @@ public:
             add(op);
             return o;
         }
-        int level = std::max(level_of(A), level_of(B)) + 1;
+        int level = std::max({level_of(A), level_of(B), gfloor_}) + 1;
         if (Cd >= 0) level = std::max(level, level_of(Cd) + 1);
         const int out = Cd >= 0 ? scalar(level) : tensor(M * N, level);
         Op op;
@@ -289,7 +300,7 @@ public:
     }
 
     int dot(int A, int B, int64_t n) {
-        const int level = std::max(level_of(A), level_of(B)) + 1;
+        const int level = std::max({level_of(A), level_of(B), gfloor_}) + 1;
         const int out = scalar(level);
         Op op;
         op.kind = OP_DOT;
@@ -307,6 +318,8 @@ private:
     Program& pg_;
     int one_ = -1;
     int floor_ = 0;
+    int gfloor_ = 0;
+    int max_level_ = 0;
     std::map<std::pair<int, int>, int> E_;
     std::map<std::tuple<int, int64_t, int64_t, int64_t, int64_t>, int> split_;
 };
@@ -450,64 +463,75 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
         const bool with_sites = work == TN_WORK_ENERGY && !pairs;
         const int bondA = work_is_bonds(work) ? work_bond_a(work) : PH_Z;
         const int bondB = work_is_bonds(work) ? work_bond_b(work) : PH_Z;
-        int Env[4] = {-1, -1, -1, -1};
+        const bool recompute = pg.knobs.recompute;
         auto nonempty = [&](int q) { return !pl.corner[q].steps.empty(); };
-        if (nonempty(TL)) Env[TL] = bd.gemm(Mbot, Qt[TR], hbL, vrT, hbR, hbR, 1, vrT, 1);
-        if (nonempty(TR)) Env[TR] = bd.gemm(Mbot, Qt[TL], hbR, vrT, hbL, 1, hbR, vrT, 1);
-        if (nonempty(BL)) Env[BL] = bd.gemm(Mtop, Qt[BR], hbL, vrB, hbR, hbR, 1, vrB, 1);
-        if (nonempty(BR)) Env[BR] = bd.gemm(Mtop, Qt[BL], hbR, vrB, hbL, 1, hbR, vrB, 1);
-        // environment sweeps
+        // the rest of the ring seen from corner q
+        auto env_of = [&](int q) {
+            switch (q) {
+                case TL: return bd.gemm(Mbot, Qt[TR], hbL, vrT, hbR, hbR, 1, vrT, 1);
+                case TR: return bd.gemm(Mbot, Qt[TL], hbR, vrT, hbL, 1, hbR, vrT, 1);
+                case BL: return bd.gemm(Mtop, Qt[BR], hbL, vrB, hbR, hbR, 1, vrB, 1);
+                default: return bd.gemm(Mtop, Qt[BL], hbR, vrB, hbL, 1, hbR, vrB, 1);
+            }
+        };
+        // environment sweeps (cached form)
         std::vector<int> G[4];
-        for (int q = 0; q < 4; ++q) {
-            const int T = (int)pl.corner[q].steps.size();
-            G[q].assign(T + 1, -1);
-            if (!T) continue;
-            G[q][T] = Env[q];
-            for (int t = T; t >= 2; --t) G[q][t - 1] = bd.absorb(G[q][t], E_at(q, t, PH_I), step_of(q, t), true);
+        if (!recompute) {
+            int Env[4] = {-1, -1, -1, -1};
+            for (int q = 0; q < 4; ++q)
+                if (nonempty(q)) Env[q] = env_of(q);
+            for (int q = 0; q < 4; ++q) {
+                const int T = (int)pl.corner[q].steps.size();
+                G[q].assign(T + 1, -1);
+                if (!T) continue;
+                G[q][T] = Env[q];
+                for (int t = T; t >= 2; --t) G[q][t - 1] = bd.absorb(G[q][t], E_at(q, t, PH_I), step_of(q, t), true);
+            }
         }
         // norm along each step's path: <F[q][t], G[q][t]> (from the site's triple
         // absorb-dot where the streaming kernel serves the step, else a dot).
         // Dividing by it cancels the rounding the numerator shares with it;
         // FP64 has no rounding worth cancelling at the library's tolerance, so
         // there every ratio takes the ring's norm and the extra dots and ring
-        // products of the path norms are not built.
+        // products of the path norms are not built.  Fm gives F[q][t-1] (the
+        // recompute form takes F[q][t] one step from it).
         const bool path_norms = pg.dt != DT_F64;
         std::map<std::pair<int, int>, int> local_norm;
-        auto norm_at = [&](int q, int t) {
+        auto norm_at = [&](int q, int t, int Gt, const std::function<int()>& Fm) {
             if (!path_norms) return pg.norm_slot;
             auto key = std::make_pair(q, t);
             auto it = local_norm.find(key);
             if (it != local_norm.end()) return it->second;
-            const int v = bd.dot(F[q][t], G[q][t], step_of(q, t).n_out);
+            const int Ft = recompute ? bd.absorb(Fm(), E_at(q, t, PH_I), step_of(q, t), false) : F[q][t];
+            const int v = bd.dot(Ft, Gt, step_of(q, t).n_out);
             const int sl = pg.tensors[v].slot;
             local_norm[key] = sl;
             return sl;
         };
-        // sites
+        // one site's observables from F[q][t-1] and G[q][t]
         pg.sx_slot.assign(with_sites ? nsite : 0, -1);
         pg.sz_slot.assign(with_sites ? nsite : 0, -1);
         pg.sx_den.assign(with_sites ? nsite : 0, -1);
         pg.sy_slot.assign(with_sites && cplx ? nsite : 0, -1);
-        for (int s = 0; s < (with_sites ? nsite : 0); ++s) {
+        auto emit_site = [&](int s, int Fm, int Gt) {
             const SiteRef& w = where[s];
             const Step& st = step_of(w.q, w.t);
             if (bd.dual_ok(st)) {
                 // the site's <X>, <Z> and the local norm <absorb(F[t-1], E_I), G[t]> in one pass
-                const auto v3 = bd.absorb_dot3(F[w.q][w.t - 1], E_at(w.q, w.t, PH_X), E_at(w.q, w.t, PH_Z),
-                                               E_at(w.q, w.t, PH_I), G[w.q][w.t], st);
+                const auto v3 = bd.absorb_dot3(Fm, E_at(w.q, w.t, PH_X), E_at(w.q, w.t, PH_Z),
+                                               E_at(w.q, w.t, PH_I), Gt, st);
                 pg.sx_slot[s] = pg.tensors[std::get<0>(v3)].slot;
                 pg.sz_slot[s] = pg.tensors[std::get<1>(v3)].slot;
                 local_norm[std::make_pair(w.q, w.t)] = pg.tensors[std::get<2>(v3)].slot;
             } else {
-                const int vx = bd.absorb_dot(F[w.q][w.t - 1], E_at(w.q, w.t, PH_X), G[w.q][w.t], st);
-                const int vz = bd.absorb_dot(F[w.q][w.t - 1], E_at(w.q, w.t, PH_Z), G[w.q][w.t], st);
+                const int vx = bd.absorb_dot(Fm, E_at(w.q, w.t, PH_X), Gt, st);
+                const int vz = bd.absorb_dot(Fm, E_at(w.q, w.t, PH_Z), Gt, st);
                 pg.sx_slot[s] = pg.tensors[vx].slot;
                 pg.sz_slot[s] = pg.tensors[vz].slot;
             }
-            if (cplx)
-                pg.sy_slot[s] = pg.tensors[bd.absorb_dot(F[w.q][w.t - 1], E_at(w.q, w.t, PH_Y), G[w.q][w.t], st)].slot;
-            pg.sx_den[s] = norm_at(w.q, w.t);
-        }
+            if (cplx) pg.sy_slot[s] = pg.tensors[bd.absorb_dot(Fm, E_at(w.q, w.t, PH_Y), Gt, st)].slot;
+            pg.sx_den[s] = norm_at(w.q, w.t, Gt, [&] { return Fm; });
+        };
         // bonds, output order: horizontal row-major, then vertical row-major
         // the correlators to form: every nearest-neighbour bond with (A, B), or the caller's pairs
         std::vector<PairSpec> bonds;
@@ -545,107 +569,209 @@ std::shared_ptr<const Program> program_build_plan(const Plan& plan, tn_precision
             }
             return x;
         };
-        auto regrow = [&](int q, int t, int op) {
-            const int T = (int)pl.corner[q].steps.size();
-            return chain(q, F[q][t - 1], t, T, -1, op, PH_I);
+        // A pair whose sites lie in two corners: both corners regrown with the
+        // operators from F[qa][ta-1] and F[qb][tb-1] to their last step, then
+        // the product(s) with the rest of the ring.  Each class of such pairs
+        // is normalised by the same fused product on the unmodified corners
+        // (the norm through the same path).
+        auto emit_cross = [&](size_t bi, int qa, int ta, int opa, int qb, int tb, int opb, int Fa, int Fb) {
+            const int Ta = (int)pl.corner[qa].steps.size(), Tb = (int)pl.corner[qb].steps.size();
+            const int Za = chain(qa, Fa, ta, Ta, -1, opa, PH_I), Zb = chain(qb, Fb, tb, Tb, -1, opb, PH_I);
+            int v = -1;
+            if (qa == TL && qb == TR) {
+                v = bd.gemm(Mbot, Zb, hbL, vrT, hbR, hbR, 1, vrT, 1, Za);
+                if (!path_norms) den_cross[0] = pg.norm_slot;
+                if (den_cross[0] < 0)
+                    den_cross[0] = pg.tensors[bd.gemm(Mbot, Qt[TR], hbL, vrT, hbR, hbR, 1, vrT, 1, Qt[TL])].slot;
+                pg.zz_den[bi] = den_cross[0];
+            } else if (qa == BL && qb == BR) {
+                v = bd.gemm(Mtop, Zb, hbL, vrB, hbR, hbR, 1, vrB, 1, Za);
+                if (!path_norms) den_cross[1] = pg.norm_slot;
+                if (den_cross[1] < 0)
+                    den_cross[1] = pg.tensors[bd.gemm(Mtop, Qt[BR], hbL, vrB, hbR, hbR, 1, vrB, 1, Qt[BL])].slot;
+                pg.zz_den[bi] = den_cross[1];
+            } else if (qa == TL && qb == BL) {
+                if (Xr < 0) Xr = bd.gemm(Qt[TR], Qt[BR], vrT, vrB, hbR, 1, vrT, vrB, 1);
+                v = bd.gemm(Za, Zb, vrT, vrB, hbL, 1, vrT, vrB, 1, Xr);
+                if (!path_norms) den_cross[2] = pg.norm_slot;
+                if (den_cross[2] < 0)
+                    den_cross[2] = pg.tensors[bd.gemm(Qt[TL], Qt[BL], vrT, vrB, hbL, 1, vrT, vrB, 1, Xr)].slot;
+                pg.zz_den[bi] = den_cross[2];
+            } else if (qa == TR && qb == BR) {
+                if (Xl < 0) Xl = bd.gemm(Qt[TL], Qt[BL], vrT, vrB, hbL, 1, vrT, vrB, 1);
+                v = bd.gemm(Za, Zb, vrT, vrB, hbR, 1, vrT, vrB, 1, Xl);
+                if (!path_norms) den_cross[3] = pg.norm_slot;
+                if (den_cross[3] < 0)
+                    den_cross[3] = pg.tensors[bd.gemm(Qt[TR], Qt[BR], vrT, vrB, hbR, 1, vrT, vrB, 1, Xl)].slot;
+                pg.zz_den[bi] = den_cross[3];
+            } else if (qa == TL && qb == BR) {
+                // diagonal corners: <Za TR^T, BL Zb^T>, two products
+                const int P1 = bd.gemm(Za, Qt[TR], hbL, hbR, vrT, vrT, 1, 1, vrT);
+                v = bd.gemm(Qt[BL], Zb, hbL, hbR, vrB, vrB, 1, 1, vrB, P1);
+                if (!path_norms) den_cross[4] = pg.norm_slot;
+                if (den_cross[4] < 0)
+                    den_cross[4] = pg.tensors[bd.gemm(Qt[BL], Qt[BR], hbL, hbR, vrB, vrB, 1, 1, vrB, Mtop)].slot;
+                pg.zz_den[bi] = den_cross[4];
+            } else if (qa == TR && qb == BL) {
+                // diagonal corners: <TL Za^T, Zb BR^T>, two products
+                const int P1 = bd.gemm(Qt[TL], Za, hbL, hbR, vrT, vrT, 1, 1, vrT);
+                v = bd.gemm(Zb, Qt[BR], hbL, hbR, vrB, vrB, 1, 1, vrB, P1);
+                if (!path_norms) den_cross[5] = pg.norm_slot;
+                if (den_cross[5] < 0)
+                    den_cross[5] = pg.tensors[bd.gemm(Qt[BL], Qt[BR], hbL, hbR, vrB, vrB, 1, 1, vrB, Mtop)].slot;
+                pg.zz_den[bi] = den_cross[5];
+            } else {
+                throw std::logic_error("pair between unknown corners");
+            }
+            return v;
         };
         pg.zz_slot.assign(bonds.size(), -1);
         pg.zz_den.assign(bonds.size(), pg.norm_slot);
-        // Bond chains run in stages: a chain whose temporaries would push the
-        // stage above kStageElems starts after every earlier chain has
-        // finished, so the arena reuses their memory (only the amount of
-        // concurrent work changes, not any value).
-        constexpr int64_t kStageElems = int64_t(1) << 27;
-        int64_t stage_used = 0;
-        int stage_floor = 0, stage_end = 0;
+        // the pairs in corner order: a.q <= b.q, and a.t < b.t inside one corner
+        struct Pair { SiteRef a, b; int opa, opb; };
+        std::vector<Pair> pr(bonds.size());
+        for (size_t bi = 0; bi < bonds.size(); ++bi) {
+            if (bonds[bi].a == bonds[bi].b || bonds[bi].a < 0 || bonds[bi].b < 0 || bonds[bi].a >= nsite ||
+                bonds[bi].b >= nsite)
+                throw std::invalid_argument("a pair needs two distinct sites of the lattice");
+            Pair& p = pr[bi];
+            p.a = where[bonds[bi].a]; p.b = where[bonds[bi].b];
+            p.opa = bonds[bi].op_a; p.opb = bonds[bi].op_b;
+            if (p.a.q > p.b.q || (p.a.q == p.b.q && p.a.t > p.b.t)) {
+                std::swap(p.a, p.b);
+                std::swap(p.opa, p.opb);
+            }
+        }
         auto max_out = [&](int q, int t0, int t1) {
             int64_t m = 0;
             for (int u = t0; u <= t1; ++u) m = std::max(m, step_of(q, u).n_out);
             return m;
         };
-        auto begin_chain = [&](int64_t temp) {
-            if (stage_used > 0 && stage_used + temp > kStageElems) {
-                stage_floor = stage_end;
-                stage_used = 0;
-            }
-            stage_used += temp;
-            bd.set_floor(stage_floor);
-        };
-        auto end_chain = [&](int last_tensor) {
-            stage_end = std::max(stage_end, pg.tensors[last_tensor].level);
-            bd.set_floor(0);
-        };
-        for (size_t bi = 0; bi < bonds.size(); ++bi) {
-            if (bonds[bi].a == bonds[bi].b || bonds[bi].a < 0 || bonds[bi].b < 0 || bonds[bi].a >= nsite ||
-                bonds[bi].b >= nsite)
-                throw std::invalid_argument("a pair needs two distinct sites of the lattice");
-            SiteRef a = where[bonds[bi].a], b = where[bonds[bi].b];
-            int opa = bonds[bi].op_a, opb = bonds[bi].op_b;
-            int v = -1;
-            if (a.q == b.q) {
-                if (a.t > b.t) { std::swap(a, b); std::swap(opa, opb); }
-                const int q = a.q;
-                begin_chain(2 * max_out(q, a.t, b.t));
-                v = chain(q, F[q][a.t - 1], a.t, b.t, G[q][b.t], opa, opb);
-                end_chain(v);
-                pg.zz_den[bi] = norm_at(q, b.t);
-            } else {
-                int qa = a.q, qb = b.q;
-                int ta = a.t, tb = b.t;
-                if (qa > qb) { std::swap(qa, qb); std::swap(ta, tb); std::swap(opa, opb); }
-                const int Ta = (int)pl.corner[qa].steps.size(), Tb = (int)pl.corner[qb].steps.size();
-                begin_chain(2 * max_out(qa, ta, Ta) + 2 * max_out(qb, tb, Tb));
-                const int Za = regrow(qa, ta, opa), Zb = regrow(qb, tb, opb);
-                // each class of cut-crossing bond is normalised by the same fused
-                // product on the unmodified corners (the norm through the same path)
-                if (qa == TL && qb == TR) {
-                    v = bd.gemm(Mbot, Zb, hbL, vrT, hbR, hbR, 1, vrT, 1, Za);
-                    if (!path_norms) den_cross[0] = pg.norm_slot;
-                    if (den_cross[0] < 0)
-                        den_cross[0] = pg.tensors[bd.gemm(Mbot, Qt[TR], hbL, vrT, hbR, hbR, 1, vrT, 1, Qt[TL])].slot;
-                    pg.zz_den[bi] = den_cross[0];
-                } else if (qa == BL && qb == BR) {
-                    v = bd.gemm(Mtop, Zb, hbL, vrB, hbR, hbR, 1, vrB, 1, Za);
-                    if (!path_norms) den_cross[1] = pg.norm_slot;
-                    if (den_cross[1] < 0)
-                        den_cross[1] = pg.tensors[bd.gemm(Mtop, Qt[BR], hbL, vrB, hbR, hbR, 1, vrB, 1, Qt[BL])].slot;
-                    pg.zz_den[bi] = den_cross[1];
-                } else if (qa == TL && qb == BL) {
-                    if (Xr < 0) Xr = bd.gemm(Qt[TR], Qt[BR], vrT, vrB, hbR, 1, vrT, vrB, 1);
-                    v = bd.gemm(Za, Zb, vrT, vrB, hbL, 1, vrT, vrB, 1, Xr);
-                    if (!path_norms) den_cross[2] = pg.norm_slot;
-                    if (den_cross[2] < 0)
-                        den_cross[2] = pg.tensors[bd.gemm(Qt[TL], Qt[BL], vrT, vrB, hbL, 1, vrT, vrB, 1, Xr)].slot;
-                    pg.zz_den[bi] = den_cross[2];
-                } else if (qa == TR && qb == BR) {
-                    if (Xl < 0) Xl = bd.gemm(Qt[TL], Qt[BL], vrT, vrB, hbL, 1, vrT, vrB, 1);
-                    v = bd.gemm(Za, Zb, vrT, vrB, hbR, 1, vrT, vrB, 1, Xl);
-                    if (!path_norms) den_cross[3] = pg.norm_slot;
-                    if (den_cross[3] < 0)
-                        den_cross[3] = pg.tensors[bd.gemm(Qt[TR], Qt[BR], vrT, vrB, hbR, 1, vrT, vrB, 1, Xl)].slot;
-                    pg.zz_den[bi] = den_cross[3];
-                } else if (qa == TL && qb == BR) {
-                    // diagonal corners: <Za TR^T, BL Zb^T>, two products
-                    const int P1 = bd.gemm(Za, Qt[TR], hbL, hbR, vrT, vrT, 1, 1, vrT);
-                    v = bd.gemm(Qt[BL], Zb, hbL, hbR, vrB, vrB, 1, 1, vrB, P1);
-                    if (!path_norms) den_cross[4] = pg.norm_slot;
-                    if (den_cross[4] < 0)
-                        den_cross[4] = pg.tensors[bd.gemm(Qt[BL], Qt[BR], hbL, hbR, vrB, vrB, 1, 1, vrB, Mtop)].slot;
-                    pg.zz_den[bi] = den_cross[4];
-                } else if (qa == TR && qb == BL) {
-                    // diagonal corners: <TL Za^T, Zb BR^T>, two products
-                    const int P1 = bd.gemm(Qt[TL], Za, hbL, hbR, vrT, vrT, 1, 1, vrT);
-                    v = bd.gemm(Zb, Qt[BR], hbL, hbR, vrB, vrB, 1, 1, vrB, P1);
-                    if (!path_norms) den_cross[5] = pg.norm_slot;
-                    if (den_cross[5] < 0)
-                        den_cross[5] = pg.tensors[bd.gemm(Qt[BL], Qt[BR], hbL, hbR, vrB, vrB, 1, 1, vrB, Mtop)].slot;
-                    pg.zz_den[bi] = den_cross[5];
-                } else {
-                    throw std::logic_error("pair between unknown corners");
+        // Chains run in stages: a chain whose temporaries would push the stage
+        // above kStageElems starts after every earlier chain has finished, so
+        // the arena reuses their memory (only the amount of concurrent work
+        // changes, not any value).
+        constexpr int64_t kStageElems = int64_t(1) << 27;
+        if (!recompute) {
+            // sites
+            for (int s = 0; s < (with_sites ? nsite : 0); ++s)
+                emit_site(s, F[where[s].q][where[s].t - 1], G[where[s].q][where[s].t]);
+            int64_t stage_used = 0;
+            int stage_floor = 0, stage_end = 0;
+            auto begin_chain = [&](int64_t temp) {
+                if (stage_used > 0 && stage_used + temp > kStageElems) {
+                    stage_floor = stage_end;
+                    stage_used = 0;
                 }
-                end_chain(v);
+                stage_used += temp;
+                bd.set_floor(stage_floor);
+            };
+            auto end_chain = [&](int last_tensor) {
+                stage_end = std::max(stage_end, pg.tensors[last_tensor].level);
+                bd.set_floor(0);
+            };
+            for (size_t bi = 0; bi < bonds.size(); ++bi) {
+                const Pair& p = pr[bi];
+                int v = -1;
+                if (p.a.q == p.b.q) {
+                    const int q = p.a.q;
+                    begin_chain(2 * max_out(q, p.a.t, p.b.t));
+                    v = chain(q, F[q][p.a.t - 1], p.a.t, p.b.t, G[q][p.b.t], p.opa, p.opb);
+                    end_chain(v);
+                    pg.zz_den[bi] = norm_at(q, p.b.t, G[q][p.b.t], {});
+                } else {
+                    const int Ta = (int)pl.corner[p.a.q].steps.size(), Tb = (int)pl.corner[p.b.q].steps.size();
+                    begin_chain(2 * max_out(p.a.q, p.a.t, Ta) + 2 * max_out(p.b.q, p.b.t, Tb));
+                    v = emit_cross(bi, p.a.q, p.a.t, p.opa, p.b.q, p.b.t, p.opb, F[p.a.q][p.a.t - 1],
+                                   F[p.b.q][p.b.t - 1]);
+                    end_chain(v);
+                }
+                pg.zz_slot[bi] = pg.tensors[v].slot;
             }
-            pg.zz_slot[bi] = pg.tensors[v].slot;
+        } else {
+            // Recompute form.  The forward chains keep only the states that
+            // start a frame row (and the finished corners); every other state
+            // is absorbed again from the checkpoint before it where an
+            // observable needs it.  Corner by corner, the environment sweep
+            // runs from the ring back to the corner's first step, holding one
+            // G[q][t] at a time, and every observable whose environment is
+            // G[q][t] is formed before the sweep moves on.
+            auto is_ckpt = [&](int q, int t) {
+                const int T = (int)pl.corner[q].steps.size();
+                return t == 0 || t == T || step_of(q, t + 1).c == 0;
+            };
+            auto ckpt_before = [&](int q, int t) {
+                while (!is_ckpt(q, t)) --t;
+                return t;
+            };
+            // F[q][t]: the checkpoint, then single steps (the forward chain's own ops)
+            auto F_at = [&](int q, int t) {
+                const int u = ckpt_before(q, t);
+                int x = F[q][u];
+                for (int v = u + 1; v <= t; ++v) x = bd.absorb(x, E_at(q, v, PH_I), step_of(q, v), false);
+                return x;
+            };
+            // a stage holds about two of the largest chain states: small
+            // observables still share a stage, large ones run one at a time
+            const int64_t stage_elems = std::min(kStageElems, 2 * pl.peak);
+            int64_t used = 0;
+            int stage_floor = 0;
+            auto stage = [&](int64_t temp) {
+                if (used > 0 && used + temp > stage_elems) {
+                    stage_floor = bd.max_level();
+                    used = 0;
+                }
+                used += temp;
+                bd.set_gfloor(stage_floor);
+            };
+            // temporaries of a chain from the checkpoint before step t0 through step t1
+            auto chain_temp = [&](int q, int t0, int t1) {
+                const int u = ckpt_before(q, t0 - 1);
+                return 2 * max_out(q, std::max(u, 1), std::max(t1, 1));
+            };
+            std::vector<std::vector<size_t>> inner(4 * (nsite + 1));
+            std::vector<size_t> cross;
+            for (size_t bi = 0; bi < bonds.size(); ++bi) {
+                if (pr[bi].a.q == pr[bi].b.q) inner[pr[bi].b.q * (nsite + 1) + pr[bi].b.t].push_back(bi);
+                else cross.push_back(bi);
+            }
+            for (int q = 0; q < 4; ++q) {
+                const int T = (int)pl.corner[q].steps.size();
+                if (!T) continue;
+                stage(stage_elems);
+                int Gt = env_of(q);
+                for (int t = T; t >= 1; --t) {
+                    const int64_t nt = step_of(q, t).n_out;
+                    if (with_sites) {
+                        stage(chain_temp(q, t, t) + nt);
+                        emit_site(site_of(q, t), F_at(q, t - 1), Gt);
+                    }
+                    for (size_t bi : inner[q * (nsite + 1) + t]) {
+                        const Pair& p = pr[bi];
+                        stage(chain_temp(q, p.a.t, t) + nt);
+                        const int v = chain(q, F_at(q, p.a.t - 1), p.a.t, t, Gt, p.opa, p.opb);
+                        pg.zz_slot[bi] = pg.tensors[v].slot;
+                        pg.zz_den[bi] = norm_at(q, t, Gt, [&] { return F_at(q, t - 1); });
+                    }
+                    if (t >= 2) {
+                        stage(step_of(q, t).n_in + nt);
+                        Gt = bd.absorb(Gt, E_at(q, t, PH_I), step_of(q, t), true);
+                    }
+                }
+            }
+            // pairs across the cuts, one class after another (the cached
+            // products of a class die before the next class starts)
+            auto cls = [&](size_t bi) { return pr[bi].a.q * 4 + pr[bi].b.q; };
+            std::stable_sort(cross.begin(), cross.end(), [&](size_t x, size_t y) { return cls(x) < cls(y); });
+            for (size_t bi : cross) {
+                const Pair& p = pr[bi];
+                const int Ta = (int)pl.corner[p.a.q].steps.size(), Tb = (int)pl.corner[p.b.q].steps.size();
+                stage(chain_temp(p.a.q, p.a.t, Ta) + chain_temp(p.b.q, p.b.t, Tb));
+                const int v = emit_cross(bi, p.a.q, p.a.t, p.opa, p.b.q, p.b.t, p.opb, F_at(p.a.q, p.a.t - 1),
+                                         F_at(p.b.q, p.b.t - 1));
+                pg.zz_slot[bi] = pg.tensors[v].slot;
+            }
+            bd.set_gfloor(0);
         }
     }
     int nl = 0;

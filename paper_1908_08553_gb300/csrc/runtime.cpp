@@ -469,7 +469,10 @@ tn_status batch_create(tn_ctx* ctx, int n, const int* L, const int* W, const int
         std::shared_ptr<const Program> pg;
         try {
             pg = opts->program ? opts->program
-                               : program_cached(L[k], W[k], D[k], sched, prec, work, opts->knobs, opts->complex_sites);
+                               : program_cached(L[k], W[k], D[k], sched, prec, work,
+                                                (int)opts->member_knobs.size() == n ? opts->member_knobs[k]
+                                                                                     : opts->knobs,
+                                                opts->complex_sites);
             if (pg->plan.L != L[k] || pg->plan.W != W[k] || pg->plan.D != D[k] || pg->cplx != opts->complex_sites) {
                 set_error("the given program is for another lattice shape");
                 return TN_ERR_INVALID;

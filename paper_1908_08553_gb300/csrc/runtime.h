@@ -109,6 +109,7 @@ struct BatchOpts {
     bool async_alloc = false;        // cudaMallocAsync / cudaFreeAsync on that stream
     bool use_graph = true;           // capture the launch sequence on the first run
     int knobs = -1;                  // program knobs (Knobs::code); -1: the tuning table's choice
+    std::vector<int> member_knobs;   // per member instead of knobs (when not empty)
     std::shared_ptr<const Program> program;   // every member runs this program (its shape must match)
     bool complex_sites = false;      // complex site tensors (every member)
     bool arena_external = false;     // no arena in the batch buffer: the tensors live in ext_arena

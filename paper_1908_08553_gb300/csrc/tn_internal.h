@@ -144,19 +144,24 @@ struct Knobs {
                                 // matrix, on the tensor cores in the split-BF16 precisions)
     bool tc_products = true;    // BF16x3 / BF16x6: products of >= 2^26 multiply-adds on the tensor cores
     bool tc_small = false;      // ... and the smaller ones too (else FP32 SIMT)
+    bool recompute = false;     // energies: keep only the chain states that start a frame row and
+                                // recompute the others where an observable needs them, one
+                                // observable after another (memory-bounded; the same ops on the
+                                // same inputs, so the same bits)
     int code() const {
         return (fuse_pairs ? 1 : 0) | (site_triple ? 2 : 0) | (factor_d3 ? 4 : 0) | (tc_products ? 8 : 0) |
-               (tc_small ? 16 : 0);
+               (tc_small ? 16 : 0) | (recompute ? 32 : 0);
     }
     static Knobs from_code(int c) {
         Knobs k;
         k.fuse_pairs = c & 1; k.site_triple = c & 2; k.factor_d3 = c & 4; k.tc_products = c & 8;
-        k.tc_small = c & 16;
+        k.tc_small = c & 16; k.recompute = c & 32;
         return k;
     }
 };
 constexpr int kDefaultKnobs = 15;
-constexpr int kMaxKnobs = 31;
+constexpr int kMaxKnobs = 63;
+constexpr int kRecomputeKnob = 32;
 
 // Result addressing inside one program: which scalar slots hold what.
 struct Program {

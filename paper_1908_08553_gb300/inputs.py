@@ -105,6 +105,32 @@ def product_lattice(L: int, W: int, a0: np.ndarray, a1: np.ndarray) -> np.ndarra
     return out
 
 
+def product_lattice_bonds(L: int, W: int, D: int, a0: np.ndarray, a1: np.ndarray, seed: int,
+                          with_bonds: bool = False):
+    """A product state written with bond dimension D: site k is
+    (a0[k], a1[k]) on p times one seeded uniform[-1, 1) vector per bond,
+    the same vector on both ends of the bond (edge legs: [1]).  Every bond
+    contracts to the scalar |v|^2, so the amplitudes are those of the D = 1
+    product state times a positive constant.  with_bonds: also return the
+    horizontal and vertical bond vectors, shapes (L, W-1, D) and (L-1, W, D)."""
+    rng = np.random.default_rng(seed)
+    hv = rng.uniform(-1.0, 1.0, (L, max(W - 1, 0), D))   # bond (r, c)-(r, c+1)
+    vv = rng.uniform(-1.0, 1.0, (max(L - 1, 0), W, D))   # bond (r, c)-(r+1, c)
+    one = np.ones(1)
+    a0 = np.asarray(a0, dtype=np.float64).ravel()
+    a1 = np.asarray(a1, dtype=np.float64).ravel()
+    sites = []
+    for r in range(L):
+        for c in range(W):
+            u = vv[r - 1, c] if r > 0 else one
+            l = hv[r, c - 1] if c > 0 else one
+            dn = vv[r, c] if r < L - 1 else one
+            rt = hv[r, c] if c < W - 1 else one
+            p = np.array([a0[r * W + c], a1[r * W + c]])
+            sites.append(np.einsum("p,u,l,d,r->puldr", p, u, l, dn, rt))
+    return (join_sites(sites), hv, vv) if with_bonds else join_sites(sites)
+
+
 def split_sites(flat: np.ndarray, L: int, W: int, D: int):
     """View the flat array as a list of rank-5 site tensors [p][u][l][dn][rt]."""
     out, off = [], 0

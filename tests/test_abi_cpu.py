@@ -282,7 +282,7 @@ def test_autotune_table_on_the_host(cpu_ctx, tmp_path):
         tn.tn_autotune_load(path)
         assert tn.tn_autotune_lookup(8, 8, 2, tn.TN_FP32) ["knobs"] == 14
         with pytest.raises(tn.TNError):
-            tn.tn_autotune_set(8, 8, 2, tn.TN_FP32, tn.TN_WORK_ENERGY, 32)
+            tn.tn_autotune_set(8, 8, 2, tn.TN_FP32, tn.TN_WORK_ENERGY, 64)
         with pytest.raises(tn.TNError) as e:
             tn.tn_autotune(cpu_ctx, [4], [4], [2], tn.TN_FP32)
         assert e.value.status == tn.TN_ERR_NO_DEVICE
@@ -345,3 +345,40 @@ def test_batch_group_arguments(cpu_ctx):
     with pytest.raises(tn.TNError) as e:
         tn.tn_batch_group_create(cpu_ctx, [], [], [], tn.TN_FP32, 1 << 30)
     assert e.value.status == tn.TN_ERR_INVALID
+
+
+def test_recompute_form_footprints(cpu_ctx):
+    """Program choice bit 32 (the recompute form of the energy program): its
+    programs pass the builder's consistency check (ordering, lifetimes, no two
+    live tensors sharing bytes), need less memory than the cached form, and
+    bring the D = 3 lattices of up to 10 x 10 under one GB300's memory."""
+    tn.tn_autotune_clear()
+    try:
+        E = tn.TN_WORK_ENERGY
+        cases = [(6, 6, 2, tn.TN_FP32), (8, 8, 2, tn.TN_FP64), (6, 6, 3, tn.TN_BF16X6), (7, 7, 3, tn.TN_FP32),
+                 (5, 7, 3, tn.TN_FP32), (12, 12, 2, tn.TN_BF16X3)]
+        for (L, W, D, prec) in cases:
+            lat = tn.tn_create_lattice(cpu_ctx, L, W, D)
+            try:
+                cached = tn.tn_program_info(lat, prec, tn.TN_SCHED_AUTO, E)
+                tn.tn_autotune_set(L, W, D, prec, E, 15 | 32)
+                rec = tn.tn_program_info(lat, prec, tn.TN_SCHED_AUTO, E)     # verified by the builder
+                tn.tn_autotune_set(L, W, D, prec, E, 15)
+                assert rec["footprint_bytes"] < cached["footprint_bytes"], (L, W, D, prec)
+                assert rec["product_macs"] == cached["product_macs"]
+                assert rec["ops"] > cached["ops"]                   # the recomputed chain steps
+            finally:
+                tn.tn_destroy_lattice(lat)
+        # cached form vs recompute form, FP32 (GB): the ring products stay, the caches go
+        for (L, W, D, lim) in [(9, 9, 3, 80e9), (9, 10, 3, 130e9), (10, 10, 3, 160e9), (9, 11, 3, 64e9),
+                               (8, 12, 3, 8e9)]:
+            lat = tn.tn_create_lattice(cpu_ctx, L, W, D)
+            try:
+                cached = tn.tn_footprint(lat, tn.TN_SCHED_AUTO, tn.TN_FP32, E)
+                tn.tn_autotune_set(L, W, D, tn.TN_FP32, E, 15 | 32)
+                rec = tn.tn_footprint(lat, tn.TN_SCHED_AUTO, tn.TN_FP32, E)
+                assert cached > 200e9 and rec < lim, (L, W, D, cached, rec)
+            finally:
+                tn.tn_destroy_lattice(lat)
+    finally:
+        tn.tn_autotune_clear()

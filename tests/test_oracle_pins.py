@@ -95,6 +95,24 @@ def test_product_state_closed_form(L, W):
     np.testing.assert_allclose(ob.szsz, zz, atol=1e-13)
 
 
+@pytest.mark.parametrize("L,W,D", [(3, 4, 2), (2, 3, 3)])
+def test_product_state_with_bonds_closed_form(L, W, D):
+    # the same product state written with bond dimension D (one vector per
+    # bond on both ends): each bond adds |v|^4 to the norm, nothing else
+    rng = np.random.default_rng(L * 10 + W + D)
+    a0 = rng.uniform(-1, 1, L * W)
+    a1 = rng.uniform(-1, 1, L * W)
+    A, hv, vv = inputs.product_lattice_bonds(L, W, D, a0, a1, 77, with_bonds=True)
+    ob = oracle.observables(L, W, D, A)
+    q = a0 ** 2 + a1 ** 2
+    log2n = np.sum(np.log2(q)) + 2 * (np.sum(np.log2(np.sum(hv ** 2, -1))) + np.sum(np.log2(np.sum(vv ** 2, -1))))
+    assert abs(ob.log2_norm - log2n) < 1e-12 * max(1.0, abs(log2n))
+    np.testing.assert_allclose(ob.sx, 2 * a0 * a1 / q, atol=1e-13)
+    z = (a1 ** 2 - a0 ** 2) / q
+    zz = [z[ri * W + ci] * z[rj * W + cj] for (ri, ci), (rj, cj) in inputs.bonds(L, W)]
+    np.testing.assert_allclose(ob.szsz, zz, atol=1e-13)
+
+
 # --------------------------------------- all-ones workload of Sec. 6 (exact)
 
 @pytest.mark.parametrize("L,W,D", [(4, 4, 2), (5, 5, 2), (6, 6, 2), (8, 8, 2), (3, 7, 2)])
