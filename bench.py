@@ -737,11 +737,13 @@ def run_next(args):
 
 # ------------------------------------------------------------------ serving --
 
-def serve_stream(n: int, calibrate: int, precision: str, seq_seconds: float) -> dict:
+def serve_stream(n: int, calibrate: int, precision: str, seq_seconds: float, recompute: bool = False) -> dict:
     """Serving: a Poisson stream of requests (L, W ~ U{4..12}, D ~ U{2,3},
     h ~ U[0.5, 5], seeded tensors) at 80% of the measured capacity, admitted by
     exact footprint against a 160 GB budget; p50/p99 latency and throughput,
-    beside sequential FP64 solves of the same requests (the lighter ones)."""
+    beside sequential FP64 solves of the same requests (the lighter ones).
+    recompute: shapes whose cached-state program exceeds the budget are served
+    in the recompute form (program choice bit 5 set in the tuning table)."""
     import threading
 
     import numpy as np
@@ -756,6 +758,17 @@ def serve_stream(n: int, calibrate: int, precision: str, seq_seconds: float) -> 
              float(rng.uniform(0.5, 5.0)), 10_000 + k) for k in range(n + calibrate)]
     ctx = tn.tn_ctx_create(torch.cuda.current_device(), budget)
     probe = tn.tn_ctx_create(-1)
+    recompute_shapes = []
+    if recompute:
+        for (L, W, D) in sorted({r[:3] for r in reqs}):
+            lat = tn.tn_create_lattice(probe, L, W, D)
+            if tn.tn_footprint(lat, tn.TN_SCHED_AUTO, prec, tn.TN_WORK_ENERGY) > budget:
+                tn.tn_autotune_set(L, W, D, prec, tn.TN_WORK_ENERGY, 15 | 32)
+                if tn.tn_footprint(lat, tn.TN_SCHED_AUTO, prec, tn.TN_WORK_ENERGY) <= budget:
+                    recompute_shapes.append((L, W, D))
+                else:
+                    tn.tn_autotune_set(L, W, D, prec, tn.TN_WORK_ENERGY, 15)
+            tn.tn_destroy_lattice(lat)
     fits = []
     for (L, W, D, h, seed) in reqs:
         lat = tn.tn_create_lattice(probe, L, W, D)
@@ -860,6 +873,8 @@ def serve_stream(n: int, calibrate: int, precision: str, seq_seconds: float) -> 
     return {"metric": "served p50/p99 latency", "workload": "Poisson stream of TFIM-PEPS energy requests",
             "unit": "s", "precision": precision, "requests": n, "served": served,
             "rejected_over_budget": rejected, "budget_gb": budget / 1e9, "capacity_jobs_per_s": cap,
+            "recompute_form_shapes": recompute_shapes,
+            "recompute_form_served": int(sum(1 for t in done if shapes_of[t] in set(recompute_shapes))),
             "offered_rate_jobs_per_s": rate, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
             "throughput_energies_per_s": served / (t_end - t_start),
@@ -883,7 +898,7 @@ def serve_stream(n: int, calibrate: int, precision: str, seq_seconds: float) -> 
 def run_serve(args):
     import torch
     torch.cuda.set_device(0)
-    line = serve_stream(args.requests, args.calibrate, args.precision or "bf16x6", args.seq_seconds)
+    line = serve_stream(args.requests, args.calibrate, args.precision or "bf16x6", args.seq_seconds, args.recompute)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1148,7 +1163,7 @@ def main():
     ap.add_argument("--work", default="energy", choices=["energy", "norm"], help="case: work kind")
     ap.add_argument("--recompute", action="store_true",
                     help="case: the recompute form of the energy program (chain states recomputed, not cached); "
-                         "batch: members whose cached form exceeds the pass budget run in the recompute form")
+                         "batch / serve: lattices whose cached form exceeds the budget run in the recompute form")
     ap.add_argument("--clock-log", default=None, help="CSV file for the nvidia-smi clock samples")
     ap.add_argument("--members", type=int, default=512, help="batch: lattices")
     ap.add_argument("--batch-seed", type=int, default=2, help="batch: tensor seed")
