@@ -792,16 +792,157 @@ k_absorb_2pass(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restric
     }
 }
 
+// FP32 form of the same two passes with paired FMAs (fma.rn.f32x2): pass 1
+// pairs the i_b index -- a thread's inputs are held as (i_b, i_b + 1) register
+// pairs, each factor entry of Fa as an (f, f) pair in shared memory -- and
+// pass 2 pairs the o_b index against (o_b, o_b + 1) pairs of Fb rows read as
+// 16-byte loads.  Every output accumulates the same products in the same
+// order as k_absorb_2pass<float>, so the results are the same bits, with about
+// half the arithmetic and shared-memory instructions.
+template <int MODE>
+__global__ void __launch_bounds__(kTwoPassThreads)
+k_absorb_2pass_f32(const AbsorbTask* __restrict__ tasks, int ntasks, Slot* __restrict__ slots,
+                   const int* __restrict__ tmap) {
+    pdl_enter();
+    __shared__ __align__(16) unsigned long long FaD[2][9][9];   // (f, f): [p][i_a][o_a]
+    __shared__ __align__(16) unsigned long long FbP[2][9][6];   // (o_b, o_b + 1) pairs, the last (8, 0)
+    __shared__ double red[32];
+    const long long tile = blockIdx.x;
+    const AbsorbTask& t = tasks[tmap ? __ldg(tmap + tile) : find_task(tasks, ntasks, tile)];
+    const float* F = static_cast<const float*>(t.E);
+    for (int idx = threadIdx.x; idx < 162; idx += blockDim.x) {
+        const int p = idx / 81, io = idx - p * 81, i = io / 9, o = io - i * 9;
+        // forward: [p][in = (h u)][out = (dn rt)]; backward: in and out swap
+        const float v = F[idx];
+        if (t.transE) FaD[p][o][i] = f2_pack(v, v); else FaD[p][i][o] = f2_pack(v, v);
+    }
+    for (int idx = threadIdx.x; idx < 2 * 9 * 6; idx += blockDim.x) {
+        const int p = idx / 54, rem = idx - p * 54, ib = rem / 6, j = rem - ib * 6;
+        auto fb = [&](int ob) -> float {
+            if (ob > 8) return 0.0f;
+            return t.transE ? F[162 + p * 81 + ob * 9 + ib] : F[162 + p * 81 + ib * 9 + ob];
+        };
+        FbP[p][ib][j] = f2_pack(fb(2 * j), fb(2 * j + 1));
+    }
+    int e_in = slot_shift(&slots[t.slot_in]), e_adj = 0;
+    const float sc_in = pow2<float>(-e_in);
+    float sc_adj = 1.0f;
+    if (MODE == 2) { e_adj = slot_shift(&slots[t.slot_adj]); sc_adj = pow2<float>(-e_adj); }
+    __syncthreads();
+    const long long S = t.S;
+    const long long local = tile - t.tile0;
+    const long long o = local * kTwoPassThreads + threadIdx.x;
+    double lmax = 0.0;
+    CSum<float> dacc;
+    if (o < t.P * S) {
+        const long long p0 = o / S, s = o - p0 * S;
+        const float* in = static_cast<const float*>(t.in) + p0 * 81 * S + s;
+        unsigned long long xp[9][4];   // (X(i_a, 2j), X(i_a, 2j + 1))
+        float xs[9];                   // X(i_a, 8)
+#pragma unroll
+        for (int ia = 0; ia < 9; ++ia) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                xp[ia][j] = f2_pack(in[(long long)dl_index(ia, 2 * j) * S] * sc_in,
+                                    in[(long long)dl_index(ia, 2 * j + 1) * S] * sc_in);
+            xs[ia] = in[(long long)dl_index(ia, 8) * S] * sc_in;
+        }
+        float* out = MODE == 1 ? static_cast<float*>(t.out) + p0 * 81 * S + s : nullptr;
+        const float* adj = MODE == 2 ? static_cast<const float*>(t.adj) + p0 * 81 * S + s : nullptr;
+        float m = 0.0f;
+#pragma unroll 1
+        for (int oa = 0; oa < 9; ++oa) {
+            unsigned long long tp[2][4];
+            float ts[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                ts[q] = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) tp[q][j] = 0ull;
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+#pragma unroll
+                for (int ia = 0; ia < 9; ++ia) {
+                    const unsigned long long f2 = FaD[q][ia][oa];
+                    float f, f_dup;
+                    f2_unpack(f2, f, f_dup);
+                    (void)f_dup;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) f2_fma(tp[q][j], xp[ia][j], f2);
+                    ts[q] = fmaf(xs[ia], f, ts[q]);
+                }
+            unsigned long long yp[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+#pragma unroll
+                for (int ib = 0; ib < 9; ++ib) {
+                    float tv;
+                    if (ib == 8) {
+                        tv = ts[q];
+                    } else {
+                        float lo, hi;
+                        f2_unpack(tp[q][ib / 2], lo, hi);
+                        tv = (ib & 1) ? hi : lo;
+                    }
+                    const unsigned long long tv2 = f2_pack(tv, tv);
+                    const ulonglong2 b01 = *reinterpret_cast<const ulonglong2*>(&FbP[q][ib][0]);
+                    const ulonglong2 b23 = *reinterpret_cast<const ulonglong2*>(&FbP[q][ib][2]);
+                    const unsigned long long b4 = FbP[q][ib][4];
+                    f2_fma(yp[0], tv2, b01.x);
+                    f2_fma(yp[1], tv2, b01.y);
+                    f2_fma(yp[2], tv2, b23.x);
+                    f2_fma(yp[3], tv2, b23.y);
+                    f2_fma(yp[4], tv2, b4);
+                }
+            float y[10];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) f2_unpack(yp[j], y[2 * j], y[2 * j + 1]);
+            // output n = (oa, ob) sits at (oa / 3) * 27 + (oa % 3) * 3 + (ob / 3) * 9 + ob % 3
+            const long long nb = (long long)((oa / 3) * 27 + (oa % 3) * 3) * S;
+            if (MODE == 1) {
+#pragma unroll
+                for (int ob = 0; ob < 9; ++ob) {
+                    out[nb + ((ob / 3) * 9 + ob % 3) * S] = y[ob];
+                    m = fmaxf(m, fabsf(y[ob]));
+                }
+            } else {
+                float part = 0.0f;
+#pragma unroll
+                for (int ob = 0; ob < 9; ++ob) part = fmaf(y[ob], __ldg(adj + nb + ((ob / 3) * 9 + ob % 3) * S), part);
+                dacc.add(part * sc_adj);
+            }
+        }
+        lmax = (double)m;
+    }
+    if (MODE == 1) {
+        const double mx = block_max(lmax, red);
+        if (threadIdx.x == 0) {
+            record_max(&slots[t.slot_out], mx);
+            if (local == 0) slots[t.slot_out].X = slots[t.slot_in].X + e_in + slots[t.slot_E].X;
+        }
+    } else {
+        const double part = block_sum((double)dacc.value(), red);
+        const long long X = slots[t.slot_in].X + e_in + slots[t.slot_E].X + slots[t.slot_adj].X + e_adj;
+        finish_sum(part, t.partial, t.ntiles, local, &slots[t.slot_out], X, red);
+    }
+}
+
 long long absorb_2pass_tiles(long long P, long long S) { return (P * S + kTwoPassThreads - 1) / kTwoPassThreads; }
 
 namespace {
 template <typename T, int MODE>
 cudaError_t launch_2pass_t(const AbsorbTask* tasks, int ntasks, long long nblocks, Slot* slots, cudaStream_t st,
                            const int* tmap) {
-    const size_t smem = sizeof(T) == 8 ? (size_t)81 * kTwoPassThreads * sizeof(T) : 0;
-    auto fn = k_absorb_2pass<T, MODE>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    TN_LAUNCH(fn, dim3((unsigned)nblocks), dim3(kTwoPassThreads), smem, st, tasks, ntasks, slots, tmap);
+    if constexpr (sizeof(T) == 4) {
+        TN_LAUNCH(k_absorb_2pass_f32<MODE>, dim3((unsigned)nblocks), dim3(kTwoPassThreads), 0, st, tasks, ntasks,
+                  slots, tmap);
+    } else {
+        const size_t smem = (size_t)81 * kTwoPassThreads * sizeof(T);
+        auto fn = k_absorb_2pass<T, MODE>;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        TN_LAUNCH(fn, dim3((unsigned)nblocks), dim3(kTwoPassThreads), smem, st, tasks, ntasks, slots, tmap);
+    }
     return cudaGetLastError();
 }
 }  // namespace
