@@ -234,3 +234,54 @@ def test_10x10_d3_product_state_closed_form_bf16x6(ctx):
     log2n = float(np.sum(np.log2(a0 ** 2 + a1 ** 2)))
     log2n += 2.0 * float(np.sum(np.log2(np.sum(hv ** 2, axis=-1))) + np.sum(np.log2(np.sum(vv ** 2, axis=-1))))
     assert abs(math.log2(abs(mant)) + exp2 - log2n) <= 1e-5 * abs(log2n)
+
+
+def test_pairs_fall_back_when_the_cache_does_not_fit(ctx):
+    L, W, D, prec = 7, 7, 3, tn.TN_FP32
+    A = inputs.random_lattice(L, W, D, 9700)
+    rng = np.random.default_rng(97)
+    i = rng.integers(0, L * W, 40)
+    j = (i + rng.integers(1, L * W, 40)) % (L * W)
+    f_cached = _footprint(L, W, D, prec)
+    f_rec = _footprint(L, W, D, prec, knobs=15 | RECOMPUTE)
+    out = []
+    small = tn.tn_ctx_create(0, (f_rec + f_cached) // 2)
+    try:
+        for c in (ctx, small):
+            lat = tn.tn_create_lattice(c, L, W, D)
+            try:
+                tn.tn_set_site_tensors(lat, A)
+                out.append(tn.tn_pair_correlators(lat, prec, tn.TN_OP_X, tn.TN_OP_Z, i, j).copy())
+            finally:
+                tn.tn_destroy_lattice(lat)
+    finally:
+        tn.tn_ctx_destroy(small)
+    assert np.array_equal(out[0], out[1])
+
+
+def test_served_in_the_recompute_form(ctx):
+    # the server takes the table's choice: with bit 5 set for the shape, a job
+    # whose cached form exceeds the budget is admitted and equals the lattice alone
+    L, W, D, prec = 7, 7, 3, tn.TN_FP32
+    f_cached = _footprint(L, W, D, prec)
+    f_rec = _footprint(L, W, D, prec, knobs=15 | RECOMPUTE)
+    srv = tn.tn_ctx_create(0, (f_rec + f_cached) // 2)
+    try:
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_submit(srv, L, W, D, prec, 1.0, 3.04, seed=9800)
+        assert e.value.status == tn.TN_ERR_OVER_BUDGET
+        tn.tn_autotune_set(L, W, D, prec, E, 15 | RECOMPUTE)
+        t = tn.tn_submit(srv, L, W, D, prec, 1.0, 3.04, seed=9800)
+        r, sx, zz = tn.tn_wait(srv, t, 300.0, L, W)
+        served = (r.energy, r.norm.mant, r.norm.exp2)
+    finally:
+        tn.tn_ctx_destroy(srv)
+    tn.tn_autotune_clear()
+    lat = tn.tn_create_lattice(ctx, L, W, D)
+    try:
+        tn.tn_fill_random(lat, 9800)
+        r2, sx2, zz2 = tn.tn_energy(lat, 1.0, 3.04, prec, tn.TN_SCHED_AUTO, L, W)
+    finally:
+        tn.tn_destroy_lattice(lat)
+    assert served == (r2.energy, r2.norm.mant, r2.norm.exp2)
+    assert np.array_equal(sx, sx2) and np.array_equal(zz, zz2)
