@@ -453,7 +453,7 @@ tn_status tn_autotune(tn_ctx *ctx, int n, const int *L, const int *W, const int 
  * default mean ms per batch run of the tuning batch, tuned = 1 if present. */
 tn_status tn_autotune_lookup(int L, int W, int D, tn_precision prec, tn_work work, int *knobs, double *best_ms,
                              double *default_ms, int *tuned);
-/* Set a shape's choice by hand (knobs 0..15). */
+/* Set a shape's choice by hand (knobs 0..63; TN_ERR_INVALID otherwise). */
 tn_status tn_autotune_set(int L, int W, int D, tn_precision prec, tn_work work, int knobs);
 tn_status tn_autotune_clear(void);
 /* The table as text, one shape per line; load merges a saved table. */
