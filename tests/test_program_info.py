@@ -67,3 +67,23 @@ def test_invalid_work_is_rejected(cpu_ctx):
         assert e.value.status == tn.TN_ERR_INVALID
     finally:
         tn.tn_destroy_lattice(lat)
+
+
+@pytest.mark.parametrize("L,W,D", SHAPES + [(6, 6, 3), (7, 7, 3), (8, 8, 3), (2, 9, 3), (9, 1, 2), (5, 4, 4)])
+@pytest.mark.parametrize("prec", [tn.TN_FP64, tn.TN_FP32, tn.TN_BF16X6])
+def test_recompute_programs_are_consistent(cpu_ctx, L, W, D, prec):
+    """Program choice bit 32 (the recompute form): the same checks, every
+    product of the cached form kept, the recomputed chain steps on top, and
+    never more memory than the cached form once the cached chain states pass
+    a few megabytes."""
+    tn.tn_autotune_clear()
+    try:
+        cached = _info(cpu_ctx, L, W, D, prec, tn.TN_WORK_ENERGY)
+        tn.tn_autotune_set(L, W, D, prec, tn.TN_WORK_ENERGY, 15 | 32)
+        rec = _info(cpu_ctx, L, W, D, prec, tn.TN_WORK_ENERGY)
+    finally:
+        tn.tn_autotune_clear()
+    assert rec["product_macs"] == cached["product_macs"]
+    assert rec["ops"] >= cached["ops"] and rec["absorb_bytes"] >= cached["absorb_bytes"]
+    if cached["arena_bytes"] > 4e6:
+        assert rec["footprint_bytes"] < cached["footprint_bytes"]
